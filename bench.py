@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Throughput of disk-blended light field rendering of stereo eye views.
+
+Workload (default): the rig-scale light field - 24 textured spheres in a
+backdrop, 1,024 source views of 1024x1024 (120 degrees) spread over a capture
+sphere of radius 0.35 m, 64x64 per-view meshes, FP32 RGBA textures resident
+in HBM - rendered as a stereo pair of 1440x1600 eye views (IPD 64 mm) per
+step, cycling through seeded random head poses.  A step is one lf_render call
+for both eyes.  L2 is flushed (a 256 MiB write) between steps, outside the
+timed events.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead (the
+reference arm: the plain FP64 restatement of the method on the host cores),
+on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "output Mpix/s (stereo eye views) vs plain FP32 form; % texel-fetch HBM roofline"
+UNIT = "Mpix/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["rig", "tiny"], default="rig")
+    p.add_argument("--poses", type=int, default=8, help="distinct head poses cycled through")
+    p.add_argument("--tex", choices=["f32", "u8", "bf16", "fp8"], default="f32")
+    p.add_argument("--tile", default="16x16")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound on the CPU baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name: str, n_heads: int, rank: int):
+    import scene
+
+    if name == "tiny":
+        lf = scene.tiny_light_field(1)
+        rng = scene.SplitMix64(1000 + rank)
+        import math as m
+        lf.eyes = []
+        for _ in range(n_heads):
+            lf.eyes += scene.head_pose_eyes(rng, 256, 256, 90.0, yaw_range=(-m.radians(10), m.radians(10)),
+                                            pitch_deg=10.0)
+        desc = ("tiny cap: 8 spheres, 16 views 128x128 (90 deg) on a 40 deg cap, 32x32 meshes, "
+                "stereo 2x256x256 eyes")
+    else:
+        lf = scene.rig_light_field(1, n_heads=0)
+        rng = scene.SplitMix64(29 + 7919 + 104729 * rank)
+        for _ in range(n_heads):
+            lf.eyes += scene.head_pose_eyes(rng, 1440, 1600, 100.0)
+        desc = ("rig scale: 24 spheres, 1024 Fibonacci views 1024x1024 (120 deg) on a 0.35 m sphere, "
+                "64x64 meshes, stereo 2x1440x1600 eyes (100 deg, IPD 64 mm)")
+    heads = [lf.eyes[2 * k:2 * k + 2] for k in range(n_heads)]
+    return lf, heads, desc
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lf_raster.cu", "lf_internal.h"):
+        with open(os.path.join(ROOT, "paper_1810_08860_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, tex: str, tile: str):
+    """DRAM bytes per raster launch from the committed ncu summary, if it was
+    taken on the current kernel source for this workload; else None."""
+    path = os.path.join(ROOT, "profiles", "raster_%s_%s_%s.txt" % (workload, tex, tile))
+    try:
+        vals = {}
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    vals[k.strip()] = v.strip()
+        if vals.get("kernel_source_sha") != kernel_source_hash():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(lf, eye, seconds: float):
+    """The oracle, as it stands, on the host cores: Mpix/s over a bounded
+    sample of random pixels of one eye of the workload."""
+    import numpy as np
+
+    import oracle
+
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(7)
+    n = 2000
+    total_pix, total_t = 0, 0.0
+    while True:
+        pix = np.stack([rng.integers(0, eye.width, n), rng.integers(0, eye.height, n)], axis=1)
+        t0 = time.perf_counter()
+        oracle.render(lf, eye, pixels=pix, threads=cores)
+        dt = time.perf_counter() - t0
+        total_pix += n
+        total_t += dt
+        if total_t >= seconds or total_pix >= 4_000_000:
+            break
+        n = int(min(max(n * 2, 2000), 400_000))
+    return {"value": total_pix / total_t / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d random pixels of one %dx%d eye of the same workload (each call also builds the "
+                      "per-view meshes it needs), %.1f s" % (total_pix, eye.width, eye.height, total_t)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    lf, heads, desc = make_workload(args.workload, max(args.poses, 1), 0)
+    import numpy as np
+
+    import oracle
+
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(11)
+    per_step = 4000 if args.workload == "rig" else 20000
+    times, pixels = [], 0
+    for s in range(args.warmup + args.steps):
+        head = heads[s % len(heads)]
+        t0 = time.perf_counter()
+        for eye in head:
+            pix = np.stack([rng.integers(0, eye.width, per_step // 2), rng.integers(0, eye.height, per_step // 2)],
+                           axis=1)
+            oracle.render(lf, eye, pixels=pix, threads=cores)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            pixels += per_step
+    total = sum(times)
+    value = pixels / total / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": desc, "sample": "%d random pixels per step over both eyes" % per_step},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": "%d random pixels per step, %d steps" % (per_step, len(times))},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_08860_gb300 as lfm
+
+    tw, th = (int(x) for x in args.tile.split("x"))
+    lf, heads, desc = make_workload(args.workload, max(args.poses, 1), rank)
+    r = lfm.Renderer(local, tile=(tw, th), timing=True)
+    r.load_views(lf, tex_format=args.tex)
+    r.build_meshes(lf)
+    stream = torch.cuda.current_stream()
+    outs = [torch.empty((e.height, e.width, 4), dtype=torch.float32, device="cuda") for e in heads[0]]
+    px_per_step = sum(e.width * e.height for e in heads[0])
+    out_bytes = px_per_step * 16
+    tex_bytes = {"f32": 16, "u8": 4, "bf16": 8, "fp8": 4}[args.tex]
+
+    # Algorithmic bytes: distinct texels each stereo frame reads, plus its output.
+    uniq = [r.unique_texels(h, lf.width, lf.height) for h in heads]
+    active = []
+    for h in heads:
+        r.render(h, out=outs)
+        active.append(sum(r.stats()["active_views"]))
+    mean_u = statistics.mean(uniq)
+    mesh_bytes = statistics.mean(active) / 2.0 * 2 * lf.grid_n ** 2 * 4  # per eye, both eyes
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+
+    def step(k, timed_pair=None):
+        head = heads[k % len(heads)]
+        flush.zero_()
+        if timed_pair:
+            timed_pair[0].record(stream)
+        r.render(head, out=outs, stream=stream)
+        if timed_pair:
+            timed_pair[1].record(stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    raster_ms, setup_v_ms, setup_t_ms = [], [], []
+    for k in range(args.steps):
+        step(args.warmup + k, ev[k])
+        st = r.stats()  # waits for the step; the kernel times come from events on the launch stream
+        raster_ms.append(st["ms_raster"])
+        setup_v_ms.append(st["ms_view_setup"])
+        setup_t_ms.append(st["ms_tri_setup"])
+        assert st["error_word"] == 0
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    value = world * px_per_step * args.steps / (total_ms / 1000.0) / 1e6
+
+    # End to end through the public call: host poses in, images read back to host.
+    host = [torch.empty(o.shape, dtype=torch.float32, pin_memory=True) for o in outs]
+    e2e_ms = []
+    for k in range(max(3, args.steps // 2)):
+        head = heads[k % len(heads)]
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r.render(head, out=outs, stream=stream)
+        for o, h in zip(outs, host):
+            h.copy_(o, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * px_per_step * len(e2e_ms) / (e2e_total / 1000.0) / 1e6
+
+    peak, peak_kind = measured_peak()
+    mean_raster = statistics.mean(raster_ms)
+    raster_bytes = mean_u * tex_bytes + out_bytes
+    achieved = raster_bytes / (mean_raster / 1000.0) / 1e9
+    step_bytes = raster_bytes + mesh_bytes
+    step_achieved = step_bytes / (total_ms / args.steps / 1000.0) / 1e9
+    traffic = ncu_traffic(args.workload, args.tex, args.tile)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "texture_storage": args.tex, "tile": args.tile,
+                   "head_poses": len(heads), "l2": "flushed (256 MiB write) between steps, outside the timed events",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "raster_kernel", "peak_source": peak_kind + " (HBM copy)",
+                     "algorithmic_bytes_per_launch": raster_bytes,
+                     "unique_texels_per_step": mean_u, "ms_per_launch": mean_raster},
+        "step_roofline": {"bytes_per_step": step_bytes, "achieved": step_achieved, "frac": step_achieved / peak,
+                          "unit": "GB/s"},
+        "phases_ms": {"view_setup": statistics.mean(setup_v_ms), "tri_setup": statistics.mean(setup_t_ms),
+                      "raster": mean_raster},
+        "active_views_per_step": statistics.mean(active),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 160 * len(heads[0]),
+                "d2h_bytes_per_step": out_bytes,
+                "what": "lf_render from host poses plus device-to-host copy of both eye images"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(lf, heads[0][0], args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    r.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,227 @@
+/*
+ * lf.h - C ABI of a GB300 (sm_103a) renderer for panoramic light fields
+ * stored as disk-blended source views with per-view geometry, after
+ * Overbeck et al., "A System for Acquiring, Processing, and Rendering
+ * Panoramic Light Field Stills for Virtual Reality", TOG 37(6), 2018.
+ *
+ * The library answers the ray queries of Eq. 1 for every pixel of one or
+ * more eye views with the disk-based reconstruction of Eq. 2:
+ *
+ *     L(o, e) = sum_i I_i(s_i, t_i) rho_i(u_i, v_i) / sum_i rho_i(u_i, v_i)
+ *
+ * where I_i is a bilinear sample of source view i at the point where the eye
+ * ray meets view i's own depth-displaced triangle mesh (Sec. 4.1, 4.5), and
+ * rho_i is the linear disk kernel of Sec. 4.1 evaluated at the ray's crossing
+ * p of the capture sphere: w_i = max(0, 1 - |p - c_i| / r_i), with disk
+ * centre c_i (by default view i's centre of projection) and radius r_i.
+ * Each mesh is depth tested against itself only (intra-image occlusion,
+ * Sec. 4.2.2); the sums are accumulated in FP32 and normalised (the two
+ * passes of Sec. 4.2).
+ *
+ * Conventions shared by every call:
+ *  - A pose is a camera->world rigid transform: R is a row-major 3x3 rotation
+ *    whose columns are the camera axes in world coordinates, t is the centre
+ *    of projection.  Camera x points right, y down, z forward.
+ *  - Intrinsics are pinhole (fx, fy, cx, cy) in pixel units.  Pixel (i, j)
+ *    covers [i, i+1) x [j, j+1); its centre is (i + 1/2, j + 1/2).
+ *  - Images are row-major, top row first, RGBA with 4 bytes (or 4 floats) per
+ *    pixel.  Source alpha is ignored.
+ *  - Every entry point returns an lf_status; none throws or aborts.  Calls
+ *    that take a stream are asynchronous on it; launch errors are returned at
+ *    once, and conditions found on the device (scratch overflow) are returned
+ *    by lf_get_stats, which waits for the last call.
+ *  - A context is not thread safe; use one context per host thread, and one
+ *    stream at a time per context (the library's scratch buffers are reused
+ *    in stream order).
+ *
+ * Ownership: the library copies host inputs before returning (the caller may
+ * free them).  Device output buffers belong to the caller.  The library owns
+ * its textures, meshes and scratch, which are freed by lf_destroy.
+ */
+#ifndef LF_H_
+#define LF_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LF_API __attribute__((visibility("default")))
+#else
+#define LF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lf_ctx lf_ctx;
+
+typedef enum {
+  LF_OK = 0,
+  LF_ERR_INVALID_ARG = 1,  /* a pointer, size or enum value is out of range */
+  LF_ERR_CUDA = 2,         /* a CUDA runtime call failed (see lf_last_error) */
+  LF_ERR_OOM = 3,          /* a device or pinned allocation failed */
+  LF_ERR_STATE = 4,        /* views or meshes not loaded, or loaded with other sizes */
+  LF_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  LF_ERR_UNSUPPORTED = 6,  /* a valid request this build does not implement */
+  LF_ERR_CAPACITY = 7      /* per-frame scratch too small; raise lf_config.tri_capacity */
+} lf_status;
+
+/* Storage of the source textures on the device (accumulation is always FP32). */
+typedef enum {
+  LF_TEX_F32 = 0,      /* 4 x float per texel, value k/255 (the plain form) */
+  LF_TEX_U8 = 1,       /* 4 x uint8 per texel */
+  LF_TEX_BF16 = 2,     /* 4 x bfloat16 per texel */
+  LF_TEX_FP8E4M3 = 3   /* 4 x FP8 E4M3 per texel times a per-view FP32 scale */
+} lf_tex_format;
+
+/* Storage of the per-view depth grids on the device. */
+typedef enum {
+  LF_MESH_F32_DEPTH = 0,   /* FP32 z-depth per vertex */
+  LF_MESH_F16_OFFSET = 1   /* FP16 (z - z0_i) per vertex plus an FP32 origin z0_i per view */
+} lf_mesh_format;
+
+typedef struct {
+  double R[9];   /* camera->world rotation, row-major */
+  double t[3];   /* centre of projection, world */
+} lf_pose;
+
+typedef struct {
+  double fx, fy, cx, cy;
+  int32_t width, height;
+} lf_intrinsics;
+
+/* Creation-time configuration.  Zeroed fields take the default in brackets. */
+typedef struct {
+  int32_t tile_w, tile_h;   /* screen tile in pixels: 16x16, 32x8 or 8x8 [16x16] */
+  int32_t max_eyes;         /* eyes per lf_render / lf_render_batch call [2] */
+  int32_t timing;           /* 1: bracket each kernel with CUDA events on the call's stream [0] */
+  int64_t tri_capacity;     /* set-up triangle records per call [8 Mi] */
+  float z_near;             /* eye-space near clip plane in metres [0.1] */
+  int32_t pad1;
+  int64_t wait_limit;       /* iteration bound on device spin waits [1<<24] */
+} lf_config;
+
+/* Counters of the last completed render call on the context. */
+typedef struct {
+  int32_t n_eyes;
+  int32_t n_views;
+  int32_t active_views[2];  /* views with a nonzero disk weight at some pixel, eyes 0 and 1 */
+  int64_t triangles;        /* set-up (sub-)triangle records written */
+  int64_t tiles;            /* screen tiles rasterised */
+  uint32_t error_word;      /* device error bits, 0 when clean */
+  float ms_view_setup;      /* kernel durations of the last call when lf_config.timing = 1, else 0 */
+  float ms_tri_setup;
+  float ms_raster;
+} lf_stats;
+
+/* One (pixel, view) record of the inspection call: a view whose disk holds
+ * the pixel's sphere crossing, its mesh coverage and its depth-test winner. */
+typedef struct {
+  int32_t view;
+  int32_t n_cover;    /* (sub-)triangles whose snapped edges cover the pixel centre */
+  int32_t winner;     /* parent triangle id of the depth-test winner, -1 if none */
+  int32_t min_id;     /* smallest covering parent id, -1 if none */
+  int32_t max_id;     /* largest covering parent id, -1 if none */
+  uint32_t id_hash;   /* xor over covering ids of the murmur3 32-bit finaliser of the id */
+} lf_frag_record;
+
+/* Defaults for lf_config (fills every field). */
+LF_API void lf_config_default(lf_config* cfg);
+
+/* Create a context on CUDA device `device`.  cfg may be NULL for defaults.
+ * Errors: LF_ERR_INVALID_ARG (bad device or config), LF_ERR_CUDA. */
+LF_API lf_status lf_create(int32_t device, const lf_config* cfg, lf_ctx** out);
+
+/* Free the context and all its device memory.  NULL-safe. */
+LF_API void lf_destroy(lf_ctx* ctx);
+
+/*
+ * Load the source views (the light field images of Sec. 4.1) and their disks.
+ *   n_views     number of views (1 .. 65536)
+ *   poses       n_views camera->world poses (host)
+ *   intr        n_views intrinsics (host); every view must have the same
+ *               width and height (else LF_ERR_UNSUPPORTED)
+ *   rgba8       n_views host pointers, each width*height*4 bytes
+ *   disk_c      n_views*3 floats, disk centres in world (host), or NULL for
+ *               the views' centres of projection (Sec. 4.1 places each disk
+ *               at its image's centre of projection)
+ *   disk_r      n_views floats, disk radii in metres (host), all > 0
+ *   sphere_c    centre of the capture sphere (3 doubles, world)
+ *   sphere_r    its radius in metres (> 0); p is the larger-root crossing of
+ *               each eye ray with this sphere
+ *   fmt         device storage of the textures
+ * Replaces any views loaded before (meshes must then be rebuilt).  Blocks
+ * until the upload is complete.  Errors: LF_ERR_INVALID_ARG, LF_ERR_OOM,
+ * LF_ERR_UNSUPPORTED, LF_ERR_CUDA.
+ */
+LF_API lf_status lf_load_views(lf_ctx* ctx, int32_t n_views, const lf_pose* poses, const lf_intrinsics* intr,
+                        const uint8_t* const* rgba8, const float* disk_c, const float* disk_r,
+                        const double sphere_c[3], double sphere_r, lf_tex_format fmt);
+
+/*
+ * Build each view's mesh (Sec. 4.5): a grid_n x grid_n grid of vertices (j, k)
+ * at source pixel-edge coordinates (j W/(grid_n-1), k H/(grid_n-1)), displaced
+ * along the view's pixel rays to the given z-depths, split into two triangles
+ * per cell, (j,k)(j+1,k)(j,k+1) and (j+1,k)(j+1,k+1)(j,k+1), with ids
+ * 2 (k (grid_n-1) + j) and that plus one.
+ *   grid_n   2 .. 1024
+ *   depth    host, n_views*grid_n*grid_n floats, row k then column j, z-depth
+ *            in the view's camera frame (> 0)
+ *   fmt      device storage of the depth grids
+ * Requires lf_load_views first (else LF_ERR_STATE).  Blocks until done.
+ */
+LF_API lf_status lf_build_view_meshes(lf_ctx* ctx, int32_t grid_n, const float* depth, lf_mesh_format fmt);
+
+/*
+ * Render n_eyes eye views (Eq. 1-2) into caller-owned device buffers.
+ *   n_eyes    1 .. lf_config.max_eyes (typically 2, a stereo pair)
+ *   eyes      n_eyes eye poses (host)
+ *   intr      n_eyes eye intrinsics (host); width, height 1 .. 32767
+ *   out_rgba  n_eyes device pointers (host array), each height*width*4 floats:
+ *             (sum w rgb / sum w, 1) where sum w > 0, else (0, 0, 0, 0)
+ *   stream    cudaStream_t to run on (NULL = legacy default stream)
+ * Asynchronous.  Errors: LF_ERR_INVALID_ARG, LF_ERR_STATE, LF_ERR_CAPACITY,
+ * LF_ERR_CUDA (including a device error left by an earlier call).
+ */
+LF_API lf_status lf_render(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                    float* const* out_rgba, void* stream);
+
+/*
+ * Render many eyes of mixed sizes in one launch sequence: a persistent
+ * raster kernel takes (eye, tile) work items from a device queue, and the
+ * whole sequence is replayed as a CUDA graph captured once per batch layout.
+ * Same arguments and output as lf_render; n_eyes up to lf_config.max_eyes.
+ * The graph is re-captured when the number or sizes of the eyes change.
+ */
+LF_API lf_status lf_render_batch(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                          float* const* out_rgba, void* stream);
+
+/*
+ * Inspection form of lf_render for one eye, for testing coverage and view
+ * selection: besides the image it writes, per pixel, up to max_records
+ * lf_frag_record entries in increasing view order (records[(j*W+i)*max_records
+ * + k]) and their count in counts[j*W+i] (which may exceed max_records; the
+ * excess is dropped), the per-view selection flags active[v] (1 if view v's
+ * disk holds some pixel's sphere crossing), and optionally a bitset over all
+ * views' texels (bit v*W*H + y*W + x) marking the texels read by winners'
+ * bilinear footprints (caller zeroes it; NULL to skip).  All buffers are
+ * device memory owned by the caller.
+ */
+LF_API lf_status lf_render_inspect(lf_ctx* ctx, const lf_pose* eye, const lf_intrinsics* intr, float* out_rgba,
+                            lf_frag_record* records, int32_t max_records, int32_t* counts,
+                            uint8_t* active, uint32_t* texel_bits, void* stream);
+
+/* Counters of the last render call; synchronises with its stream. */
+LF_API lf_status lf_get_stats(lf_ctx* ctx, lf_stats* out);
+
+/* Human-readable name of a status. */
+LF_API const char* lf_status_string(lf_status s);
+
+/* Message of the last error on the context ("" if none). */
+LF_API const char* lf_last_error(const lf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LF_H_ */

@@ -1,0 +1,277 @@
+"""Python binding of liblf.so, the GB300 disk-blended light field renderer.
+
+Argument marshalling only: every step of the rendering runs in the library's
+CUDA kernels, reached through the C ABI of include/lf.h.  PyTorch provides the
+device memory of the outputs and the CUDA streams.  There is no CPU fallback:
+if the compiled library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblf.so")
+
+LF_OK = 0
+STATUS = {0: "LF_OK", 1: "LF_ERR_INVALID_ARG", 2: "LF_ERR_CUDA", 3: "LF_ERR_OOM", 4: "LF_ERR_STATE",
+          5: "LF_ERR_TIMEOUT", 6: "LF_ERR_UNSUPPORTED", 7: "LF_ERR_CAPACITY"}
+TEX_FORMATS = {"f32": 0, "u8": 1, "bf16": 2, "fp8": 3}
+MESH_FORMATS = {"f32": 0, "f16": 1}
+
+
+class LFError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS.get(status, str(status)), message))
+        self.status = status
+
+
+class Pose(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
+
+
+class Intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
+                ("cy", ctypes.c_double), ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("max_eyes", ctypes.c_int32),
+                ("timing", ctypes.c_int32), ("tri_capacity", ctypes.c_int64), ("z_near", ctypes.c_float),
+                ("pad1", ctypes.c_int32), ("wait_limit", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_eyes", ctypes.c_int32), ("n_views", ctypes.c_int32), ("active_views", ctypes.c_int32 * 2),
+                ("triangles", ctypes.c_int64), ("tiles", ctypes.c_int64), ("error_word", ctypes.c_uint32),
+                ("ms_view_setup", ctypes.c_float), ("ms_tri_setup", ctypes.c_float), ("ms_raster", ctypes.c_float)]
+
+
+class FragRecord(ctypes.Structure):
+    _fields_ = [("view", ctypes.c_int32), ("n_cover", ctypes.c_int32), ("winner", ctypes.c_int32),
+                ("min_id", ctypes.c_int32), ("max_id", ctypes.c_int32), ("id_hash", ctypes.c_uint32)]
+
+
+FRAG_RECORD_DTYPE = np.dtype([("view", np.int32), ("n_cover", np.int32), ("winner", np.int32),
+                              ("min_id", np.int32), ("max_id", np.int32), ("id_hash", np.uint32)])
+
+# Every symbol include/lf.h declares.
+EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_build_view_meshes", "lf_render",
+           "lf_render_batch", "lf_render_inspect", "lf_get_stats", "lf_status_string", "lf_last_error"]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load liblf.so and declare its signatures.  Raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("liblf.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.lf_config_default.argtypes = [ctypes.POINTER(Config)]
+    lib.lf_config_default.restype = None
+    lib.lf_create.argtypes = [i32, ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    lib.lf_create.restype = ctypes.c_int
+    lib.lf_destroy.argtypes = [vp]
+    lib.lf_destroy.restype = None
+    lib.lf_load_views.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_int]
+    lib.lf_load_views.restype = ctypes.c_int
+    lib.lf_build_view_meshes.argtypes = [vp, i32, vp, ctypes.c_int]
+    lib.lf_build_view_meshes.restype = ctypes.c_int
+    for name in ("lf_render", "lf_render_batch"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, i32, vp, vp, vp, vp]
+        f.restype = ctypes.c_int
+    lib.lf_render_inspect.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
+    lib.lf_render_inspect.restype = ctypes.c_int
+    lib.lf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.lf_get_stats.restype = ctypes.c_int
+    lib.lf_status_string.argtypes = [ctypes.c_int]
+    lib.lf_status_string.restype = ctypes.c_char_p
+    lib.lf_last_error.argtypes = [vp]
+    lib.lf_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _poses(poses) -> ctypes.Array:
+    P = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(-1, 12))
+    arr = (Pose * P.shape[0])()
+    ctypes.memmove(arr, P.ctypes.data, P.nbytes)
+    return arr
+
+
+def _intrinsics(intr, sizes) -> ctypes.Array:
+    K = np.asarray(intr, dtype=np.float64).reshape(-1, 4)
+    arr = (Intrinsics * K.shape[0])()
+    for k in range(K.shape[0]):
+        arr[k].fx, arr[k].fy, arr[k].cx, arr[k].cy = (float(x) for x in K[k])
+        arr[k].width, arr[k].height = int(sizes[k][0]), int(sizes[k][1])
+    return arr
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Renderer:
+    """One library context on one GPU."""
+
+    def __init__(self, device: int = 0, tile=(16, 16), max_eyes: int = 2, tri_capacity: int = 0,
+                 z_near: float = 0.1, timing: bool = False):
+        self.lib = load_library()
+        cfg = Config()
+        self.lib.lf_config_default(ctypes.byref(cfg))
+        cfg.tile_w, cfg.tile_h = int(tile[0]), int(tile[1])
+        cfg.max_eyes = int(max_eyes)
+        if tri_capacity:
+            cfg.tri_capacity = int(tri_capacity)
+        cfg.z_near = float(z_near)
+        cfg.timing = 1 if timing else 0
+        self.device = device
+        self.ctx = ctypes.c_void_p()
+        self._check(self.lib.lf_create(device, ctypes.byref(cfg), ctypes.byref(self.ctx)), "lf_create")
+        self.n_views = 0
+
+    def close(self):
+        if self.ctx:
+            self.lib.lf_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, status: int, what: str):
+        if status != LF_OK:
+            msg = self.lib.lf_last_error(self.ctx).decode() if self.ctx else ""
+            raise LFError(status, "%s failed: %s" % (what, msg))
+
+    # ------------------------------------------------------------ loading
+
+    def load_views(self, lf, tex_format: str = "f32"):
+        """Upload source views, disks and the capture sphere (lf_load_views)."""
+        n = lf.poses.shape[0]
+        poses = _poses(lf.poses)
+        intr = _intrinsics(lf.intr, [(lf.width, lf.height)] * n)
+        images = np.ascontiguousarray(lf.images, dtype=np.uint8)
+        ptrs = (ctypes.c_void_p * n)(*[images.ctypes.data + k * images[0].nbytes for k in range(n)])
+        dc = np.ascontiguousarray(lf.disk_c, dtype=np.float32)
+        dr = np.ascontiguousarray(lf.disk_r, dtype=np.float32)
+        sc = (ctypes.c_double * 3)(*[float(x) for x in lf.sphere_c])
+        self._check(self.lib.lf_load_views(self.ctx, n, poses, intr, ptrs, dc.ctypes.data, dr.ctypes.data, sc,
+                                           float(lf.sphere_r), TEX_FORMATS[tex_format]), "lf_load_views")
+        self.n_views = n
+
+    def build_meshes(self, lf, mesh_format: str = "f32"):
+        """Upload the per-view depth grids (lf_build_view_meshes)."""
+        depth = np.ascontiguousarray(lf.depth, dtype=np.float32)
+        self._check(self.lib.lf_build_view_meshes(self.ctx, int(lf.grid_n), depth.ctypes.data,
+                                                  MESH_FORMATS[mesh_format]), "lf_build_view_meshes")
+
+    # ------------------------------------------------------------ rendering
+
+    @staticmethod
+    def _eye_arrays(eyes):
+        poses = _poses([e.pose for e in eyes])
+        intr = _intrinsics([e.intr for e in eyes], [(e.width, e.height) for e in eyes])
+        return poses, intr
+
+    def _outputs(self, eyes, out):
+        import torch
+        if out is None:
+            out = [torch.empty((e.height, e.width, 4), dtype=torch.float32, device="cuda:%d" % self.device)
+                   for e in eyes]
+        for e, o in zip(eyes, out):
+            if o.dtype != torch.float32 or not o.is_cuda or not o.is_contiguous() or tuple(o.shape) != (e.height, e.width, 4):
+                raise ValueError("each output must be a contiguous float32 CUDA tensor of shape (H, W, 4)")
+        ptrs = (ctypes.c_void_p * len(out))(*[o.data_ptr() for o in out])
+        return out, ptrs
+
+    def render(self, eyes, out=None, stream=None):
+        """Render eye views (lf_render); returns the output tensors (H, W, 4)."""
+        poses, intr = self._eye_arrays(eyes)
+        out, ptrs = self._outputs(eyes, out)
+        self._check(self.lib.lf_render(self.ctx, len(eyes), poses, intr, ptrs, _stream_handle(stream)), "lf_render")
+        return out
+
+    def render_host(self, eyes, stream=None):
+        """End-to-end call from host poses to host images: the render plus the
+        device->host copy of the result (what a client reading pixels back pays)."""
+        out = self.render(eyes, stream=stream)
+        return [o.cpu() for o in out]
+
+    def render_batch(self, eyes, out=None, stream=None):
+        """Render many eyes in one graph-replayed persistent launch (lf_render_batch)."""
+        poses, intr = self._eye_arrays(eyes)
+        out, ptrs = self._outputs(eyes, out)
+        self._check(self.lib.lf_render_batch(self.ctx, len(eyes), poses, intr, ptrs, _stream_handle(stream)),
+                    "lf_render_batch")
+        return out
+
+    def render_inspect(self, eye, max_records: int = 16, stream=None):
+        """Inspection render of one eye: image, per-pixel (pixel, view) coverage
+        records, view-selection flags and optionally the touched-texel bitset."""
+        import torch
+        dev = "cuda:%d" % self.device
+        poses, intr = self._eye_arrays([eye])
+        out = torch.empty((eye.height, eye.width, 4), dtype=torch.float32, device=dev)
+        n_pix = eye.width * eye.height
+        rec = torch.zeros((n_pix * max_records * 6,), dtype=torch.int32, device=dev)
+        counts = torch.zeros((n_pix,), dtype=torch.int32, device=dev)
+        active = torch.zeros((self.n_views,), dtype=torch.uint8, device=dev)
+        self._check(self.lib.lf_render_inspect(self.ctx, poses, intr, ctypes.c_void_p(out.data_ptr()),
+                                               ctypes.c_void_p(rec.data_ptr()), max_records,
+                                               ctypes.c_void_p(counts.data_ptr()), ctypes.c_void_p(active.data_ptr()),
+                                               None, _stream_handle(stream)), "lf_render_inspect")
+        torch.cuda.synchronize(self.device)
+        recs = rec.cpu().numpy().view(FRAG_RECORD_DTYPE).reshape(n_pix, max_records)
+        return {"rgba": out, "records": recs, "counts": counts.cpu().numpy(),
+                "active": active.cpu().numpy().astype(bool)}
+
+    def unique_texels(self, eyes, src_w: int, src_h: int, stream=None) -> int:
+        """Distinct source texels read by the winners' bilinear footprints over
+        all the given eyes (one shared bitset: texels both eyes read count once)."""
+        import torch
+        dev = "cuda:%d" % self.device
+        nbits = self.n_views * src_w * src_h
+        bits = torch.zeros(((nbits + 31) // 32,), dtype=torch.int32, device=dev)
+        for eye in eyes:
+            poses, intr = self._eye_arrays([eye])
+            out = torch.empty((eye.height, eye.width, 4), dtype=torch.float32, device=dev)
+            n_pix = eye.width * eye.height
+            rec = torch.zeros((n_pix * 6,), dtype=torch.int32, device=dev)
+            counts = torch.zeros((n_pix,), dtype=torch.int32, device=dev)
+            active = torch.zeros((self.n_views,), dtype=torch.uint8, device=dev)
+            self._check(self.lib.lf_render_inspect(self.ctx, poses, intr, ctypes.c_void_p(out.data_ptr()),
+                                                   ctypes.c_void_p(rec.data_ptr()), 1,
+                                                   ctypes.c_void_p(counts.data_ptr()),
+                                                   ctypes.c_void_p(active.data_ptr()),
+                                                   ctypes.c_void_p(bits.data_ptr()), _stream_handle(stream)),
+                        "lf_render_inspect")
+        torch.cuda.synchronize(self.device)
+        total = 0
+        for w in torch.split(bits, 1 << 24):
+            b = w.cpu().numpy().view(np.uint8)
+            total += int(np.unpackbits(b).sum())
+        return total
+
+    def stats(self) -> dict:
+        s = Stats()
+        st = self.lib.lf_get_stats(self.ctx, ctypes.byref(s))
+        d = {"n_eyes": s.n_eyes, "n_views": s.n_views, "active_views": [s.active_views[0], s.active_views[1]],
+             "triangles": s.triangles, "tiles": s.tiles, "error_word": s.error_word, "status": STATUS.get(st, st),
+             "ms_view_setup": s.ms_view_setup, "ms_tri_setup": s.ms_tri_setup, "ms_raster": s.ms_raster}
+        if st != LF_OK:
+            raise LFError(st, "lf_get_stats: " + self.lib.lf_last_error(self.ctx).decode())
+        return d

@@ -1,0 +1,549 @@
+// lf_api.cu - host side of the C ABI declared in include/lf.h: context,
+// uploads, per-call parameter staging, kernel sequencing, CUDA-graph replay of
+// batched calls, and statistics.  All arithmetic of the rendering method runs
+// in the kernels of lf_setup.cu and lf_raster.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lf_internal.h"
+
+using namespace lfk;
+
+namespace {
+
+constexpr int kRing = 4;
+
+struct Buffer {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct lf_ctx {
+  int device = 0;
+  lf_config cfg{};
+  std::string last_error;
+  int sm_count = 0;
+  // views
+  int32_t n_views = 0, src_w = 0, src_h = 0;
+  lf_tex_format tex_fmt = LF_TEX_F32;
+  double sphere_c[3] = {0, 0, 0};
+  double sphere_r = 0;
+  Buffer views, tex;
+  // meshes
+  int32_t G = 0;
+  lf_mesh_format mesh_fmt = LF_MESH_F32_DEPTH;
+  Buffer depth, tab_a, tab_b;
+  // per-call scratch
+  Buffer eyes, vrecs, masks, pool, small, active;
+  EyeParams* pinned = nullptr;  // kRing slots of max_eyes
+  cudaEvent_t ring_ev[kRing] = {};
+  int ring_next = 0;
+  cudaStream_t work_stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  // last call
+  cudaStream_t last_stream = nullptr;
+  int32_t last_eyes = 0;
+  int32_t last_tiles = 0;
+  bool has_call = false;
+  // batch graph
+  cudaGraphExec_t graph = nullptr;
+  std::vector<int64_t> graph_sig;
+  int persistent_blocks = 0;
+  // per-kernel timing of the last call (lf_config.timing)
+  cudaEvent_t tev[4] = {};
+  bool timed_call = false;
+};
+
+namespace {
+
+lf_status fail(lf_ctx* c, lf_status s, const char* what) {
+  if (c) c->last_error = what;
+  return s;
+}
+
+lf_status cuda_fail(lf_ctx* c, cudaError_t e, const char* what) {
+  if (c) {
+    c->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  }
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? LF_ERR_OOM : LF_ERR_CUDA;
+}
+
+#define LF_CUDA(ctx, call)                                        \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+  } while (0)
+
+void release(Buffer& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+cudaError_t ensure(Buffer& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return cudaSuccess;
+  release(b);
+  size_t want = std::max<size_t>(bytes, 256);
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e == cudaSuccess) b.bytes = want;
+  return e;
+}
+
+bool valid_tile(int w, int h) { return (w == 16 && h == 16) || (w == 32 && h == 8) || (w == 8 && h == 8); }
+
+struct Layout {
+  int32_t total_tiles = 0;
+  std::vector<EyeParams> eyes;
+};
+
+lf_status make_layout(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                      float* const* out, Layout& L) {
+  if (n_eyes < 1 || n_eyes > c->cfg.max_eyes) return fail(c, LF_ERR_INVALID_ARG, "n_eyes out of range");
+  if (!eyes || !intr || !out) return fail(c, LF_ERR_INVALID_ARG, "null argument");
+  L.eyes.resize(n_eyes);
+  int64_t base = 0;
+  for (int e = 0; e < n_eyes; ++e) {
+    const lf_intrinsics& K = intr[e];
+    if (K.width < 1 || K.height < 1 || K.width > 32767 || K.height > 32767)
+      return fail(c, LF_ERR_INVALID_ARG, "eye size out of range");
+    if (!(K.fx > 0) || !(K.fy > 0)) return fail(c, LF_ERR_INVALID_ARG, "focal length must be positive");
+    if (!out[e]) return fail(c, LF_ERR_INVALID_ARG, "null output pointer");
+    EyeParams& P = L.eyes[e];
+    std::memset(&P, 0, sizeof(P));
+    std::memcpy(P.R, eyes[e].R, sizeof(P.R));
+    std::memcpy(P.t, eyes[e].t, sizeof(P.t));
+    P.fx = K.fx; P.fy = K.fy; P.cx = K.cx; P.cy = K.cy;
+    P.W = K.width; P.H = K.height;
+    P.tiles_x = (K.width + c->cfg.tile_w - 1) / c->cfg.tile_w;
+    P.tiles_y = (K.height + c->cfg.tile_h - 1) / c->cfg.tile_h;
+    P.tile_base = (int32_t)base;
+    P.out = out[e];
+    base += (int64_t)P.tiles_x * P.tiles_y;
+    if (base > (int64_t)1 << 30) return fail(c, LF_ERR_INVALID_ARG, "too many tiles");
+  }
+  L.total_tiles = (int32_t)base;
+  return LF_OK;
+}
+
+int mask_words(const lf_ctx* c) { return (c->n_views + 31) / 32; }
+
+lf_status ensure_scratch(lf_ctx* c, int32_t n_eyes, int32_t total_tiles) {
+  LF_CUDA(c, ensure(c->eyes, sizeof(EyeParams) * (size_t)c->cfg.max_eyes));
+  LF_CUDA(c, ensure(c->vrecs, sizeof(ViewRec) * (size_t)n_eyes * c->n_views));
+  LF_CUDA(c, ensure(c->masks, sizeof(uint32_t) * (size_t)total_tiles * mask_words(c)));
+  LF_CUDA(c, ensure(c->active, (size_t)n_eyes * c->n_views));
+  LF_CUDA(c, ensure(c->small, 64));
+  int64_t cap = c->cfg.tri_capacity;
+  LF_CUDA(c, ensure(c->pool, sizeof(TriRec) * (size_t)cap));
+  return LF_OK;
+}
+
+// Copy the eye parameters through a pinned ring slot (the slot is reused only
+// after the copy that read it has completed).
+lf_status stage_eyes(lf_ctx* c, const Layout& L, cudaStream_t s) {
+  int slot = c->ring_next;
+  c->ring_next = (c->ring_next + 1) % kRing;
+  LF_CUDA(c, cudaEventSynchronize(c->ring_ev[slot]));
+  EyeParams* dst = c->pinned + (size_t)slot * c->cfg.max_eyes;
+  std::memcpy(dst, L.eyes.data(), sizeof(EyeParams) * L.eyes.size());
+  LF_CUDA(c, cudaMemcpyAsync(c->eyes.p, dst, sizeof(EyeParams) * L.eyes.size(), cudaMemcpyHostToDevice, s));
+  LF_CUDA(c, cudaEventRecord(c->ring_ev[slot], s));
+  return LF_OK;
+}
+
+FrameArgs frame_args(lf_ctx* c, const Layout& L) {
+  FrameArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.eyes = static_cast<const EyeParams*>(c->eyes.p);
+  a.n_eyes = (int32_t)L.eyes.size();
+  a.n_views = c->n_views;
+  a.src_w = c->src_w;
+  a.src_h = c->src_h;
+  a.G = c->G;
+  a.mask_words = mask_words(c);
+  a.tex_format = c->tex_fmt;
+  a.mesh_format = c->mesh_fmt;
+  a.z_near = c->cfg.z_near;
+  for (int k = 0; k < 3; ++k) a.sphere_c[k] = c->sphere_c[k];
+  a.sphere_r = c->sphere_r;
+  a.views = static_cast<const ViewStatic*>(c->views.p);
+  a.textures = c->tex.p;
+  a.depth = c->depth.p;
+  a.tables.a = static_cast<const float*>(c->tab_a.p);
+  a.tables.b = static_cast<const float*>(c->tab_b.p);
+  a.vrecs = static_cast<ViewRec*>(c->vrecs.p);
+  a.tile_masks = static_cast<uint32_t*>(c->masks.p);
+  a.pool = static_cast<TriRec*>(c->pool.p);
+  a.pool_capacity = c->cfg.tri_capacity;
+  unsigned char* sm = static_cast<unsigned char*>(c->small.p);
+  a.pool_counter = reinterpret_cast<unsigned long long*>(sm);
+  a.error_word = reinterpret_cast<uint32_t*>(sm + 8);
+  a.work_counter = reinterpret_cast<int32_t*>(sm + 12);
+  a.active = static_cast<uint8_t*>(c->active.p);
+  a.total_tiles = L.total_tiles;
+  a.tile_w = c->cfg.tile_w;
+  a.tile_h = c->cfg.tile_h;
+  return a;
+}
+
+// The per-call device work: clear, set up views, set up triangles, raster.
+lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persistent, cudaStream_t s) {
+  const bool t = c->cfg.timing != 0;
+  LF_CUDA(c, cudaMemsetAsync(a.tile_masks, 0, sizeof(uint32_t) * (size_t)a.total_tiles * a.mask_words, s));
+  // pool counter (8 B), error word (4 B) and work counter (4 B) start at zero each call
+  LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, 16, s));
+  LF_CUDA(c, cudaMemsetAsync(a.active, 0, (size_t)a.n_eyes * a.n_views, s));
+  if (t) LF_CUDA(c, cudaEventRecord(c->tev[0], s));
+  LF_CUDA(c, launch_view_setup(a, s));
+  if (t) LF_CUDA(c, cudaEventRecord(c->tev[1], s));
+  LF_CUDA(c, launch_tri_setup(a, s));
+  if (t) LF_CUDA(c, cudaEventRecord(c->tev[2], s));
+  LF_CUDA(c, launch_raster(a, inspect, persistent, c->persistent_blocks, s));
+  if (t) LF_CUDA(c, cudaEventRecord(c->tev[3], s));
+  c->timed_call = t;
+  return LF_OK;
+}
+
+lf_status check_ready(lf_ctx* c) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (c->n_views <= 0) return fail(c, LF_ERR_STATE, "views not loaded");
+  if (c->G <= 0) return fail(c, LF_ERR_STATE, "meshes not built");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lf_config_default(lf_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->tile_w = 16;
+  cfg->tile_h = 16;
+  cfg->max_eyes = 2;
+  cfg->tri_capacity = (int64_t)8 << 20;
+  cfg->z_near = 0.1f;
+  cfg->wait_limit = (int64_t)1 << 24;
+}
+
+const char* lf_status_string(lf_status s) {
+  switch (s) {
+    case LF_OK: return "LF_OK";
+    case LF_ERR_INVALID_ARG: return "LF_ERR_INVALID_ARG";
+    case LF_ERR_CUDA: return "LF_ERR_CUDA";
+    case LF_ERR_OOM: return "LF_ERR_OOM";
+    case LF_ERR_STATE: return "LF_ERR_STATE";
+    case LF_ERR_TIMEOUT: return "LF_ERR_TIMEOUT";
+    case LF_ERR_UNSUPPORTED: return "LF_ERR_UNSUPPORTED";
+    case LF_ERR_CAPACITY: return "LF_ERR_CAPACITY";
+  }
+  return "LF_ERR_UNKNOWN";
+}
+
+const char* lf_last_error(const lf_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+lf_status lf_create(int32_t device, const lf_config* cfg, lf_ctx** out) {
+  if (!out) return LF_ERR_INVALID_ARG;
+  *out = nullptr;
+  lf_config c;
+  lf_config_default(&c);
+  if (cfg) {
+    if (cfg->tile_w || cfg->tile_h) { c.tile_w = cfg->tile_w; c.tile_h = cfg->tile_h; }
+    if (cfg->max_eyes) c.max_eyes = cfg->max_eyes;
+    if (cfg->tri_capacity) c.tri_capacity = cfg->tri_capacity;
+    if (cfg->z_near != 0.0f) c.z_near = cfg->z_near;
+    if (cfg->wait_limit) c.wait_limit = cfg->wait_limit;
+    c.timing = cfg->timing ? 1 : 0;
+  }
+  if (!valid_tile(c.tile_w, c.tile_h) || c.max_eyes < 1 || c.max_eyes > 128 || c.tri_capacity < 1 ||
+      c.tri_capacity > ((int64_t)1 << 31) || !(c.z_near > 0.0f))
+    return LF_ERR_INVALID_ARG;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess) { cudaGetLastError(); return LF_ERR_CUDA; }
+  if (device < 0 || device >= n_dev) return LF_ERR_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); return LF_ERR_CUDA; }
+  lf_ctx* ctx = new (std::nothrow) lf_ctx();
+  if (!ctx) return LF_ERR_OOM;
+  ctx->device = device;
+  ctx->cfg = c;
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  bool ok = cudaMallocHost((void**)&ctx->pinned, sizeof(EyeParams) * (size_t)c.max_eyes * kRing) == cudaSuccess;
+  for (int k = 0; ok && k < kRing; ++k) ok = cudaEventCreateWithFlags(&ctx->ring_ev[k], cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < 4; ++k) ok = cudaEventCreate(&ctx->tev[k]) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&ctx->work_stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    lf_destroy(ctx);
+    return LF_ERR_CUDA;
+  }
+  *out = ctx;
+  return LF_OK;
+}
+
+void lf_destroy(lf_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->has_call && ctx->last_stream) cudaStreamSynchronize(ctx->last_stream);
+  cudaDeviceSynchronize();
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  for (Buffer* b : {&ctx->views, &ctx->tex, &ctx->depth, &ctx->tab_a, &ctx->tab_b, &ctx->eyes, &ctx->vrecs,
+                    &ctx->masks, &ctx->pool, &ctx->small, &ctx->active})
+    release(*b);
+  for (int k = 0; k < kRing; ++k)
+    if (ctx->ring_ev[k]) cudaEventDestroy(ctx->ring_ev[k]);
+  for (int k = 0; k < 4; ++k)
+    if (ctx->tev[k]) cudaEventDestroy(ctx->tev[k]);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->work_stream) cudaStreamDestroy(ctx->work_stream);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  cudaGetLastError();
+  delete ctx;
+}
+
+lf_status lf_load_views(lf_ctx* c, int32_t n_views, const lf_pose* poses, const lf_intrinsics* intr,
+                        const uint8_t* const* rgba8, const float* disk_c, const float* disk_r,
+                        const double sphere_c[3], double sphere_r, lf_tex_format fmt) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (n_views < 1 || n_views > 65536 || !poses || !intr || !rgba8 || !disk_r || !sphere_c)
+    return fail(c, LF_ERR_INVALID_ARG, "bad view arguments");
+  if (!(sphere_r > 0)) return fail(c, LF_ERR_INVALID_ARG, "sphere radius must be positive");
+  if (fmt < LF_TEX_F32 || fmt > LF_TEX_FP8E4M3) return fail(c, LF_ERR_INVALID_ARG, "bad texture format");
+  const int W = intr[0].width, H = intr[0].height;
+  if (W < 2 || H < 2 || W > 16384 || H > 16384) return fail(c, LF_ERR_INVALID_ARG, "bad source size");
+  std::vector<ViewStatic> vs(n_views);
+  for (int v = 0; v < n_views; ++v) {
+    if (intr[v].width != W || intr[v].height != H)
+      return fail(c, LF_ERR_UNSUPPORTED, "all views must share one image size");
+    if (!(intr[v].fx > 0) || !(intr[v].fy > 0)) return fail(c, LF_ERR_INVALID_ARG, "bad view focal length");
+    if (!rgba8[v]) return fail(c, LF_ERR_INVALID_ARG, "null image pointer");
+    if (!(disk_r[v] > 0.0f)) return fail(c, LF_ERR_INVALID_ARG, "disk radius must be positive");
+    ViewStatic& V = vs[v];
+    std::memset(&V, 0, sizeof(V));
+    std::memcpy(V.R, poses[v].R, sizeof(V.R));
+    std::memcpy(V.t, poses[v].t, sizeof(V.t));
+    V.fx = intr[v].fx; V.fy = intr[v].fy; V.cx = intr[v].cx; V.cy = intr[v].cy;
+    for (int k = 0; k < 3; ++k) V.disk_c[k] = disk_c ? disk_c[v * 3 + k] : (float)poses[v].t[k];
+    V.disk_r = disk_r[v];
+    V.tex_scale = 1.0f;
+  }
+  LF_CUDA(c, cudaSetDevice(c->device));
+  if (c->has_call && c->last_stream) LF_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_sig.clear(); }
+  c->n_views = 0;
+  c->G = 0;
+  release(c->depth); release(c->tab_a); release(c->tab_b);
+  cudaStream_t s = c->work_stream;
+  LF_CUDA(c, ensure(c->views, sizeof(ViewStatic) * (size_t)n_views));
+  LF_CUDA(c, cudaMemcpyAsync(c->views.p, vs.data(), sizeof(ViewStatic) * (size_t)n_views, cudaMemcpyHostToDevice, s));
+  const int64_t per_view = (int64_t)W * H;
+  const size_t texel_bytes = fmt == LF_TEX_F32 ? 16 : fmt == LF_TEX_BF16 ? 8 : 4;
+  release(c->tex);
+  LF_CUDA(c, ensure(c->tex, texel_bytes * (size_t)per_view * n_views));
+  // FP8 stores each view's texels divided by a per-view scale (max value / 448).
+  Buffer scale;
+  if (fmt == LF_TEX_FP8E4M3) {
+    LF_CUDA(c, ensure(scale, sizeof(float) * (size_t)n_views));
+  }
+  // Upload in chunks through a device staging buffer of RGBA8.
+  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(n_views, ((int64_t)256 << 20) / (per_view * 4)));
+  Buffer stage;
+  if (fmt != LF_TEX_U8) LF_CUDA(c, ensure(stage, (size_t)chunk * per_view * 4));
+  for (int v0 = 0; v0 < n_views; v0 += chunk) {
+    int nv = std::min(chunk, n_views - v0);
+    uint8_t* dst = fmt == LF_TEX_U8 ? static_cast<uint8_t*>(c->tex.p) + (size_t)v0 * per_view * 4
+                                    : static_cast<uint8_t*>(stage.p);
+    for (int k = 0; k < nv; ++k)
+      LF_CUDA(c, cudaMemcpyAsync(dst + (size_t)k * per_view * 4, rgba8[v0 + k], (size_t)per_view * 4,
+                                 cudaMemcpyHostToDevice, s));
+    if (fmt != LF_TEX_U8) {
+      void* tdst = static_cast<char*>(c->tex.p) + (size_t)v0 * per_view * texel_bytes;
+      if (fmt == LF_TEX_FP8E4M3) {
+        LF_CUDA(c, launch_view_scale(static_cast<const uint8_t*>(stage.p), nv, per_view,
+                                     static_cast<float*>(scale.p) + v0, static_cast<ViewStatic*>(c->views.p) + v0, s));
+      }
+      LF_CUDA(c, launch_convert_textures(static_cast<const uint8_t*>(stage.p), tdst, (int64_t)nv * per_view, fmt,
+                                         fmt == LF_TEX_FP8E4M3 ? static_cast<float*>(scale.p) + v0 : nullptr,
+                                         per_view, s));
+    }
+    // the staging buffer is reused by the next chunk: wait for this one
+    LF_CUDA(c, cudaStreamSynchronize(s));
+  }
+  release(stage);
+  release(scale);
+  c->n_views = n_views;
+  c->src_w = W;
+  c->src_h = H;
+  c->tex_fmt = fmt;
+  for (int k = 0; k < 3; ++k) c->sphere_c[k] = sphere_c[k];
+  c->sphere_r = sphere_r;
+  return LF_OK;
+}
+
+lf_status lf_build_view_meshes(lf_ctx* c, int32_t grid_n, const float* depth, lf_mesh_format fmt) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (c->n_views <= 0) return fail(c, LF_ERR_STATE, "views not loaded");
+  if (grid_n < 2 || grid_n > 1024 || !depth) return fail(c, LF_ERR_INVALID_ARG, "bad mesh arguments");
+  if (fmt != LF_MESH_F32_DEPTH && fmt != LF_MESH_F16_OFFSET) return fail(c, LF_ERR_INVALID_ARG, "bad mesh format");
+  LF_CUDA(c, cudaSetDevice(c->device));
+  if (c->has_call && c->last_stream) LF_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_sig.clear(); }
+  c->G = 0;
+  cudaStream_t s = c->work_stream;
+  const size_t n = (size_t)c->n_views * grid_n * grid_n;
+  LF_CUDA(c, ensure(c->tab_a, sizeof(float) * (size_t)c->n_views * grid_n));
+  LF_CUDA(c, ensure(c->tab_b, sizeof(float) * (size_t)c->n_views * grid_n));
+  release(c->depth);
+  if (fmt == LF_MESH_F32_DEPTH) {
+    LF_CUDA(c, ensure(c->depth, sizeof(float) * n));
+    LF_CUDA(c, cudaMemcpyAsync(c->depth.p, depth, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  } else {
+    Buffer stage;
+    LF_CUDA(c, ensure(stage, sizeof(float) * n));
+    LF_CUDA(c, ensure(c->depth, 2 * n));
+    LF_CUDA(c, cudaMemcpyAsync(stage.p, depth, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    LF_CUDA(c, launch_depth_offsets(static_cast<const float*>(stage.p), c->n_views, grid_n * grid_n, c->depth.p,
+                                    static_cast<ViewStatic*>(c->views.p), s));
+    LF_CUDA(c, cudaStreamSynchronize(s));
+    release(stage);
+  }
+  LF_CUDA(c, launch_grid_tables(static_cast<const ViewStatic*>(c->views.p), c->n_views, c->src_w, c->src_h, grid_n,
+                                static_cast<float*>(c->tab_a.p), static_cast<float*>(c->tab_b.p), s));
+  LF_CUDA(c, cudaStreamSynchronize(s));
+  c->G = grid_n;
+  c->mesh_fmt = fmt;
+  return LF_OK;
+}
+
+lf_status lf_render(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                    float* const* out_rgba, void* stream) {
+  lf_status st = check_ready(c);
+  if (st != LF_OK) return st;
+  Layout L;
+  if ((st = make_layout(c, n_eyes, eyes, intr, out_rgba, L)) != LF_OK) return st;
+  if ((st = ensure_scratch(c, n_eyes, L.total_tiles)) != LF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = stage_eyes(c, L, s)) != LF_OK) return st;
+  FrameArgs a = frame_args(c, L);
+  if ((st = enqueue_frame(c, a, false, false, s)) != LF_OK) return st;
+  c->last_stream = s;
+  c->last_eyes = n_eyes;
+  c->last_tiles = L.total_tiles;
+  c->has_call = true;
+  return LF_OK;
+}
+
+lf_status lf_render_inspect(lf_ctx* c, const lf_pose* eye, const lf_intrinsics* intr, float* out_rgba,
+                            lf_frag_record* records, int32_t max_records, int32_t* counts, uint8_t* active,
+                            uint32_t* texel_bits, void* stream) {
+  lf_status st = check_ready(c);
+  if (st != LF_OK) return st;
+  if (!records || !counts || !active || max_records < 1) return fail(c, LF_ERR_INVALID_ARG, "bad inspect buffers");
+  Layout L;
+  float* outs[1] = {out_rgba};
+  if ((st = make_layout(c, 1, eye, intr, outs, L)) != LF_OK) return st;
+  if ((st = ensure_scratch(c, 1, L.total_tiles)) != LF_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = stage_eyes(c, L, s)) != LF_OK) return st;
+  FrameArgs a = frame_args(c, L);
+  a.active = active;
+  a.records = records;
+  a.max_records = max_records;
+  a.counts = counts;
+  a.texel_bits = texel_bits;
+  if ((st = enqueue_frame(c, a, true, false, s)) != LF_OK) return st;
+  c->last_stream = s;
+  c->last_eyes = 1;
+  c->last_tiles = L.total_tiles;
+  c->has_call = true;
+  return LF_OK;
+}
+
+lf_status lf_render_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                          float* const* out_rgba, void* stream) {
+  lf_status st = check_ready(c);
+  if (st != LF_OK) return st;
+  Layout L;
+  if ((st = make_layout(c, n_eyes, eyes, intr, out_rgba, L)) != LF_OK) return st;
+  if ((st = ensure_scratch(c, n_eyes, L.total_tiles)) != LF_OK) return st;
+  if (c->persistent_blocks <= 0) {
+    int per_sm = 0;
+    LF_CUDA(c, raster_occupancy(c->cfg.tile_w, c->cfg.tile_h, c->tex_fmt, &per_sm));
+    c->persistent_blocks = std::max(1, per_sm) * c->sm_count;
+  }
+  // The graph depends on the layout and on every scratch address it names.
+  std::vector<int64_t> sig = {n_eyes, L.total_tiles, c->n_views, c->G, c->tex_fmt, c->mesh_fmt,
+                              (int64_t)(intptr_t)c->eyes.p, (int64_t)(intptr_t)c->vrecs.p,
+                              (int64_t)(intptr_t)c->masks.p, (int64_t)(intptr_t)c->pool.p,
+                              (int64_t)(intptr_t)c->active.p, (int64_t)(intptr_t)c->small.p,
+                              (int64_t)(intptr_t)c->tex.p, (int64_t)(intptr_t)c->depth.p, c->persistent_blocks};
+  for (int e = 0; e < n_eyes; ++e) { sig.push_back(intr[e].width); sig.push_back(intr[e].height); }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!c->graph || sig != c->graph_sig) {
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    FrameArgs a = frame_args(c, L);
+    cudaGraph_t g = nullptr;
+    LF_CUDA(c, cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    lf_status q = enqueue_frame(c, a, false, true, c->capture_stream);
+    cudaError_t ec = cudaStreamEndCapture(c->capture_stream, &g);
+    if (q != LF_OK) { if (g) cudaGraphDestroy(g); return q; }
+    if (ec != cudaSuccess) return cuda_fail(c, ec, "cudaStreamEndCapture");
+    cudaError_t ei = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) { c->graph = nullptr; return cuda_fail(c, ei, "cudaGraphInstantiate"); }
+    c->graph_sig = sig;
+  }
+  if ((st = stage_eyes(c, L, s)) != LF_OK) return st;
+  LF_CUDA(c, cudaGraphLaunch(c->graph, s));
+  c->last_stream = s;
+  c->last_eyes = n_eyes;
+  c->last_tiles = L.total_tiles;
+  c->has_call = true;
+  return LF_OK;
+}
+
+lf_status lf_get_stats(lf_ctx* c, lf_stats* out) {
+  if (!c || !out) return LF_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->n_views = c->n_views;
+  if (!c->has_call) return LF_OK;
+  LF_CUDA(c, cudaSetDevice(c->device));
+  LF_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  unsigned char sm[16];
+  LF_CUDA(c, cudaMemcpy(sm, c->small.p, 16, cudaMemcpyDeviceToHost));
+  unsigned long long tris;
+  std::memcpy(&tris, sm, 8);
+  std::memcpy(&out->error_word, sm + 8, 4);
+  out->n_eyes = c->last_eyes;
+  out->triangles = (int64_t)tris;
+  if (c->timed_call) {
+    LF_CUDA(c, cudaEventElapsedTime(&out->ms_view_setup, c->tev[0], c->tev[1]));
+    LF_CUDA(c, cudaEventElapsedTime(&out->ms_tri_setup, c->tev[1], c->tev[2]));
+    LF_CUDA(c, cudaEventElapsedTime(&out->ms_raster, c->tev[2], c->tev[3]));
+  }
+  out->tiles = c->last_tiles;
+  std::vector<uint8_t> act((size_t)std::min(c->last_eyes, 2) * c->n_views);
+  if (!act.empty()) {
+    LF_CUDA(c, cudaMemcpy(act.data(), c->active.p, act.size(), cudaMemcpyDeviceToHost));
+    for (int e = 0; e < std::min(c->last_eyes, 2); ++e) {
+      int n = 0;
+      for (int v = 0; v < c->n_views; ++v) n += act[(size_t)e * c->n_views + v];
+      out->active_views[e] = n;
+    }
+  }
+  if (out->error_word & kErrPoolOverflow) return fail(c, LF_ERR_CAPACITY, "triangle pool overflow");
+  return LF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// lf_internal.h - device data layout shared by the library's kernels and host code.
+//
+// HBM layout (all resident for the context's lifetime):
+//   ViewStatic[n_views]           pose, intrinsics, disk, storage scales
+//   textures                      n_views x H x W texels, row-major, one of
+//                                 float4 / uchar4 / 4 x bf16 / 4 x e4m3
+//   depth grids                   n_views x G x G (float, or half + per-view origin)
+//   grid ray tables a_j, b_k      n_views x G floats each
+// Per call (scratch, reused in stream order):
+//   EyeParams[n_eyes]             eye pose, intrinsics, tile range, output pointer
+//   ViewRec[n_eyes x n_views]     composed transforms, footprint, triangle segment
+//   tile masks                    per eye tile, one bit per view whose disk footprint
+//                                 overlaps the tile (ceil(n_views/32) words)
+//   TriRec pool                   set-up (sub-)triangles, one contiguous segment per
+//                                 (eye, view) in triangle-id order
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/lf.h"
+
+namespace lfk {
+
+constexpr int kMaxTileThreads = 256;
+constexpr int kSnapLimit = 1 << 29;     // |snapped| must stay below 2^29 subpixels
+constexpr int kBigEdge = 1 << 22;       // edge deltas from 2^22 subpixels use the int64 path
+constexpr int kQClamp = 1 << 28;        // clamp of the per-tile edge offset in the int32 path
+
+// device error bits
+constexpr uint32_t kErrPoolOverflow = 1u << 0;
+constexpr uint32_t kErrRecordOverflow = 1u << 1;
+
+struct ViewStatic {
+  double R[9];
+  double t[3];
+  double fx, fy, cx, cy;
+  float disk_c[3];
+  float disk_r;
+  float depth_origin;   // z0 for the FP16-offset mesh format
+  float tex_scale;      // decode scale for FP8 textures
+  int32_t pad[2];
+};
+
+struct EyeParams {
+  double R[9];
+  double t[3];
+  double fx, fy, cx, cy;
+  int32_t W, H;
+  int32_t tiles_x, tiles_y;
+  int32_t tile_base;    // first tile index of this eye in the call's flattened tile range
+  int32_t pad;
+  float* out;           // H x W float4
+};
+
+struct __align__(16) ViewRec {
+  float Hm[12];         // eye pixel (x, y, 1) and 1/z -> source (u, v) homogeneous; Hm 3x3 then hv
+  float cc[4];          // disk centre relative to the capture sphere centre, then r^2
+  float inv_r;
+  int32_t seg_base;
+  int32_t seg_count;
+  int32_t pad0;
+  int32_t bb[4];        // conservative footprint in pixels, inclusive; bb[0] > bb[2] when empty
+  float Mf[12];         // camera -> eye rotation (3x3) then translation, FP32
+};
+
+struct __align__(16) TriRec {
+  int16_t bx0, by0, bx1, by1;   // pixel-centre bounding box clipped to screen and footprint
+  int32_t x[3], y[3];           // snapped vertices (1/256 px), positively oriented
+  float ia, ib, ic;             // 1/z = ia ex + ib ey + ic
+  int32_t id_tl;                // parent id << 3 | top-left flags of edges 0..2
+};
+static_assert(sizeof(TriRec) == 48, "TriRec layout");
+
+struct GridTables {
+  const float* a;   // n_views x G
+  const float* b;   // n_views x G
+};
+
+struct FrameArgs {
+  const EyeParams* eyes;
+  int32_t n_eyes;
+  int32_t n_views;
+  int32_t src_w, src_h;
+  int32_t G;
+  int32_t mask_words;
+  int32_t tex_format;
+  int32_t mesh_format;
+  float z_near;
+  double sphere_c[3];
+  double sphere_r;
+  const ViewStatic* views;
+  const void* textures;
+  const void* depth;
+  GridTables tables;
+  ViewRec* vrecs;
+  uint32_t* tile_masks;
+  TriRec* pool;
+  int64_t pool_capacity;
+  unsigned long long* pool_counter;
+  uint32_t* error_word;
+  uint8_t* active;         // n_eyes x n_views view-selection flags
+  int32_t total_tiles;
+  int32_t tile_w, tile_h;
+  // inspection outputs (one eye)
+  lf_frag_record* records;
+  int32_t max_records;
+  int32_t* counts;
+  uint32_t* texel_bits;
+  // persistent batch raster
+  int32_t* work_counter;
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_grid_tables(const ViewStatic* views, int n_views, int src_w, int src_h, int G,
+                               float* a, float* b, cudaStream_t s);
+cudaError_t launch_convert_textures(const uint8_t* src, void* dst, int64_t n_texels, int fmt,
+                                    const float* scale_per_texel_view, int64_t texels_per_view,
+                                    cudaStream_t s);
+cudaError_t launch_view_setup(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_raster(const FrameArgs& a, bool inspect, bool persistent, int persistent_blocks,
+                          cudaStream_t s);
+cudaError_t raster_occupancy(int tile_w, int tile_h, int tex_format, int* blocks_per_sm);
+// FP8 textures: per-view scale = max(RGB) / 255 / 448, also stored in views[v].tex_scale.
+cudaError_t launch_view_scale(const uint8_t* rgba8, int n_views, int64_t texels_per_view, float* scale,
+                              ViewStatic* views, cudaStream_t s);
+// FP16-offset meshes: per-view origin z0 = min depth (views[v].depth_origin), half(z - z0) per vertex.
+cudaError_t launch_depth_offsets(const float* depth, int n_views, int per_view, void* dst_half, ViewStatic* views,
+                                 cudaStream_t s);
+
+}  // namespace lfk

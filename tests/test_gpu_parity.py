@@ -1,0 +1,276 @@
+"""Parity of the CUDA renderer (through the C ABI) with the CPU oracle.
+
+Coverage and view selection must match bit for bit: every (pixel, view) pair
+whose disk holds the pixel's sphere crossing, with its covering-triangle
+count, id range, id hash and depth-test winner.  Colour must match within
+2e-3 max-abs per channel on every pixel both sides call valid, and the valid
+masks must be identical.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scene
+from tests import lfcase
+
+pytestmark = pytest.mark.gpu
+
+COLOUR_TOL = 2e-3
+
+
+@pytest.fixture(scope="module")
+def lfmod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_08860_gb300 as lf
+
+    return lf
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return scene.tiny_light_field(1)
+
+
+@pytest.fixture(scope="module")
+def tiny_renderer(lfmod, tiny):
+    r = lfmod.Renderer(0)
+    r.load_views(tiny)
+    r.build_meshes(tiny)
+    yield r
+    r.close()
+
+
+def _ref_records(ref, W, pixels=None):
+    """Oracle records grouped by flat pixel index j*W+i, sorted by view."""
+    out = {}
+    for f in ref["frags"]:
+        k = int(f["pixel"])
+        if pixels is not None:
+            i, j = pixels[k]
+            k = int(j) * W + int(i)
+        out.setdefault(k, []).append((int(f["view"]), int(f["n_cover"]), int(f["winner"]), int(f["min_id"]),
+                                      int(f["max_id"]), int(f["id_hash"])))
+    return out
+
+
+def _gpu_records(got, flat_pixels):
+    out = {}
+    recs, counts = got["records"], got["counts"]
+    for k in flat_pixels:
+        n = int(counts[k])
+        assert n <= recs.shape[1], "record overflow at pixel %d" % k
+        if n:
+            out[int(k)] = [(int(r["view"]), int(r["n_cover"]), int(r["winner"]), int(r["min_id"]),
+                            int(r["max_id"]), int(r["id_hash"])) for r in recs[k][:n]]
+    return out
+
+
+def _check_full_frame(r, lf, eye, max_records=16):
+    got = r.render_inspect(eye, max_records=max_records)
+    ref = oracle.render(lf, eye, fragments=True, max_slots=max_records)
+    assert ref["stats"]["frag_overflow"] == 0
+    W, H = eye.width, eye.height
+    g = _gpu_records(got, range(W * H))
+    o = _ref_records(ref, W)
+    assert g.keys() == o.keys()
+    bad = [k for k in o if g[k] != o[k]]
+    assert not bad, "coverage differs at %d pixels, first %s: gpu %s oracle %s" % (
+        len(bad), bad[0], g[bad[0]], o[bad[0]])
+    img = got["rgba"].cpu().numpy().astype(np.float64)
+    want = ref["rgba"]
+    valid = want[..., 3] > 0
+    assert np.array_equal(img[..., 3] > 0, valid)
+    assert np.all(img[~valid] == 0.0)
+    if valid.any():
+        err = np.max(np.abs(img[valid][:, :3] - want[valid][:, :3]))
+        assert err <= COLOUR_TOL, err
+    sel = oracle.select_views(lf, eye)
+    assert np.array_equal(got["active"], sel)
+    return got, ref
+
+
+# ---------------------------------------------------------------- tiny configuration (256 x 256 eye, 16 views)
+
+
+def test_tiny_full_frame(tiny_renderer, tiny):
+    got, ref = _check_full_frame(tiny_renderer, tiny, tiny.eyes[0])
+    assert ref["stats"]["frag_win"] > 10000
+    assert got["active"].sum() >= 4
+
+
+def test_ragged_offcentre_eye(tiny_renderer, tiny):
+    """Eye sizes that are not multiples of the tile, off-centre principal point."""
+    for (w, h, fx, fy, cx, cy) in [(75, 53, 50.0, 47.0, 31.3, 29.9), (17, 131, 30.0, 60.0, 9.0, 70.0)]:
+        eye = scene.Eye(tiny.eyes[0].pose, np.array([fx, fy, cx, cy]), w, h)
+        _check_full_frame(tiny_renderer, tiny, eye)
+
+
+def test_more_tiny_poses(lfmod):
+    for seed in (2, 3):
+        lf = scene.tiny_light_field(seed)
+        r = lfmod.Renderer(0)
+        r.load_views(lf)
+        r.build_meshes(lf)
+        _check_full_frame(r, lf, lf.eyes[0])
+        r.close()
+
+
+def test_one_pixel_and_empty_eyes(tiny_renderer, tiny):
+    one = scene.Eye(tiny.eyes[0].pose, np.array([1.0, 1.0, 0.5, 0.5]), 1, 1)
+    _check_full_frame(tiny_renderer, tiny, one)
+    # looking away from the cap: no disk holds any crossing, the image is empty
+    R = scene.look_rotation([0.0, 0.0, -1.0])
+    away = scene.Eye(scene.pose_array(R, (0.0, 0.0, 0.0)), np.array([32.0, 32.0, 32.0, 32.0]), 64, 64)
+    got, _ = _check_full_frame(tiny_renderer, tiny, away)
+    assert got["active"].sum() == 0
+    assert float(got["rgba"].abs().max()) == 0.0
+
+
+def test_tile_shapes_identical(lfmod, tiny, tiny_renderer):
+    eye = tiny.eyes[0]
+    base = tiny_renderer.render([eye])[0].cpu()
+    for tile in [(32, 8), (8, 8)]:
+        r = lfmod.Renderer(0, tile=tile)
+        r.load_views(tiny)
+        r.build_meshes(tiny)
+        out = r.render([eye])[0].cpu()
+        assert (out == base).all(), tile
+        r.close()
+
+
+def test_render_matches_inspect_and_batch(lfmod, tiny):
+    eyes = [tiny.eyes[0], scene.Eye(tiny.eyes[0].pose, np.array([60.0, 60.0, 50.0, 40.0]), 100, 90)]
+    r = lfmod.Renderer(0, max_eyes=4)
+    r.load_views(tiny)
+    r.build_meshes(tiny)
+    a = [o.cpu() for o in r.render(eyes)]
+    for e, img in zip(eyes, a):
+        assert (r.render_inspect(e)["rgba"].cpu() == img).all()
+    for _ in range(2):  # capture, then replay
+        b = [o.cpu() for o in r.render_batch(eyes)]
+        for x, y in zip(a, b):
+            assert (x == y).all()
+    st = r.stats()
+    assert st["error_word"] == 0 and st["n_eyes"] == 2
+    r.close()
+
+
+# ---------------------------------------------------------------- hand-built geometry
+
+
+def _identity_pose(t=(0.0, 0.0, 0.0), R=None):
+    return scene.pose_array(np.eye(3) if R is None else R, t)
+
+
+def test_fold_over_and_clipping(lfmod):
+    rng = np.random.default_rng(3)
+    G, n = 17, 64
+    depth = np.full((1, G, G), 4.0, dtype=np.float32)
+    depth[0, 6:11, 6:11] = 1.5
+    img = rng.integers(0, 256, size=(1, n, n, 4), dtype=np.uint8)
+    intr = scene.intrinsics_for_fov(n, n, 90.0)
+    lf = lfcase.custom_lf([_identity_pose()], [intr], img, depth, disk_c=[[0.0, 0.0, 0.0]], disk_r=[10.0],
+                          sphere_r=2.0)
+    r = lfmod.Renderer(0)
+    r.load_views(lf)
+    r.build_meshes(lf)
+    for off in [(0.5, 0.15, 0.0), (-0.4, 0.45, 0.3)]:
+        eye = scene.Eye(_identity_pose(off), np.array([40.0, 40.0, 32.0, 32.0]), 64, 64)
+        got, ref = _check_full_frame(r, lf, eye)
+        assert (got["records"]["n_cover"] >= 2).sum() > 20
+    r.close()
+    # a plane that passes beside and behind the eye is clipped at z_near
+    depth = np.full((1, 10, 10), 2.0, dtype=np.float32)
+    img = rng.integers(0, 256, size=(1, 48, 48, 4), dtype=np.uint8)
+    lf = lfcase.custom_lf([_identity_pose((0.0, 0.0, -1.0))], [scene.intrinsics_for_fov(48, 48, 90.0)], img, depth,
+                          disk_c=[[0.0, 0.0, 0.0]], disk_r=[10.0], sphere_r=0.5)
+    r = lfmod.Renderer(0)
+    r.load_views(lf)
+    r.build_meshes(lf)
+    eye = scene.Eye(_identity_pose((0.0, 0.0, 0.0), scene.look_rotation([1.0, 0.0, 0.2])),
+                    np.array([24.0, 24.0, 24.0, 24.0]), 48, 48)
+    _check_full_frame(r, lf, eye)
+    r.close()
+
+
+# ---------------------------------------------------------------- storage formats
+
+
+def test_reduced_precision_textures(lfmod, tiny):
+    eye = tiny.eyes[0]
+    ref = oracle.render(tiny, eye)["rgba"]
+    valid = ref[..., 3] > 0
+    errs = {}
+    for fmt, tol in [("u8", COLOUR_TOL), ("bf16", 8e-3), ("fp8", 0.08)]:
+        r = lfmod.Renderer(0)
+        r.load_views(tiny, tex_format=fmt)
+        r.build_meshes(tiny)
+        img = r.render([eye])[0].cpu().numpy().astype(np.float64)
+        assert np.array_equal(img[..., 3] > 0, valid)
+        errs[fmt] = float(np.max(np.abs(img[valid][:, :3] - ref[valid][:, :3])))
+        assert errs[fmt] <= tol, (fmt, errs[fmt])
+        r.close()
+
+
+def test_f16_offset_meshes_match_oracle_on_the_stored_depths(lfmod, tiny):
+    """The FP16-offset mesh is exact against the oracle run on the depths it stores."""
+    d = tiny.depth.astype(np.float32)
+    z0 = d.reshape(d.shape[0], -1).min(axis=1).astype(np.float32)
+    stored = (z0[:, None, None] + (d - z0[:, None, None]).astype(np.float16).astype(np.float32)).astype(np.float32)
+    lfq = lfcase.custom_lf(tiny.poses, tiny.intr, tiny.images, stored, disk_c=tiny.disk_c, disk_r=tiny.disk_r)
+    r = lfmod.Renderer(0)
+    r.load_views(tiny)
+    r.build_meshes(tiny, mesh_format="f16")
+    _check_full_frame(r, lfq, tiny.eyes[0])
+    r.close()
+
+
+# ---------------------------------------------------------------- rig scale (1,024 views of 1024^2, stereo 1440x1600)
+
+
+@pytest.fixture(scope="module")
+def rig():
+    return scene.rig_light_field(1)
+
+
+def test_rig_scale_sampled(lfmod, rig):
+    import torch
+
+    r = lfmod.Renderer(0)
+    r.load_views(rig)
+    r.build_meshes(rig)
+    out = r.render(rig.eyes)  # the stereo call the benchmark times
+    torch.cuda.synchronize()
+    st = r.stats()
+    assert st["error_word"] == 0
+    rng = np.random.default_rng(0)
+    for e, eye in enumerate(rig.eyes):
+        img = out[e].cpu().numpy().astype(np.float64)
+        pix = np.stack([rng.integers(0, eye.width, 3000), rng.integers(0, eye.height, 3000)], axis=1)
+        ref = oracle.render(rig, eye, pixels=pix, fragments=True, max_slots=32)
+        want = ref["rgba"]
+        g = img[pix[:, 1], pix[:, 0]]
+        valid = want[:, 3] > 0
+        assert valid.mean() > 0.95
+        assert np.array_equal(g[:, 3] > 0, valid)
+        assert np.max(np.abs(g[valid][:, :3] - want[valid][:, :3])) <= COLOUR_TOL
+        # coverage records at the sampled pixels, from the inspection call
+        got = r.render_inspect(eye, max_records=32)
+        flat = [int(j) * eye.width + int(i) for i, j in pix]
+        gr = _gpu_records(got, flat)
+        orr = _ref_records(ref, eye.width, pixels=pix)
+        for k in set(flat):
+            assert gr.get(k, []) == orr.get(k, []), k
+        # view selection over every pixel
+        sel = oracle.select_views(rig, eye)
+        assert np.array_equal(got["active"], sel)
+        assert st["active_views"][e] == int(sel.sum())
+        assert (got["rgba"].cpu() == out[e].cpu()).all()
+    r.close()
