@@ -42,7 +42,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=40)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["rig", "tiny"], default="rig")
+    p.add_argument("--workload", choices=["rig", "rig256", "tiny"], default="rig")
     p.add_argument("--poses", type=int, default=8, help="distinct head poses cycled through")
     p.add_argument("--tex", choices=["f32", "u8", "bf16", "fp8"], default="f32")
     p.add_argument("--tile", default="16x16")
@@ -72,12 +72,13 @@ def make_workload(name: str, n_heads: int, rank: int):
         desc = ("tiny cap: 8 spheres, 16 views 128x128 (90 deg) on a 40 deg cap, 32x32 meshes, "
                 "stereo 2x256x256 eyes")
     else:
-        lf = scene.rig_light_field(1, n_heads=0)
+        src = 1024 if name == "rig" else 256
+        lf = scene.rig_light_field(1, width=src, n_heads=0)
         rng = scene.SplitMix64(29 + 7919 + 104729 * rank)
         for _ in range(n_heads):
             lf.eyes += scene.head_pose_eyes(rng, 1440, 1600, 100.0)
-        desc = ("rig scale: 24 spheres, 1024 Fibonacci views 1024x1024 (120 deg) on a 0.35 m sphere, "
-                "64x64 meshes, stereo 2x1440x1600 eyes (100 deg, IPD 64 mm)")
+        desc = ("rig scale: 24 spheres, 1024 Fibonacci views %dx%d (120 deg) on a 0.35 m sphere, "
+                "64x64 meshes, stereo 2x1440x1600 eyes (100 deg, IPD 64 mm)" % (src, src))
     heads = [lf.eyes[2 * k:2 * k + 2] for k in range(n_heads)]
     return lf, heads, desc
 

@@ -164,7 +164,7 @@ LF_API lf_status lf_load_views(lf_ctx* ctx, int32_t n_views, const lf_pose* pose
  * along the view's pixel rays to the given z-depths, split into two triangles
  * per cell, (j,k)(j+1,k)(j,k+1) and (j+1,k)(j+1,k+1)(j,k+1), with ids
  * 2 (k (grid_n-1) + j) and that plus one.
- *   grid_n   2 .. 1024
+ *   grid_n   2 .. 257
  *   depth    host, n_views*grid_n*grid_n floats, row k then column j, z-depth
  *            in the view's camera frame (> 0)
  *   fmt      device storage of the depth grids

@@ -42,7 +42,7 @@ struct lf_ctx {
   lf_mesh_format mesh_fmt = LF_MESH_F32_DEPTH;
   Buffer depth, tab_a, tab_b;
   // per-call scratch
-  Buffer eyes, vrecs, masks, pool, small, active;
+  Buffer eyes, eyes_f, vrecs, masks, pool, clusters, small, active;
   EyeParams* pinned = nullptr;  // kRing slots of max_eyes
   cudaEvent_t ring_ev[kRing] = {};
   int ring_next = 0;
@@ -136,14 +136,19 @@ lf_status make_layout(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_i
 
 int mask_words(const lf_ctx* c) { return (c->n_views + 31) / 32; }
 
+// A non-empty cluster holds at least one triangle record.
+int64_t cluster_capacity(const lf_ctx* c) { return c->cfg.tri_capacity / 2 + 1024; }
+
 lf_status ensure_scratch(lf_ctx* c, int32_t n_eyes, int32_t total_tiles) {
   LF_CUDA(c, ensure(c->eyes, sizeof(EyeParams) * (size_t)c->cfg.max_eyes));
+  LF_CUDA(c, ensure(c->eyes_f, sizeof(EyeFloat) * (size_t)c->cfg.max_eyes));
   LF_CUDA(c, ensure(c->vrecs, sizeof(ViewRec) * (size_t)n_eyes * c->n_views));
   LF_CUDA(c, ensure(c->masks, sizeof(uint32_t) * (size_t)total_tiles * mask_words(c)));
   LF_CUDA(c, ensure(c->active, (size_t)n_eyes * c->n_views));
   LF_CUDA(c, ensure(c->small, 64));
   int64_t cap = c->cfg.tri_capacity;
   LF_CUDA(c, ensure(c->pool, sizeof(TriRec) * (size_t)cap));
+  LF_CUDA(c, ensure(c->clusters, sizeof(ClusterRec) * (size_t)cluster_capacity(c)));
   return LF_OK;
 }
 
@@ -182,12 +187,17 @@ FrameArgs frame_args(lf_ctx* c, const Layout& L) {
   a.tables.b = static_cast<const float*>(c->tab_b.p);
   a.vrecs = static_cast<ViewRec*>(c->vrecs.p);
   a.tile_masks = static_cast<uint32_t*>(c->masks.p);
+  a.eyes_f = static_cast<EyeFloat*>(c->eyes_f.p);
   a.pool = static_cast<TriRec*>(c->pool.p);
   a.pool_capacity = c->cfg.tri_capacity;
+  a.clusters = static_cast<ClusterRec*>(c->clusters.p);
+  a.cluster_capacity = cluster_capacity(c);
+  // counter block: triangle count (8 B), error word, work counter, cluster count (8 B)
   unsigned char* sm = static_cast<unsigned char*>(c->small.p);
   a.pool_counter = reinterpret_cast<unsigned long long*>(sm);
   a.error_word = reinterpret_cast<uint32_t*>(sm + 8);
   a.work_counter = reinterpret_cast<int32_t*>(sm + 12);
+  a.cluster_counter = reinterpret_cast<unsigned long long*>(sm + 16);
   a.active = static_cast<uint8_t*>(c->active.p);
   a.total_tiles = L.total_tiles;
   a.tile_w = c->cfg.tile_w;
@@ -199,8 +209,8 @@ FrameArgs frame_args(lf_ctx* c, const Layout& L) {
 lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persistent, cudaStream_t s) {
   const bool t = c->cfg.timing != 0;
   LF_CUDA(c, cudaMemsetAsync(a.tile_masks, 0, sizeof(uint32_t) * (size_t)a.total_tiles * a.mask_words, s));
-  // pool counter (8 B), error word (4 B) and work counter (4 B) start at zero each call
-  LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, 16, s));
+  // the counter block starts at zero each call
+  LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, 24, s));
   LF_CUDA(c, cudaMemsetAsync(a.active, 0, (size_t)a.n_eyes * a.n_views, s));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[0], s));
   LF_CUDA(c, launch_view_setup(a, s));
@@ -298,8 +308,8 @@ void lf_destroy(lf_ctx* ctx) {
   if (ctx->has_call && ctx->last_stream) cudaStreamSynchronize(ctx->last_stream);
   cudaDeviceSynchronize();
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
-  for (Buffer* b : {&ctx->views, &ctx->tex, &ctx->depth, &ctx->tab_a, &ctx->tab_b, &ctx->eyes, &ctx->vrecs,
-                    &ctx->masks, &ctx->pool, &ctx->small, &ctx->active})
+  for (Buffer* b : {&ctx->views, &ctx->tex, &ctx->depth, &ctx->tab_a, &ctx->tab_b, &ctx->eyes, &ctx->eyes_f,
+                    &ctx->vrecs, &ctx->masks, &ctx->pool, &ctx->clusters, &ctx->small, &ctx->active})
     release(*b);
   for (int k = 0; k < kRing; ++k)
     if (ctx->ring_ev[k]) cudaEventDestroy(ctx->ring_ev[k]);
@@ -394,7 +404,7 @@ lf_status lf_load_views(lf_ctx* c, int32_t n_views, const lf_pose* poses, const 
 lf_status lf_build_view_meshes(lf_ctx* c, int32_t grid_n, const float* depth, lf_mesh_format fmt) {
   if (!c) return LF_ERR_INVALID_ARG;
   if (c->n_views <= 0) return fail(c, LF_ERR_STATE, "views not loaded");
-  if (grid_n < 2 || grid_n > 1024 || !depth) return fail(c, LF_ERR_INVALID_ARG, "bad mesh arguments");
+  if (grid_n < 2 || grid_n > kMaxGridForSetup || !depth) return fail(c, LF_ERR_INVALID_ARG, "bad mesh arguments");
   if (fmt != LF_MESH_F32_DEPTH && fmt != LF_MESH_F16_OFFSET) return fail(c, LF_ERR_INVALID_ARG, "bad mesh format");
   LF_CUDA(c, cudaSetDevice(c->device));
   if (c->has_call && c->last_stream) LF_CUDA(c, cudaStreamSynchronize(c->last_stream));
@@ -484,7 +494,8 @@ lf_status lf_render_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const 
   }
   // The graph depends on the layout and on every scratch address it names.
   std::vector<int64_t> sig = {n_eyes, L.total_tiles, c->n_views, c->G, c->tex_fmt, c->mesh_fmt,
-                              (int64_t)(intptr_t)c->eyes.p, (int64_t)(intptr_t)c->vrecs.p,
+                              (int64_t)(intptr_t)c->eyes.p, (int64_t)(intptr_t)c->eyes_f.p,
+                              (int64_t)(intptr_t)c->clusters.p, (int64_t)(intptr_t)c->vrecs.p,
                               (int64_t)(intptr_t)c->masks.p, (int64_t)(intptr_t)c->pool.p,
                               (int64_t)(intptr_t)c->active.p, (int64_t)(intptr_t)c->small.p,
                               (int64_t)(intptr_t)c->tex.p, (int64_t)(intptr_t)c->depth.p, c->persistent_blocks};

@@ -11,8 +11,10 @@
 //   ViewRec[n_eyes x n_views]     composed transforms, footprint, triangle segment
 //   tile masks                    per eye tile, one bit per view whose disk footprint
 //                                 overlaps the tile (ceil(n_views/32) words)
+//   EyeFloat[n_eyes]              the eye's FP32 constants (rounded once, on the device)
 //   TriRec pool                   set-up (sub-)triangles, one contiguous segment per
-//                                 (eye, view) in triangle-id order
+//                                 (eye, view), grouped by 4x4-cell clusters
+//   ClusterRec pool               per non-empty cluster: bounding box and its triangles
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -52,13 +54,23 @@ struct EyeParams {
   float* out;           // H x W float4
 };
 
+// FP32 copies of an eye's parameters feeding the integer decisions, each the
+// round-to-nearest of the FP64 value (of t - C and R^2 for the sphere terms).
+struct __align__(16) EyeFloat {
+  float R[9];
+  float o[3];           // eye centre minus capture-sphere centre
+  float fx, fy, cx, cy;
+  float R2;             // capture-sphere radius squared
+  float pad[3];
+};
+
 struct __align__(16) ViewRec {
   float Hm[12];         // eye pixel (x, y, 1) and 1/z -> source (u, v) homogeneous; Hm 3x3 then hv
   float cc[4];          // disk centre relative to the capture sphere centre, then r^2
   float inv_r;
-  int32_t seg_base;
-  int32_t seg_count;
-  int32_t pad0;
+  int32_t cl_base;      // first ClusterRec of this (eye, view)
+  int32_t cl_count;     // its non-empty clusters
+  int32_t tri_count;    // its set-up triangles
   int32_t bb[4];        // conservative footprint in pixels, inclusive; bb[0] > bb[2] when empty
   float Mf[12];         // camera -> eye rotation (3x3) then translation, FP32
 };
@@ -70,6 +82,17 @@ struct __align__(16) TriRec {
   int32_t id_tl;                // parent id << 3 | top-left flags of edges 0..2
 };
 static_assert(sizeof(TriRec) == 48, "TriRec layout");
+
+// A 4x4-cell block of a view's grid (up to 32 triangles) after set-up: the
+// union of its triangles' pixel boxes and where its triangles are.
+struct __align__(16) ClusterRec {
+  int16_t bx0, by0, bx1, by1;
+  int32_t tri_base;
+  int32_t tri_count;
+};
+static_assert(sizeof(ClusterRec) == 16, "ClusterRec layout");
+constexpr int kClusterCells = 4;         // cells per cluster side
+constexpr int kMaxGridForSetup = 257;    // (G-1)/4 squared clusters must fit the set-up kernel's table
 
 struct GridTables {
   const float* a;   // n_views x G
@@ -94,9 +117,13 @@ struct FrameArgs {
   GridTables tables;
   ViewRec* vrecs;
   uint32_t* tile_masks;
+  EyeFloat* eyes_f;
   TriRec* pool;
   int64_t pool_capacity;
   unsigned long long* pool_counter;
+  ClusterRec* clusters;
+  int64_t cluster_capacity;
+  unsigned long long* cluster_counter;
   uint32_t* error_word;
   uint8_t* active;         // n_eyes x n_views view-selection flags
   int32_t total_tiles;

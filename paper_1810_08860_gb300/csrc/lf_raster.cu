@@ -26,15 +26,16 @@
 
 namespace lfk {
 
+// 80-byte stride: eight consecutive 16-byte stores hit distinct bank groups.
 struct __align__(16) TileTri {
   int32_t q0, q1, q2, id;   // id bit 31: edge deltas too large for the int32 path
   int32_t a0, b0, a1, b1;
   int32_t a2, b2;
   float ia, ib;
   float ic;
-  int32_t pad[3];
+  int32_t pad[7];           // pad[0]: view slot within the round
 };
-static_assert(sizeof(TileTri) == 64, "TileTri layout");
+static_assert(sizeof(TileTri) == 80, "TileTri layout");
 
 __device__ __forceinline__ float dot3_rn(float a0, float a1, float a2, float b0, float b1, float b2) {
   return __fmaf_rn(a0, b0, __fmaf_rn(a1, b1, __fmul_rn(a2, b2)));
@@ -98,9 +99,120 @@ __device__ __forceinline__ float3 bilinear(const void* tex, int64_t base, int W,
                      w00 * c00.z + w10 * c10.z + w01 * c01.z + w11 * c11.z);
 }
 
+
+constexpr int kMaxViewsPerRound = 64;   // views of one tile handled per round (bits of a 64-bit mask)
+constexpr int kWinnerBuf = 8;           // buffered depth-test winners per pixel before shading
+constexpr int kPx = 2;                  // vertically adjacent pixels per thread
+
+template <int BLOCK>
+struct RasterSmem {
+  TileTri tri[BLOCK];
+  int cl_tri_base[BLOCK];
+  int cl_off[BLOCK + 1];
+  int cl_slot[BLOCK];
+  long long q64[BLOCK * 3];
+  float wiz[kWinnerBuf][kPx][BLOCK];
+  uint8_t wslot[kWinnerBuf][kPx][BLOCK];
+  float4 cc[kMaxViewsPerRound];
+  float Hm[kMaxViewsPerRound][12];
+  float inv_r[kMaxViewsPerRound];
+  int cl_base[kMaxViewsPerRound];
+  int cl_count[kMaxViewsPerRound];
+  int views[kMaxViewsPerRound];
+  int off[kMaxViewsPerRound + 1];
+  int warp_cnt[BLOCK / 32];
+  unsigned any_lo, any_hi;
+  int n_views;
+  int n_list;
+  int cur_word;
+  int cur_partial;
+  uint32_t cur_bits;
+  int item;
+};
+
+// Warp 0: the next (up to 64) views of the tile's mask, in increasing order,
+// resuming from (cur_word, cur_bits) when the previous round stopped mid-word.
+__device__ __forceinline__ void collect_views(const uint32_t* mask, int mask_words, int* views, int& n_out,
+                                              int& cur_word, int& cur_partial, uint32_t& cur_bits) {
+  const int lane = threadIdx.x & 31;
+  int n = 0, w = cur_word;
+  bool partial = cur_partial != 0;
+  uint32_t pbits = cur_bits;
+  while (w < mask_words) {
+    const int wl = w + lane;
+    uint32_t b = 0;
+    if (wl < mask_words) b = (lane == 0 && partial) ? pbits : mask[wl];
+    const int c = __popc(b);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - c;
+    const int room = kMaxViewsPerRound - n;
+    const int take = min(max(room - excl, 0), c);
+    uint32_t bb = b;
+    for (int k = 0; k < take; ++k) {
+      const int bp = __ffs(bb) - 1;
+      bb &= bb - 1;
+      views[n + excl + k] = wl * 32 + bp;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total <= room) {
+      n += total;
+      w += 32;
+      partial = false;
+      continue;
+    }
+    const unsigned over = __ballot_sync(0xffffffffu, incl > room);
+    const int L = __ffs(over) - 1;
+    pbits = __shfl_sync(0xffffffffu, bb, L);
+    n = kMaxViewsPerRound;
+    w += L;
+    partial = true;
+    break;
+  }
+  n_out = n;
+  cur_word = w;
+  cur_partial = partial ? 1 : 0;
+  cur_bits = pbits;
+}
+
+// Ordered compaction of a block-wide predicate: returns this thread's slot
+// (valid when pred) and the total, via warp ballots and one barrier.
+template <int BLOCK>
+__device__ __forceinline__ int block_compact(bool pred, int* warp_cnt, int& total, uint32_t& ballot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ballot = __ballot_sync(0xffffffffu, pred);
+  if (lane == 0) warp_cnt[warp] = __popc(ballot);
+  __syncthreads();
+  int off = 0;
+  total = 0;
+#pragma unroll
+  for (int w2 = 0; w2 < BLOCK / 32; ++w2) {
+    const int c = warp_cnt[w2];
+    off += (w2 < warp) ? c : 0;
+    total += c;
+  }
+  return off + __popc(ballot & ((1u << lane) - 1u));
+}
+
+// One tile.  Per round of up to 64 views: (a) warp 0 lists the views from the
+// tile mask; (b) their records are loaded in parallel; (c) every pixel tests
+// its sphere crossing against every listed disk (one bit per view); (d) the
+// clusters of the views some pixel sees are tested against the tile, and the
+// triangles of the overlapping clusters are streamed in view order, BLOCK at
+// a time: bounding-box and edge-function tests against the tile, ballot
+// compaction into shared memory, then each pixel tests the compacted
+// triangles (warps skip triangles outside their rows or views none of their
+// pixels see); when the view changes, each pixel's winner for the finished
+// view is buffered; (e) buffered winners are shaded (bilinear fetch, weight,
+// accumulate) with both pixels' texel loads in flight together.
 template <int TW, int TH, int FMT, bool INSPECT>
-__device__ void raster_tile(const FrameArgs& A, int item, TileTri* s_tri, int64_t* s_q64, int* s_warp) {
-  constexpr int BLOCK = TW * TH;
+__device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * TH / kPx>& S) {
+  constexpr int BLOCK = TW * TH / kPx;
+  constexpr int ROWS_PER_WARP = (32 / TW) * kPx;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int e = 0;
   while (e + 1 < A.n_eyes && A.eyes[e + 1].tile_base <= item) ++e;
@@ -108,218 +220,414 @@ __device__ void raster_tile(const FrameArgs& A, int item, TileTri* s_tri, int64_
   const int tile = item - E.tile_base;
   const int tx = tile % E.tiles_x, ty = tile / E.tiles_x;
   const int i0 = tx * TW, j0 = ty * TH;
-  const int di = tid % TW, dj = tid / TW;
-  const int pi = i0 + di, pj = j0 + dj;
-  const bool valid = pi < E.W && pj < E.H;
-
-  // Eye ray (Eq. 1) and its crossing of the capture sphere, FP32, fixed order.
-  const float fx = __double2float_rn(E.fx), fy = __double2float_rn(E.fy);
-  const float cx = __double2float_rn(E.cx), cy = __double2float_rn(E.cy);
-  const float ex = __fdiv_rn(__fsub_rn(__fadd_rn((float)pi, 0.5f), cx), fx);
-  const float ey = __fdiv_rn(__fsub_rn(__fadd_rn((float)pj, 0.5f), cy), fy);
-  float d[3], o[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    d[k] = __fmaf_rn(__double2float_rn(E.R[k * 3 + 0]), ex,
-                     __fmaf_rn(__double2float_rn(E.R[k * 3 + 1]), ey, __double2float_rn(E.R[k * 3 + 2])));
-    o[k] = __double2float_rn(__dsub_rn(E.t[k], A.sphere_c[k]));
-  }
-  const float R2 = __double2float_rn(__dmul_rn(A.sphere_r, A.sphere_r));
-  const float qa = dot3_rn(d[0], d[1], d[2], d[0], d[1], d[2]);
-  const float qb = dot3_rn(o[0], o[1], o[2], d[0], d[1], d[2]);
-  const float qc = __fsub_rn(dot3_rn(o[0], o[1], o[2], o[0], o[1], o[2]), R2);
-  const float disc = __fsub_rn(__fmul_rn(qb, qb), __fmul_rn(qa, qc));
-  bool has_p = false;
-  float p[3] = {0.f, 0.f, 0.f};
-  if (disc >= 0.0f) {
-    float t = __fdiv_rn(__fsub_rn(__fsqrt_rn(disc), qb), qa);
-    if (t >= 0.0f) {
-      has_p = true;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) p[k] = __fmaf_rn(t, d[k], o[k]);
-    }
-  }
-  const float px = (float)pi + 0.5f, py = (float)pj + 0.5f;
-  float acc_r = 0.f, acc_g = 0.f, acc_b = 0.f, acc_w = 0.f;
-  int n_rec = 0;
-  const int64_t pix = (int64_t)pj * E.W + pi;
+  const int di = lane % TW;
+  const int dj = warp * ROWS_PER_WARP + (lane / TW) * kPx;  // first of this thread's pixel rows
+  const int wrow0 = j0 + warp * ROWS_PER_WARP, wrow1 = wrow0 + ROWS_PER_WARP - 1;
+  const int pi = i0 + di;
+  const EyeFloat& EF = A.eyes_f[e];
+  const float ex = __fdiv_rn(__fsub_rn(__fadd_rn((float)pi, 0.5f), EF.cx), EF.fx);
+  const float px = (float)pi + 0.5f;
   const int64_t P0x = 256 * (int64_t)i0 + 128, P0y = 256 * (int64_t)j0 + 128;
   const int64_t tex_per_view = (int64_t)A.src_w * A.src_h;
-
   const uint32_t* mask = A.tile_masks + (int64_t)item * A.mask_words;
-  for (int wd = 0; wd < A.mask_words; ++wd) {
-    uint32_t bits = mask[wd];
-    while (bits) {
-      const int v = wd * 32 + __ffs(bits) - 1;
-      bits &= bits - 1;
-      const ViewRec& VR = A.vrecs[(int64_t)e * A.n_views + v];
-      const float4 cc = *reinterpret_cast<const float4*>(VR.cc);
-      bool inside = false;
-      float w = 0.0f;
-      if (valid && has_p) {
-        float dx = __fsub_rn(p[0], cc.x), dy = __fsub_rn(p[1], cc.y), dz = __fsub_rn(p[2], cc.z);
-        float d2 = dot3_rn(dx, dy, dz, dx, dy, dz);
-        inside = d2 < cc.w;
-        w = fmaxf(0.0f, 1.0f - sqrtf(d2) * VR.inv_r);
-      }
-      if (!__syncthreads_or(inside)) continue;
-      if (tid == 0) A.active[(int64_t)e * A.n_views + v] = 1;
 
-      float best_iz = 0.0f;
-      int best_id = -1;
-      int n_cover = 0, min_id = 0x7fffffff, max_id = -1;
-      uint32_t hash = 0;
-      const int seg_base = VR.seg_base, seg_count = VR.seg_count;
-      for (int c0 = 0; c0 < seg_count; c0 += BLOCK) {
-        const int c = c0 + tid;
-        bool pred = false;
-        const TriRec* tr = A.pool + seg_base + c;
-        if (c < seg_count) {
-          const int2 bb = *reinterpret_cast<const int2*>(tr);
-          const int bx0 = (int16_t)(bb.x & 0xffff), by0 = bb.x >> 16;
-          const int bx1 = (int16_t)(bb.y & 0xffff), by1 = bb.y >> 16;
-          pred = bx0 <= i0 + TW - 1 && bx1 >= i0 && by0 <= j0 + TH - 1 && by1 >= j0;
-        }
-        const uint32_t ballot = __ballot_sync(0xffffffffu, pred);
-        if (lane == 0) s_warp[warp] = __popc(ballot);
-        __syncthreads();
-        int off = 0, n_list = 0;
+  bool valid[kPx], has_p[kPx];
+  float ey[kPx], py[kPx], p[kPx][3];
+  float acc_r[kPx], acc_g[kPx], acc_b[kPx], acc_w[kPx];
+  int n_rec[kPx];
 #pragma unroll
-        for (int w2 = 0; w2 < BLOCK / 32; ++w2) {
-          int cw = s_warp[w2];
-          off += (w2 < warp) ? cw : 0;
-          n_list += cw;
-        }
-        if (pred) {
-          const int pos = off + __popc(ballot & ((1u << lane) - 1u));
-          const int32_t X[3] = {tr->x[0], tr->x[1], tr->x[2]};
-          const int32_t Y[3] = {tr->y[0], tr->y[1], tr->y[2]};
-          const int32_t idtl = tr->id_tl;
-          TileTri tt;
-          bool big = false;
-          int64_t q64[3];
-          int32_t a[3], b[3];
+  for (int q = 0; q < kPx; ++q) {
+    const int pj = j0 + dj + q;
+    valid[q] = pi < E.W && pj < E.H;
+    // Eye ray (Eq. 1) and its crossing of the capture sphere, FP32, fixed order.
+    ey[q] = __fdiv_rn(__fsub_rn(__fadd_rn((float)pj, 0.5f), EF.cy), EF.fy);
+    py[q] = (float)pj + 0.5f;
+    float d[3];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int k1 = (k + 1) % 3;
-            const int64_t DX = (int64_t)X[k1] - X[k], DY = (int64_t)Y[k1] - Y[k];
-            const int64_t Ev = DX * (P0y - Y[k]) - DY * (P0x - X[k]) + ((idtl >> k) & 1) - 1;
-            q64[k] = Ev >> 8;  // floor division by 256
-            a[k] = (int32_t)(-DY);
-            b[k] = (int32_t)DX;
-            big |= (DX >= kBigEdge || DX <= -kBigEdge || DY >= kBigEdge || DY <= -kBigEdge);
-          }
-          tt.q0 = (int32_t)max(min(q64[0], (int64_t)kQClamp), -(int64_t)kQClamp);
-          tt.q1 = (int32_t)max(min(q64[1], (int64_t)kQClamp), -(int64_t)kQClamp);
-          tt.q2 = (int32_t)max(min(q64[2], (int64_t)kQClamp), -(int64_t)kQClamp);
-          tt.id = (idtl >> 3) | (big ? (int32_t)0x80000000 : 0);
-          tt.a0 = a[0]; tt.b0 = b[0]; tt.a1 = a[1]; tt.b1 = b[1]; tt.a2 = a[2]; tt.b2 = b[2];
-          tt.ia = tr->ia; tt.ib = tr->ib; tt.ic = tr->ic;
-          tt.pad[0] = tt.pad[1] = tt.pad[2] = 0;
-          s_tri[pos] = tt;
-          if (big) {
-            s_q64[pos * 3 + 0] = q64[0];
-            s_q64[pos * 3 + 1] = q64[1];
-            s_q64[pos * 3 + 2] = q64[2];
-          }
-        }
-        __syncthreads();
-        for (int t = 0; t < n_list; ++t) {
-          const TileTri& T = s_tri[t];
-          bool cov;
-          if (T.id >= 0) {
-            const int k0 = T.q0 + T.a0 * di + T.b0 * dj;
-            const int k1 = T.q1 + T.a1 * di + T.b1 * dj;
-            const int k2 = T.q2 + T.a2 * di + T.b2 * dj;
-            cov = (k0 | k1 | k2) >= 0;
-          } else {
-            const int64_t k0 = s_q64[t * 3 + 0] + (int64_t)T.a0 * di + (int64_t)T.b0 * dj;
-            const int64_t k1 = s_q64[t * 3 + 1] + (int64_t)T.a1 * di + (int64_t)T.b1 * dj;
-            const int64_t k2 = s_q64[t * 3 + 2] + (int64_t)T.a2 * di + (int64_t)T.b2 * dj;
-            cov = (k0 | k1 | k2) >= 0;
-          }
-          if (cov) {
-            const int id = T.id & 0x7fffffff;
-            if constexpr (INSPECT) {
-              ++n_cover;
-              min_id = min(min_id, id);
-              max_id = max(max_id, id);
-              hash ^= mix32((uint32_t)id);
-            }
-            const float iz = __fmaf_rn(T.ia, ex, __fmaf_rn(T.ib, ey, T.ic));
-            if (iz > 0.0f && (best_id < 0 || iz > best_iz)) {
-              best_iz = iz;
-              best_id = id;
-            }
-          }
-        }
-        __syncthreads();
+    for (int k = 0; k < 3; ++k) d[k] = __fmaf_rn(EF.R[k * 3 + 0], ex, __fmaf_rn(EF.R[k * 3 + 1], ey[q], EF.R[k * 3 + 2]));
+    const float qa = dot3_rn(d[0], d[1], d[2], d[0], d[1], d[2]);
+    const float qb = dot3_rn(EF.o[0], EF.o[1], EF.o[2], d[0], d[1], d[2]);
+    const float qc = __fsub_rn(dot3_rn(EF.o[0], EF.o[1], EF.o[2], EF.o[0], EF.o[1], EF.o[2]), EF.R2);
+    const float disc = __fsub_rn(__fmul_rn(qb, qb), __fmul_rn(qa, qc));
+    has_p[q] = false;
+    p[q][0] = p[q][1] = p[q][2] = 0.0f;
+    if (valid[q] && disc >= 0.0f) {
+      const float t = __fdiv_rn(__fsub_rn(__fsqrt_rn(disc), qb), qa);
+      if (t >= 0.0f) {
+        has_p[q] = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p[q][k] = __fmaf_rn(t, d[k], EF.o[k]);
       }
-      if (inside) {
-        if (best_id >= 0) {
-          const float* Hm = VR.Hm;
-          const float hx = fmaf(Hm[0], px, fmaf(Hm[1], py, fmaf(Hm[9], best_iz, Hm[2])));
-          const float hy = fmaf(Hm[3], px, fmaf(Hm[4], py, fmaf(Hm[10], best_iz, Hm[5])));
-          const float hz = fmaf(Hm[6], px, fmaf(Hm[7], py, fmaf(Hm[11], best_iz, Hm[8])));
+    }
+    acc_r[q] = acc_g[q] = acc_b[q] = acc_w[q] = 0.0f;
+    n_rec[q] = 0;
+  }
+
+  if (tid == 0) {
+    S.cur_word = 0;
+    S.cur_partial = 0;
+    S.cur_bits = 0;
+  }
+  __syncthreads();
+  for (;;) {
+    // ---- (a) views of this round, in increasing id order
+    if (warp == 0) {
+      int n, w = S.cur_word, part = S.cur_partial;
+      uint32_t bits = S.cur_bits;
+      collect_views(mask, A.mask_words, S.views, n, w, part, bits);
+      if (lane == 0) {
+        S.n_views = n; S.cur_word = w; S.cur_partial = part; S.cur_bits = bits;
+        S.any_lo = 0u; S.any_hi = 0u;
+      }
+    }
+    __syncthreads();
+    const int nv = S.n_views;
+    if (nv == 0) break;
+    // ---- (b) their per-eye records
+    for (int sl = tid; sl < nv; sl += BLOCK) {
+      const ViewRec& VR = A.vrecs[(int64_t)e * A.n_views + S.views[sl]];
+      S.cc[sl] = *reinterpret_cast<const float4*>(VR.cc);
+      S.inv_r[sl] = VR.inv_r;
+      S.cl_base[sl] = VR.cl_base;
+      S.cl_count[sl] = VR.cl_count;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) S.Hm[sl][k] = VR.Hm[k];
+    }
+    __syncthreads();
+    // ---- (c) disk membership of each pixel's sphere crossing, one bit per view
+    unsigned long long inmask[kPx];
+#pragma unroll
+    for (int q = 0; q < kPx; ++q) {
+      inmask[q] = 0ull;
+      if (has_p[q]) {
+        for (int sl = 0; sl < nv; ++sl) {
+          const float4 cc = S.cc[sl];
+          const float dx = __fsub_rn(p[q][0], cc.x), dy = __fsub_rn(p[q][1], cc.y), dz = __fsub_rn(p[q][2], cc.z);
+          if (dot3_rn(dx, dy, dz, dx, dy, dz) < cc.w) inmask[q] |= 1ull << sl;
+        }
+      }
+    }
+    unsigned long long wmask;  // views some pixel of this warp sees
+    {
+      unsigned long long m = 0ull;
+#pragma unroll
+      for (int q = 0; q < kPx; ++q) m |= inmask[q];
+      const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)m);
+      const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(m >> 32));
+      wmask = ((unsigned long long)hi << 32) | lo;
+      if (lane == 0) {
+        if (lo) atomicOr(&S.any_lo, lo);
+        if (hi) atomicOr(&S.any_hi, hi);
+      }
+    }
+    __syncthreads();
+    const unsigned long long any = ((unsigned long long)S.any_hi << 32) | S.any_lo;
+    for (int sl = tid; sl < nv; sl += BLOCK)
+      if ((any >> sl) & 1ull) A.active[(int64_t)e * A.n_views + S.views[sl]] = 1;
+    if (tid == 0) {
+      int acc = 0;
+      for (int sl = 0; sl < nv; ++sl) {
+        S.off[sl] = acc;
+        if ((any >> sl) & 1ull) acc += S.cl_count[sl];
+      }
+      S.off[nv] = acc;
+    }
+    __syncthreads();
+    const int Tc = S.off[nv];
+
+    // ---- (d) triangles of the seen views, in view order
+    int cur = -1;
+    int best_id[kPx], wcount[kPx], next_emit[kPx];
+    float best_iz[kPx];
+    int n_cover[kPx], min_id[kPx], max_id[kPx];
+    uint32_t hash[kPx];
+#pragma unroll
+    for (int q = 0; q < kPx; ++q) {
+      best_id[q] = -1; best_iz[q] = 0.0f; wcount[q] = 0; next_emit[q] = 0;
+      n_cover[q] = 0; min_id[q] = 0x7fffffff; max_id[q] = -1; hash[q] = 0u;
+    }
+
+    // (e) shade the buffered winners in view order, both pixels together
+    auto shade_flush = [&]() {
+      const int kmax = max(wcount[0], wcount[kPx - 1]);
+      for (int k = 0; k < kmax; ++k) {
+#pragma unroll
+        for (int q = 0; q < kPx; ++q) {
+          if (k >= wcount[q]) continue;
+          const int sl = S.wslot[k][q][tid];
+          const float iz = S.wiz[k][q][tid];
+          const float4 cc = S.cc[sl];
+          const float dx = __fsub_rn(p[q][0], cc.x), dy = __fsub_rn(p[q][1], cc.y), dz = __fsub_rn(p[q][2], cc.z);
+          const float d2 = dot3_rn(dx, dy, dz, dx, dy, dz);
+          const float w = fmaxf(0.0f, 1.0f - sqrtf(d2) * S.inv_r[sl]);
+          const float* Hm = S.Hm[sl];
+          const float hx = fmaf(Hm[0], px, fmaf(Hm[1], py[q], fmaf(Hm[9], iz, Hm[2])));
+          const float hy = fmaf(Hm[3], px, fmaf(Hm[4], py[q], fmaf(Hm[10], iz, Hm[5])));
+          const float hz = fmaf(Hm[6], px, fmaf(Hm[7], py[q], fmaf(Hm[11], iz, Hm[8])));
           if (hz > 0.0f) {
+            const int v = S.views[sl];
             const float rz = 1.0f / hz;
             const float scale = (FMT == LF_TEX_FP8E4M3) ? A.views[v].tex_scale : 1.0f;
             const float3 c = bilinear<FMT>(A.textures, (int64_t)v * tex_per_view, A.src_w, A.src_h, hx * rz,
                                            hy * rz, scale, INSPECT ? A.texel_bits : nullptr);
-            acc_r = fmaf(w, c.x, acc_r);
-            acc_g = fmaf(w, c.y, acc_g);
-            acc_b = fmaf(w, c.z, acc_b);
-            acc_w += w;
+            acc_r[q] = fmaf(w, c.x, acc_r[q]);
+            acc_g[q] = fmaf(w, c.y, acc_g[q]);
+            acc_b[q] = fmaf(w, c.z, acc_b[q]);
+            acc_w[q] += w;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kPx; ++q) wcount[q] = 0;
+    };
+    auto emit = [&](int q, int sl, int nc, int win, int mn, int mx, uint32_t h) {
+      if (n_rec[q] < A.max_records) {
+        lf_frag_record r;
+        r.view = S.views[sl];
+        r.n_cover = nc;
+        r.winner = win;
+        r.min_id = nc ? mn : -1;
+        r.max_id = nc ? mx : -1;
+        r.id_hash = h;
+        const int64_t pix = (int64_t)(j0 + dj + q) * E.W + pi;
+        A.records[pix * A.max_records + n_rec[q]] = r;
+      }
+      ++n_rec[q];
+    };
+    // Close the running view: buffer each pixel's winner; in the inspection
+    // form, emit records for it and for seen views before `upto` without triangles.
+    auto finalize = [&](int upto) {
+      bool full = false;
+#pragma unroll
+      for (int q = 0; q < kPx; ++q) {
+        if (cur >= 0 && ((inmask[q] >> cur) & 1ull)) {
+          if constexpr (INSPECT) {
+            for (int sl = next_emit[q]; sl < cur; ++sl)
+              if ((inmask[q] >> sl) & 1ull) emit(q, sl, 0, -1, 0, 0, 0u);
+            emit(q, cur, n_cover[q], best_id[q], min_id[q], max_id[q], hash[q]);
+            next_emit[q] = cur + 1;
+          }
+          if (best_id[q] >= 0) {
+            S.wslot[wcount[q]][q][tid] = (uint8_t)cur;
+            S.wiz[wcount[q]][q][tid] = best_iz[q];
+            full |= (++wcount[q] == kWinnerBuf);
           }
         }
         if constexpr (INSPECT) {
-          if (n_rec < A.max_records) {
-            lf_frag_record r;
-            r.view = v;
-            r.n_cover = n_cover;
-            r.winner = best_id;
-            r.min_id = n_cover ? min_id : -1;
-            r.max_id = max_id;
-            r.id_hash = hash;
-            A.records[pix * A.max_records + n_rec] = r;
-          }
-          ++n_rec;
+          for (int sl = next_emit[q]; sl < upto; ++sl)
+            if ((inmask[q] >> sl) & 1ull) emit(q, sl, 0, -1, 0, 0, 0u);
+          if (upto > next_emit[q]) next_emit[q] = upto;
         }
       }
+      if (full) shade_flush();
+    };
+
+    for (int c0 = 0; c0 < Tc; c0 += BLOCK) {
+      // clusters of this chunk that overlap the tile, compacted in order
+      {
+        const int f = c0 + tid;
+        bool cpred = false;
+        int csl = 0;
+        ClusterRec cr;
+        if (f < Tc) {
+          int lo = 0, hi = nv;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (S.off[mid] <= f) lo = mid;
+            else hi = mid;
+          }
+          csl = lo;
+          const int4 raw = __ldg(reinterpret_cast<const int4*>(A.clusters + S.cl_base[csl] + (f - S.off[csl])));
+          cr = *reinterpret_cast<const ClusterRec*>(&raw);
+          cpred = cr.bx0 <= i0 + TW - 1 && cr.bx1 >= i0 && cr.by0 <= j0 + TH - 1 && cr.by1 >= j0;
+        }
+        int cn;
+        uint32_t cb;
+        const int pos = block_compact<BLOCK>(cpred, S.warp_cnt, cn, cb);
+        if (cpred) {
+          S.cl_tri_base[pos] = cr.tri_base;
+          S.cl_off[pos] = cr.tri_count;
+          S.cl_slot[pos] = csl;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          int acc = 0;
+          for (int k = 0; k < cn; ++k) {
+            const int nt = S.cl_off[k];
+            S.cl_off[k] = acc;
+            acc += nt;
+          }
+          S.cl_off[cn] = acc;
+          S.n_list = cn;
+        }
+        __syncthreads();
+      }
+      const int ncl_list = S.n_list;
+      const int T = S.cl_off[ncl_list];
+      for (int f0 = 0; f0 < T; f0 += BLOCK) {
+        const int f = f0 + tid;
+        bool pred = false;
+        int sl = 0;
+        const TriRec* tr = A.pool;
+        int4 ra, rb, rc;
+        int64_t q64[3];
+        bool big = false;
+        if (f < T) {
+          int lo = 0, hi = ncl_list;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (S.cl_off[mid] <= f) lo = mid;
+            else hi = mid;
+          }
+          sl = S.cl_slot[lo];
+          tr = A.pool + S.cl_tri_base[lo] + (f - S.cl_off[lo]);
+          ra = __ldg(reinterpret_cast<const int4*>(tr));       // bbox, x0, x1
+          const int bx0 = (int16_t)(ra.x & 0xffff), by0 = ra.x >> 16;
+          const int bx1 = (int16_t)(ra.y & 0xffff), by1 = ra.y >> 16;
+          pred = bx0 <= i0 + TW - 1 && bx1 >= i0 && by0 <= j0 + TH - 1 && by1 >= j0;
+          if (pred) {
+            rb = __ldg(reinterpret_cast<const int4*>(tr) + 1);   // x2, y0, y1, y2
+            rc = __ldg(reinterpret_cast<const int4*>(tr) + 2);   // ia, ib, ic, id_tl
+            const int32_t X[3] = {ra.z, ra.w, rb.x};
+            const int32_t Y[3] = {rb.y, rb.z, rb.w};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const int k1 = (k + 1) % 3;
+              const int64_t DX = (int64_t)X[k1] - X[k], DY = (int64_t)Y[k1] - Y[k];
+              const int64_t Ev = DX * (P0y - Y[k]) - DY * (P0x - X[k]) + ((rc.w >> k) & 1) - 1;
+              q64[k] = Ev >> 8;  // floor division by 256
+              big |= (DX >= kBigEdge || DX <= -kBigEdge || DY >= kBigEdge || DY <= -kBigEdge);
+              // largest value of this edge over the tile's pixel centres; < 0 rejects the tile
+              const int64_t emax = q64[k] + max((int64_t)0, -DY * (TW - 1)) + max((int64_t)0, DX * (TH - 1));
+              pred &= emax >= 0;
+            }
+          }
+        }
+        int n_list;
+        uint32_t ballot;
+        const int pos = block_compact<BLOCK>(pred, S.warp_cnt, n_list, ballot);
+        if (pred) {
+          const int32_t X[3] = {ra.z, ra.w, rb.x};
+          const int32_t Y[3] = {rb.y, rb.z, rb.w};
+          TileTri tt;
+          tt.q0 = (int32_t)max(min(q64[0], (int64_t)kQClamp), -(int64_t)kQClamp);
+          tt.q1 = (int32_t)max(min(q64[1], (int64_t)kQClamp), -(int64_t)kQClamp);
+          tt.q2 = (int32_t)max(min(q64[2], (int64_t)kQClamp), -(int64_t)kQClamp);
+          tt.id = (rc.w >> 3) | (big ? (int32_t)0x80000000 : 0);
+          tt.a0 = Y[0] - Y[1]; tt.b0 = X[1] - X[0];
+          tt.a1 = Y[1] - Y[2]; tt.b1 = X[2] - X[1];
+          tt.a2 = Y[2] - Y[0]; tt.b2 = X[0] - X[2];
+          tt.ia = __int_as_float(rc.x); tt.ib = __int_as_float(rc.y); tt.ic = __int_as_float(rc.z);
+          tt.pad[0] = sl;
+          tt.pad[1] = ra.x >> 16;                 // first bbox row
+          tt.pad[2] = ra.y >> 16;                 // last bbox row
+          S.tri[pos] = tt;
+          if (big) {
+            S.q64[pos * 3 + 0] = q64[0];
+            S.q64[pos * 3 + 1] = q64[1];
+            S.q64[pos * 3 + 2] = q64[2];
+          }
+        }
+        __syncthreads();
+        for (int t = 0; t < n_list; ++t) {
+          const int4 w0 = *reinterpret_cast<const int4*>(&S.tri[t]);           // q0 q1 q2 id
+          const int4 w3 = *(reinterpret_cast<const int4*>(&S.tri[t]) + 3);     // ic, slot, row0, row1
+          const int tsl = w3.y;
+          if (tsl != cur) {
+            finalize(tsl);
+            cur = tsl;
+#pragma unroll
+            for (int q = 0; q < kPx; ++q) {
+              best_id[q] = -1;
+              best_iz[q] = 0.0f;
+              if constexpr (INSPECT) {
+                n_cover[q] = 0; min_id[q] = 0x7fffffff; max_id[q] = -1; hash[q] = 0u;
+              }
+            }
+          }
+          // warp-uniform skips: no pixel of the warp sees the view, or the
+          // triangle's rows miss the warp's rows
+          if (!((wmask >> tsl) & 1ull) || w3.w < wrow0 || w3.z > wrow1) continue;
+          const int4 w1 = *(reinterpret_cast<const int4*>(&S.tri[t]) + 1);     // a0 b0 a1 b1
+          const int4 w2 = *(reinterpret_cast<const int4*>(&S.tri[t]) + 2);     // a2 b2 ia ib
+          const int id = w0.w & 0x7fffffff;
+          const float ia = __int_as_float(w2.z), ib = __int_as_float(w2.w), ic = __int_as_float(w3.x);
+          bool cov[kPx];
+          if (w0.w >= 0) {
+            int k0 = w0.x + w1.x * di + w1.y * dj;
+            int k1 = w0.y + w1.z * di + w1.w * dj;
+            int k2 = w0.z + w2.x * di + w2.y * dj;
+#pragma unroll
+            for (int q = 0; q < kPx; ++q) {
+              cov[q] = (k0 | k1 | k2) >= 0;
+              k0 += w1.y; k1 += w1.w; k2 += w2.y;
+            }
+          } else {
+            int64_t k0 = S.q64[t * 3 + 0] + (int64_t)w1.x * di + (int64_t)w1.y * dj;
+            int64_t k1 = S.q64[t * 3 + 1] + (int64_t)w1.z * di + (int64_t)w1.w * dj;
+            int64_t k2 = S.q64[t * 3 + 2] + (int64_t)w2.x * di + (int64_t)w2.y * dj;
+#pragma unroll
+            for (int q = 0; q < kPx; ++q) {
+              cov[q] = (k0 | k1 | k2) >= 0;
+              k0 += w1.y; k1 += w1.w; k2 += w2.y;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < kPx; ++q) {
+            if (!cov[q] || !((inmask[q] >> tsl) & 1ull)) continue;
+            if constexpr (INSPECT) {
+              ++n_cover[q];
+              min_id[q] = min(min_id[q], id);
+              max_id[q] = max(max_id[q], id);
+              hash[q] ^= mix32((uint32_t)id);
+            }
+            const float iz = __fmaf_rn(ia, ex, __fmaf_rn(ib, ey[q], ic));
+            // nearest wins; equal depths go to the lower id, whatever the visiting order
+            if (iz > 0.0f && (best_id[q] < 0 || iz > best_iz[q] || (iz == best_iz[q] && id < best_id[q]))) {
+              best_iz[q] = iz;
+              best_id[q] = id;
+            }
+          }
+        }
+        __syncthreads();
+      }
     }
+    finalize(nv);
+    shade_flush();
+    __syncthreads();  // the view table is rewritten by the next round
   }
-  if (valid) {
+#pragma unroll
+  for (int q = 0; q < kPx; ++q) {
+    if (!valid[q]) continue;
+    const int64_t pix = (int64_t)(j0 + dj + q) * E.W + pi;
     float4 out;
-    if (acc_w > 0.0f) {
-      const float inv = 1.0f / acc_w;
-      out = make_float4(acc_r * inv, acc_g * inv, acc_b * inv, 1.0f);
+    if (acc_w[q] > 0.0f) {
+      const float inv = 1.0f / acc_w[q];
+      out = make_float4(acc_r[q] * inv, acc_g[q] * inv, acc_b[q] * inv, 1.0f);
     } else {
       out = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     reinterpret_cast<float4*>(E.out)[pix] = out;
     if constexpr (INSPECT) {
-      A.counts[pix] = n_rec;
-      if (n_rec > A.max_records) atomicOr(A.error_word, kErrRecordOverflow);
+      A.counts[pix] = n_rec[q];
+      if (n_rec[q] > A.max_records) atomicOr(A.error_word, kErrRecordOverflow);
     }
   }
 }
 
 template <int TW, int TH, int FMT, bool INSPECT, bool PERSISTENT>
-__global__ void __launch_bounds__(TW * TH) raster_kernel(FrameArgs A) {
-  __shared__ TileTri s_tri[TW * TH];
-  __shared__ int64_t s_q64[TW * TH * 3];
-  __shared__ int s_warp[TW * TH / 32];
+__global__ void __launch_bounds__(TW * TH / kPx, 5) raster_kernel(FrameArgs A) {
+  __shared__ RasterSmem<TW * TH / kPx> S;
   if constexpr (!PERSISTENT) {
-    raster_tile<TW, TH, FMT, INSPECT>(A, blockIdx.x, s_tri, s_q64, s_warp);
+    raster_tile<TW, TH, FMT, INSPECT>(A, blockIdx.x, S);
   } else {
-    __shared__ int s_item;
     for (;;) {
-      if (threadIdx.x == 0) s_item = atomicAdd(A.work_counter, 1);
+      if (threadIdx.x == 0) S.item = atomicAdd(A.work_counter, 1);
       __syncthreads();
-      const int item = s_item;
+      const int item = S.item;
       __syncthreads();
       if (item >= A.total_tiles) break;
-      raster_tile<TW, TH, FMT, INSPECT>(A, item, s_tri, s_q64, s_warp);
+      raster_tile<TW, TH, FMT, INSPECT>(A, item, S);
     }
   }
 }
@@ -327,11 +635,11 @@ __global__ void __launch_bounds__(TW * TH) raster_kernel(FrameArgs A) {
 template <int TW, int TH, int FMT>
 static cudaError_t launch_fmt(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s) {
   if (inspect) {
-    raster_kernel<TW, TH, FMT, true, false><<<a.total_tiles, TW * TH, 0, s>>>(a);
+    raster_kernel<TW, TH, FMT, true, false><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
   } else if (persistent) {
-    raster_kernel<TW, TH, FMT, false, true><<<pblocks, TW * TH, 0, s>>>(a);
+    raster_kernel<TW, TH, FMT, false, true><<<pblocks, TW * TH / kPx, 0, s>>>(a);
   } else {
-    raster_kernel<TW, TH, FMT, false, false><<<a.total_tiles, TW * TH, 0, s>>>(a);
+    raster_kernel<TW, TH, FMT, false, false><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -359,13 +667,13 @@ template <int TW, int TH>
 static cudaError_t occupancy_tile(int fmt, int* n) {
   switch (fmt) {
     case LF_TEX_F32:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_F32, false, true>, TW * TH, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_F32, false, true>, TW * TH / kPx, 0);
     case LF_TEX_U8:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_U8, false, true>, TW * TH, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_U8, false, true>, TW * TH / kPx, 0);
     case LF_TEX_BF16:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_BF16, false, true>, TW * TH, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_BF16, false, true>, TW * TH / kPx, 0);
     default:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_FP8E4M3, false, true>, TW * TH, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_FP8E4M3, false, true>, TW * TH / kPx, 0);
   }
 }
 

@@ -36,8 +36,8 @@ __device__ __forceinline__ bool snap_rn(float x, float y, float z, float fx, flo
   float su = __fmul_rn(u, 256.0f), sv = __fmul_rn(v, 256.0f);
   const float lim = (float)kSnapLimit;
   if (!(fabsf(su) < lim) || !(fabsf(sv) < lim)) return false;
-  sx = (int32_t)__float2ll_rn(su);
-  sy = (int32_t)__float2ll_rn(sv);
+  sx = __float2int_rn(su);  // |su| < 2^29: the 32-bit round-to-nearest-even conversion is exact
+  sy = __float2int_rn(sv);
   return true;
 }
 
@@ -156,123 +156,192 @@ cudaError_t launch_depth_offsets(const float* depth, int n_views, int per_view, 
 
 // ------------------------------------------------------------------ view set-up
 
-// x/z extent of a ball (centre (c, cz), radius rho) seen from the origin, in
-// the plane spanned by one image axis and the optical axis.  Returns false
-// when the ball lies entirely behind the eye; sets unbounded when it crosses
-// the eye plane or contains the eye.
-__device__ bool ball_extent(double c, double cz, double rho, double& lo, double& hi, bool& unbounded) {
-  unbounded = false;
-  if (cz < -rho) return false;
-  double L2 = c * c + cz * cz - rho * rho;
-  if (cz <= rho || L2 <= 0.0) {
-    unbounded = true;
+// Range of x/z over forward rays (z > 0) that meet a ball of radius rho whose
+// centre projects to (c, cz) in the plane of one image axis and the optical
+// axis: the directions within asin(rho/L) of the centre's direction, clipped to
+// the forward half-plane.  Returns false when no forward ray meets it; an
+// infinite bound is returned as +-inf.  FP32 is enough: the caller pads the
+// ball and the pixel range, and the result only culls.
+__device__ bool axis_extent(float c, float cz, float rho, float& lo, float& hi) {
+  const float half_pi = 1.57079632679f;
+  const float L2 = c * c + cz * cz;
+  if (L2 <= rho * rho * 1.0001f) {  // the eye's projection lies inside the ball's
+    lo = -INFINITY;
+    hi = INFINITY;
     return true;
   }
-  double L = sqrt(L2);
-  double den = cz * cz - rho * rho;
-  lo = (c * cz - rho * L) / den;
-  hi = (c * cz + rho * L) / den;
+  const float th = atan2f(c, cz), de = asinf(fminf(1.0f, rho * rsqrtf(L2)) ) + 1e-5f;
+  const float a = fmaxf(th - de, -half_pi), b = fminf(th + de, half_pi);
+  if (!(a < b)) return false;
+  lo = (a <= -half_pi + 1e-4f) ? -INFINITY : tanf(a);
+  hi = (b >= half_pi - 1e-4f) ? INFINITY : tanf(b);
   return true;
 }
 
-__global__ void view_setup_kernel(FrameArgs A) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  int e = blockIdx.y;
-  if (v >= A.n_views) return;
+// Pixel-index range [i0, i1] whose centres' x/z lies in [lo, hi], padded by two pixels.
+__device__ void pixel_range(float lo, float hi, float f, float c, int n, int& i0, int& i1) {
+  const float u0 = f * lo + c, u1 = f * hi + c;
+  i0 = (int)fmaxf(-1.0f, fminf((float)n, floorf(u0 - 0.5f) - 2.0f));
+  i1 = (int)fmaxf(-1.0f, fminf((float)n, ceilf(u1 - 0.5f) + 2.0f));
+}
+
+constexpr int kViewsPerSetupBlock = 16;
+constexpr int kViewSetupThreads = 128;
+
+// A block takes 16 views of one eye.  Threads 0-15 do the per-view set-up
+// (FP64 composition, FP32 shading map and disk constants, conservative
+// footprint); then all threads test every (view, tile) pair of the block's
+// footprints and OR the view's bit into the masks of the tiles it can reach.
+// The tile test compares cones from the eye: a pixel whose sphere crossing
+// lies in the disk has its ray within asin(rho/|c|) of the direction to the
+// disk centre c, and every pixel ray of a tile lies within (half diagonal)/f
+// of the tile's centre ray (rays through image points s apart differ by at
+// most s/f in angle), so a tile is skipped only when the two cones are apart.
+__global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs A) {
+  __shared__ int s_bb[kViewsPerSetupBlock][4];
+  __shared__ float s_dir[kViewsPerSetupBlock][4];   // unit direction to the disk centre, cos of the cone limit
+  __shared__ int s_off[kViewsPerSetupBlock + 1];
+  const int e = blockIdx.y;
+  const int v0 = blockIdx.x * kViewsPerSetupBlock;
   const EyeParams& E = A.eyes[e];
-  const ViewStatic& V = A.views[v];
-  ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
-
-  // A1: M = R_eye^T R_i, m = R_eye^T (t_i - t_eye) in FP64, fixed order, no fusion.
-  double M[9], m[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double s = __dmul_rn(E.R[0 * 3 + r], V.R[0 * 3 + c]);
-      s = __dadd_rn(s, __dmul_rn(E.R[1 * 3 + r], V.R[1 * 3 + c]));
-      s = __dadd_rn(s, __dmul_rn(E.R[2 * 3 + r], V.R[2 * 3 + c]));
-      M[r * 3 + c] = s;
-    }
-  double d[3] = {__dsub_rn(V.t[0], E.t[0]), __dsub_rn(V.t[1], E.t[1]), __dsub_rn(V.t[2], E.t[2])};
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    double s = __dmul_rn(E.R[0 * 3 + r], d[0]);
-    s = __dadd_rn(s, __dmul_rn(E.R[1 * 3 + r], d[1]));
-    s = __dadd_rn(s, __dmul_rn(E.R[2 * 3 + r], d[2]));
-    m[r] = s;
+  const float tile_half_diag = 0.5f * sqrtf((float)(A.tile_w * A.tile_w + A.tile_h * A.tile_h));
+  const float alpha_tile = tile_half_diag / fminf((float)E.fx, (float)E.fy);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // the eye's FP32 decision constants, each rounded once from FP64
+    EyeFloat& F = A.eyes_f[e];
+    for (int k = 0; k < 9; ++k) F.R[k] = __double2float_rn(E.R[k]);
+    for (int k = 0; k < 3; ++k) F.o[k] = __double2float_rn(__dsub_rn(E.t[k], A.sphere_c[k]));
+    F.fx = __double2float_rn(E.fx); F.fy = __double2float_rn(E.fy);
+    F.cx = __double2float_rn(E.cx); F.cy = __double2float_rn(E.cy);
+    F.R2 = __double2float_rn(__dmul_rn(A.sphere_r, A.sphere_r));
+    F.pad[0] = F.pad[1] = F.pad[2] = 0.0f;
   }
+  if (threadIdx.x < kViewsPerSetupBlock) {
+    const int v = v0 + threadIdx.x;
+    int bb[4] = {1, 1, 0, 0};
+    float dir[4] = {0.f, 0.f, 1.f, 2.f};
+    if (v < A.n_views) {
+      const ViewStatic& V = A.views[v];
+      ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
+      // A1: M = R_eye^T R_i, m = R_eye^T (t_i - t_eye) in FP64, fixed order, no fusion.
+      double M[9], m[3];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) R.Mf[k] = __double2float_rn(M[k]);
+      for (int r = 0; r < 3; ++r)
 #pragma unroll
-  for (int k = 0; k < 3; ++k) R.Mf[9 + k] = __double2float_rn(m[k]);
+        for (int c = 0; c < 3; ++c) {
+          double s = __dmul_rn(E.R[0 * 3 + r], V.R[0 * 3 + c]);
+          s = __dadd_rn(s, __dmul_rn(E.R[1 * 3 + r], V.R[1 * 3 + c]));
+          s = __dadd_rn(s, __dmul_rn(E.R[2 * 3 + r], V.R[2 * 3 + c]));
+          M[r * 3 + c] = s;
+        }
+      const double d[3] = {__dsub_rn(V.t[0], E.t[0]), __dsub_rn(V.t[1], E.t[1]), __dsub_rn(V.t[2], E.t[2])};
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        double s = __dmul_rn(E.R[0 * 3 + r], d[0]);
+        s = __dadd_rn(s, __dmul_rn(E.R[1 * 3 + r], d[1]));
+        s = __dadd_rn(s, __dmul_rn(E.R[2 * 3 + r], d[2]));
+        m[r] = s;
+      }
+      float Mc[9], mc[3];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) R.Mf[k] = Mc[k] = __double2float_rn(M[k]);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) R.Mf[9 + k] = mc[k] = __double2float_rn(m[k]);
 
-  // Source projection for shading: h = K_i' M^T (Kinv_e [x, y, 1] - m / z), with
-  // K_i' using (cx - 1/2, cy - 1/2) so h.x/h.z is the bilinear coordinate u = s - 1/2.
-  double Ki[9] = {V.fx, 0.0, V.cx - 0.5, 0.0, V.fy, V.cy - 0.5, 0.0, 0.0, 1.0};
-  double Ke[9] = {1.0 / E.fx, 0.0, -E.cx / E.fx, 0.0, 1.0 / E.fy, -E.cy / E.fy, 0.0, 0.0, 1.0};
-  double KM[9];  // Ki M^T
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) KM[r * 3 + c] = Ki[r * 3 + 0] * M[c * 3 + 0] + Ki[r * 3 + 1] * M[c * 3 + 1] + Ki[r * 3 + 2] * M[c * 3 + 2];
-  for (int r = 0; r < 3; ++r) {
-    for (int c = 0; c < 3; ++c)
-      R.Hm[r * 3 + c] = (float)(KM[r * 3 + 0] * Ke[0 * 3 + c] + KM[r * 3 + 1] * Ke[1 * 3 + c] + KM[r * 3 + 2] * Ke[2 * 3 + c]);
-    R.Hm[9 + r] = (float)(-(KM[r * 3 + 0] * m[0] + KM[r * 3 + 1] * m[1] + KM[r * 3 + 2] * m[2]));
-  }
+      // Source projection for shading: h = K_i' M^T (Kinv_e [x, y, 1] - m / z), with
+      // K_i' using (cx - 1/2, cy - 1/2) so h.x/h.z is the bilinear coordinate u = s - 1/2.
+      // FP32 from the composition: it only places texture samples.
+      const float Ki[9] = {(float)V.fx, 0.f, (float)(V.cx - 0.5), 0.f, (float)V.fy, (float)(V.cy - 0.5),
+                           0.f, 0.f, 1.f};
+      const float ifx = 1.0f / (float)E.fx, ify = 1.0f / (float)E.fy;
+      const float Ke[9] = {ifx, 0.f, -(float)E.cx * ifx, 0.f, ify, -(float)E.cy * ify, 0.f, 0.f, 1.f};
+      float KM[9];  // Ki M^T
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+          KM[r * 3 + c] = Ki[r * 3 + 0] * Mc[c * 3 + 0] + Ki[r * 3 + 1] * Mc[c * 3 + 1] + Ki[r * 3 + 2] * Mc[c * 3 + 2];
+      for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c)
+          R.Hm[r * 3 + c] = KM[r * 3 + 0] * Ke[0 * 3 + c] + KM[r * 3 + 1] * Ke[1 * 3 + c] + KM[r * 3 + 2] * Ke[2 * 3 + c];
+        R.Hm[9 + r] = -(KM[r * 3 + 0] * mc[0] + KM[r * 3 + 1] * mc[1] + KM[r * 3 + 2] * mc[2]);
+      }
 
-  // Disk (Sec. 4.1): centre relative to the sphere centre in FP32, r^2.
-  for (int k = 0; k < 3; ++k) R.cc[k] = __double2float_rn(__dsub_rn((double)V.disk_c[k], A.sphere_c[k]));
-  R.cc[3] = __fmul_rn(V.disk_r, V.disk_r);
-  R.inv_r = __frcp_rn(V.disk_r);
-  R.seg_base = 0;
-  R.seg_count = 0;
+      // Disk (Sec. 4.1): centre relative to the sphere centre in FP32, r^2.
+      for (int k = 0; k < 3; ++k) R.cc[k] = __double2float_rn(__dsub_rn((double)V.disk_c[k], A.sphere_c[k]));
+      R.cc[3] = __fmul_rn(V.disk_r, V.disk_r);
+      R.inv_r = __frcp_rn(V.disk_r);
+      R.cl_base = 0;
+      R.cl_count = 0;
+      R.tri_count = 0;
 
-  // Conservative footprint: every pixel whose sphere crossing can fall inside
-  // the disk sees a ray passing within r of c_i, so it lies in the screen
-  // extent of the ball of radius r (slightly inflated) about c_i.
-  double cw[3] = {(double)V.disk_c[0] - E.t[0], (double)V.disk_c[1] - E.t[1], (double)V.disk_c[2] - E.t[2]};
-  double ce[3];
-  for (int r = 0; r < 3; ++r) ce[r] = E.R[0 * 3 + r] * cw[0] + E.R[1 * 3 + r] * cw[1] + E.R[2 * 3 + r] * cw[2];
-  double rho = (double)V.disk_r * (1.0 + 1e-4) + 1e-5;
-  double xlo, xhi, ylo, yhi;
-  bool ux, uy;
-  int bx0 = 0, by0 = 0, bx1 = E.W - 1, by1 = E.H - 1;
-  bool vis = ball_extent(ce[0], ce[2], rho, xlo, xhi, ux) && ball_extent(ce[1], ce[2], rho, ylo, yhi, uy);
-  if (vis) {
-    if (!ux) {
-      double u0 = E.fx * xlo + E.cx, u1 = E.fx * xhi + E.cx;
-      bx0 = (int)fmax(-1.0, floor(u0 - 0.5) - 1.0);
-      bx1 = (int)fmin((double)E.W, ceil(u1 - 0.5) + 1.0);
+      // Conservative footprint: a pixel whose sphere crossing can fall inside the
+      // disk has a forward ray passing within r of c_i, so it lies in the screen
+      // extent of the ball of radius r (padded) about c_i.
+      float cw[3], ce[3];
+      for (int k = 0; k < 3; ++k) cw[k] = (float)((double)V.disk_c[k] - E.t[k]);
+      for (int r = 0; r < 3; ++r)
+        ce[r] = (float)E.R[0 * 3 + r] * cw[0] + (float)E.R[1 * 3 + r] * cw[1] + (float)E.R[2 * 3 + r] * cw[2];
+      const float rho = V.disk_r * 1.001f + 1e-4f;
+      float xlo, xhi, ylo, yhi;
+      if (axis_extent(ce[0], ce[2], rho, xlo, xhi) && axis_extent(ce[1], ce[2], rho, ylo, yhi)) {
+        int x0, x1, y0, y1;
+        pixel_range(xlo, xhi, (float)E.fx, (float)E.cx, E.W, x0, x1);
+        pixel_range(ylo, yhi, (float)E.fy, (float)E.cy, E.H, y0, y1);
+        x0 = max(x0, 0); y0 = max(y0, 0);
+        x1 = min(x1, E.W - 1); y1 = min(y1, E.H - 1);
+        if (x0 <= x1 && y0 <= y1) { bb[0] = x0; bb[1] = y0; bb[2] = x1; bb[3] = y1; }
+      }
+      R.bb[0] = bb[0]; R.bb[1] = bb[1]; R.bb[2] = bb[2]; R.bb[3] = bb[3];
+      // cone of the ball seen from the eye, widened by a tile's angular radius
+      const float L = sqrtf(ce[0] * ce[0] + ce[1] * ce[1] + ce[2] * ce[2]);
+      if (L > rho) {
+        const float lim = asinf(rho / L) + alpha_tile + 1e-4f;
+        dir[0] = ce[0] / L; dir[1] = ce[1] / L; dir[2] = ce[2] / L;
+        dir[3] = lim < 3.14159f ? cosf(lim) : -2.0f;
+      } else {
+        dir[3] = -2.0f;  // the eye is inside the ball: every tile of the footprint
+      }
     }
-    if (!uy) {
-      double v0 = E.fy * ylo + E.cy, v1 = E.fy * yhi + E.cy;
-      by0 = (int)fmax(-1.0, floor(v0 - 0.5) - 1.0);
-      by1 = (int)fmin((double)E.H, ceil(v1 - 0.5) + 1.0);
-    }
-    bx0 = max(bx0, 0);
-    by0 = max(by0, 0);
-    bx1 = min(bx1, E.W - 1);
-    by1 = min(by1, E.H - 1);
-    if (bx0 > bx1 || by0 > by1) vis = false;
+    for (int k = 0; k < 4; ++k) { s_bb[threadIdx.x][k] = bb[k]; s_dir[threadIdx.x][k] = dir[k]; }
   }
-  if (!vis) {
-    R.bb[0] = 1; R.bb[1] = 1; R.bb[2] = 0; R.bb[3] = 0;
-    return;
-  }
-  R.bb[0] = bx0; R.bb[1] = by0; R.bb[2] = bx1; R.bb[3] = by1;
-  int tx0 = bx0 / A.tile_w, tx1 = bx1 / A.tile_w, ty0 = by0 / A.tile_h, ty1 = by1 / A.tile_h;
-  uint32_t bit = 1u << (v & 31);
-  int word = v >> 5;
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) {
-      int64_t tile = (int64_t)E.tile_base + (int64_t)ty * E.tiles_x + tx;
-      atomicOr(&A.tile_masks[tile * A.mask_words + word], bit);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < kViewsPerSetupBlock; ++k) {
+      s_off[k] = acc;
+      if (s_bb[k][0] <= s_bb[k][2] && s_bb[k][1] <= s_bb[k][3]) {
+        const int ntx = s_bb[k][2] / A.tile_w - s_bb[k][0] / A.tile_w + 1;
+        const int nty = s_bb[k][3] / A.tile_h - s_bb[k][1] / A.tile_h + 1;
+        acc += ntx * nty;
+      }
     }
+    s_off[kViewsPerSetupBlock] = acc;
+  }
+  __syncthreads();
+  const int total = s_off[kViewsPerSetupBlock];
+  const float fx = (float)E.fx, fy = (float)E.fy, cx = (float)E.cx, cy = (float)E.cy;
+  for (int f = threadIdx.x; f < total; f += kViewSetupThreads) {
+    int k = 0;
+    while (k + 1 < kViewsPerSetupBlock && s_off[k + 1] <= f) ++k;
+    const int q = f - s_off[k];
+    const int tx0 = s_bb[k][0] / A.tile_w, ty0 = s_bb[k][1] / A.tile_h;
+    const int ntx = s_bb[k][2] / A.tile_w - tx0 + 1;
+    const int tx = tx0 + q % ntx, ty = ty0 + q / ntx;
+    // centre ray of the tile's pixel-centre rectangle
+    const float xc = (float)(tx * A.tile_w) + 0.5f * (float)(A.tile_w - 1) + 0.5f;
+    const float yc = (float)(ty * A.tile_h) + 0.5f * (float)(A.tile_h - 1) + 0.5f;
+    const float rx = (xc - cx) / fx, ry = (yc - cy) / fy;
+    const float inv = rsqrtf(rx * rx + ry * ry + 1.0f);
+    const float cosang = (rx * s_dir[k][0] + ry * s_dir[k][1] + s_dir[k][2]) * inv;
+    if (cosang < s_dir[k][3]) continue;
+    const int v = v0 + k;
+    const int64_t tile = (int64_t)E.tile_base + (int64_t)ty * E.tiles_x + tx;
+    atomicOr(&A.tile_masks[tile * A.mask_words + (v >> 5)], 1u << (v & 31));
+  }
 }
 
 cudaError_t launch_view_setup(const FrameArgs& a, cudaStream_t s) {
-  dim3 grid((a.n_views + 127) / 128, a.n_eyes);
-  view_setup_kernel<<<grid, 128, 0, s>>>(a);
+  dim3 grid((a.n_views + kViewsPerSetupBlock - 1) / kViewsPerSetupBlock, a.n_eyes);
+  view_setup_kernel<<<grid, kViewSetupThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -282,10 +351,10 @@ struct VtxSmem {
   float* x;
   float* y;
   float* z;
-  int32_t* sx;
-  int32_t* sy;
-  uint8_t* fl;  // bit0: z >= z_near, bit1: snapped beyond the limit
+  uint8_t* oc;  // outcode: bit0..3 left/right/above/below the padded footprint, bit4 behind z_near
 };
+
+constexpr uint8_t kOcBehind = 16;
 
 struct SetupCtx {
   float fx, fy, cx, cy, zn;
@@ -315,70 +384,71 @@ __device__ bool setup_sub(const int32_t* sx, const int32_t* sy, const SetupCtx& 
   t.x[0] = (int32_t)X0; t.y[0] = (int32_t)Y0;
   t.x[1] = (int32_t)X1; t.y[1] = (int32_t)Y1;
   t.x[2] = (int32_t)X2; t.y[2] = (int32_t)Y2;
-  int64_t X[3] = {X0, X1, X2}, Y[3] = {Y0, Y1, Y2};
+  const int64_t X[3] = {X0, X1, X2}, Y[3] = {Y0, Y1, Y2};
   tl = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    int k1 = (k + 1) % 3;
-    bool f = (Y[k] == Y[k1] && X[k1] > X[k]) || (Y[k1] < Y[k]);
+    const int k1 = (k + 1) % 3;
+    const bool f = (Y[k] == Y[k1] && X[k1] > X[k]) || (Y[k1] < Y[k]);
     tl |= (int)f << k;
   }
   return true;
 }
 
-// Set up parent triangle `id` (vertex slots q0, q1, q2 in smem); writes up to two
-// records into out[] and returns how many were kept.
-__device__ int setup_parent(int id, int q0, int q1, int q2, const VtxSmem& S, const SetupCtx& C, TriRec* out) {
-  int q[3] = {q0, q1, q2};
-  int in0 = S.fl[q0] & 1, in1 = S.fl[q1] & 1, in2 = S.fl[q2] & 1;
-  int n_in = in0 + in1 + in2;
-  if (n_in == 0) return 0;
-  // cheap reject: all vertices in front and the snapped bbox misses the footprint
-  if (n_in == 3) {
-    if ((S.fl[q0] | S.fl[q1] | S.fl[q2]) & 2) return 0;
-    int32_t mnx = min(S.sx[q0], min(S.sx[q1], S.sx[q2])), mxx = max(S.sx[q0], max(S.sx[q1], S.sx[q2]));
-    int32_t mny = min(S.sy[q0], min(S.sy[q1], S.sy[q2])), mxy = max(S.sy[q0], max(S.sy[q1], S.sy[q2]));
-    // pixel centre 256 i + 128 within [mn, mx]
-    if (mxx < 256 * C.bb0 + 128 || mnx > 256 * C.bb2 + 128 || mxy < 256 * C.bb1 + 128 || mny > 256 * C.bb3 + 128)
-      return 0;
-  }
+// Set up parent triangle `id` from vertex slots q0, q1, q2; writes up to two
+// records into out[] and returns how many were kept.  The decisions (snap,
+// clip, orientation, fill rule) are taken exactly as the oracle takes them;
+// the outcode test only drops triangles that lie wholly outside the padded
+// disk footprint, whose pixels never see this view.
+__device__ __forceinline__ int setup_parent(int id, int q0, int q1, int q2, const VtxSmem& S, const SetupCtx& C,
+                                            TriRec* out) {
+  const uint8_t o0 = S.oc[q0], o1 = S.oc[q1], o2 = S.oc[q2];
+  if (o0 & o1 & o2) return 0;  // all behind, or all beyond one side of the footprint
+  const int n_in = ((o0 & kOcBehind) == 0) + ((o1 & kOcBehind) == 0) + ((o2 & kOcBehind) == 0);
+  const float x0 = S.x[q0], y0 = S.y[q0], z0 = S.z[q0];
+  const float x1 = S.x[q1], y1 = S.y[q1], z1 = S.z[q1];
+  const float x2 = S.x[q2], y2 = S.y[q2], z2 = S.z[q2];
   // FP32 inverse-depth plane of the parent (original vertex order), fixed order.
-  float e1x = __fsub_rn(S.x[q1], S.x[q0]), e1y = __fsub_rn(S.y[q1], S.y[q0]), e1z = __fsub_rn(S.z[q1], S.z[q0]);
-  float e2x = __fsub_rn(S.x[q2], S.x[q0]), e2y = __fsub_rn(S.y[q2], S.y[q0]), e2z = __fsub_rn(S.z[q2], S.z[q0]);
-  float nx = __fsub_rn(__fmul_rn(e1y, e2z), __fmul_rn(e1z, e2y));
-  float ny = __fsub_rn(__fmul_rn(e1z, e2x), __fmul_rn(e1x, e2z));
-  float nz = __fsub_rn(__fmul_rn(e1x, e2y), __fmul_rn(e1y, e2x));
-  float dd = dot3_rn(nx, ny, nz, S.x[q0], S.y[q0], S.z[q0]);
-  float ia = __fdiv_rn(nx, dd), ib = __fdiv_rn(ny, dd), ic = __fdiv_rn(nz, dd);
+  const float e1x = __fsub_rn(x1, x0), e1y = __fsub_rn(y1, y0), e1z = __fsub_rn(z1, z0);
+  const float e2x = __fsub_rn(x2, x0), e2y = __fsub_rn(y2, y0), e2z = __fsub_rn(z2, z0);
+  const float nx = __fsub_rn(__fmul_rn(e1y, e2z), __fmul_rn(e1z, e2y));
+  const float ny = __fsub_rn(__fmul_rn(e1z, e2x), __fmul_rn(e1x, e2z));
+  const float nz = __fsub_rn(__fmul_rn(e1x, e2y), __fmul_rn(e1y, e2x));
+  const float dd = dot3_rn(nx, ny, nz, x0, y0, z0);
+  const float ia = __fdiv_rn(nx, dd), ib = __fdiv_rn(ny, dd), ic = __fdiv_rn(nz, dd);
   if (dd == 0.0f || !isfinite(ia) || !isfinite(ib) || !isfinite(ic)) return 0;
   int32_t px[4], py[4];
   int np = 0;
-  bool far = false;
   if (n_in == 3) {
-    for (int k = 0; k < 3; ++k) { px[k] = S.sx[q[k]]; py[k] = S.sy[q[k]]; }
+    if (!snap_rn(x0, y0, z0, C.fx, C.fy, C.cx, C.cy, px[0], py[0])) return 0;
+    if (!snap_rn(x1, y1, z1, C.fx, C.fy, C.cx, C.cy, px[1], py[1])) return 0;
+    if (!snap_rn(x2, y2, z2, C.fx, C.fy, C.cx, C.cy, px[2], py[2])) return 0;
     np = 3;
   } else {
+    // Sutherland-Hodgman against z >= z_near, walking v0 -> v1 -> v2 -> v0.
+    const float vx[3] = {x0, x1, x2}, vy[3] = {y0, y1, y2}, vz[3] = {z0, z1, z2};
+    const bool in[3] = {(o0 & kOcBehind) == 0, (o1 & kOcBehind) == 0, (o2 & kOcBehind) == 0};
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      int a = q[k], b = q[(k + 1) % 3];
-      bool ain = S.fl[a] & 1, bin = S.fl[b] & 1;
-      if (ain) {
-        px[np] = S.sx[a]; py[np] = S.sy[a];
-        far |= (S.fl[a] & 2) != 0;
+      const int k1 = (k + 1) % 3;
+      if (in[k]) {
+        if (!snap_rn(vx[k], vy[k], vz[k], C.fx, C.fy, C.cx, C.cy, px[np], py[np])) return 0;
         ++np;
       }
-      if (ain != bin) {
-        float tt = __fdiv_rn(__fsub_rn(C.zn, S.z[a]), __fsub_rn(S.z[b], S.z[a]));
-        float ix = __fmaf_rn(tt, __fsub_rn(S.x[b], S.x[a]), S.x[a]);
-        float iy = __fmaf_rn(tt, __fsub_rn(S.y[b], S.y[a]), S.y[a]);
-        if (!snap_rn(ix, iy, C.zn, C.fx, C.fy, C.cx, C.cy, px[np], py[np])) far = true;
+      if (in[k] != in[k1]) {
+        const float tt = __fdiv_rn(__fsub_rn(C.zn, vz[k]), __fsub_rn(vz[k1], vz[k]));
+        const float ix = __fmaf_rn(tt, __fsub_rn(vx[k1], vx[k]), vx[k]);
+        const float iy = __fmaf_rn(tt, __fsub_rn(vy[k1], vy[k]), vy[k]);
+        if (!snap_rn(ix, iy, C.zn, C.fx, C.fy, C.cx, C.cy, px[np], py[np])) return 0;
         ++np;
       }
     }
   }
-  if (far) return 0;
   int n = 0;
-  for (int f = 0; f + 2 < np; ++f) {
-    int32_t sx[3] = {px[0], px[f + 1], px[f + 2]}, sy[3] = {py[0], py[f + 1], py[f + 2]};
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    if (f + 2 >= np) break;
+    const int32_t sx[3] = {px[0], px[f + 1], px[f + 2]}, sy[3] = {py[0], py[f + 1], py[f + 2]};
     int32_t tl;
     TriRec& t = out[n];
     if (!setup_sub(sx, sy, C, t, tl)) continue;
@@ -411,140 +481,201 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& tot
   return base + x - v;
 }
 
+// Shared-memory row stride of the vertex arrays: >= G and = 4 (mod 32), so
+// the 4x4 cells of a cluster read 16 different banks.
+__host__ __device__ inline int vertex_row_stride(int G) { return G + ((36 - G % 32) % 32); }
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_rows) {
+  constexpr int NW = BLOCK / 32;
   const int v = blockIdx.x, e = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
   const int bb0 = R.bb[0], bb1 = R.bb[1], bb2 = R.bb[2], bb3 = R.bb[3];
   if (bb0 > bb2 || bb1 > bb3) return;  // disk footprint misses the eye
   const EyeParams& E = A.eyes[e];
+  const EyeFloat& EF = A.eyes_f[e];
   const int G = A.G;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nv_band = (band_rows + 1) * G;
+  const int RS = vertex_row_stride(G);
+  const int nv_band = (band_rows + 1) * RS;
+  const int ncl_side = (G - 1 + kClusterCells - 1) / kClusterCells;
+  int* s_cnt = reinterpret_cast<int*>(smem);          // kept triangles per cluster, then their prefix
+  int* s_cidx = s_cnt + ncl_side * ncl_side;           // 1 if non-empty, then its index among those
   VtxSmem S;
-  S.x = reinterpret_cast<float*>(smem);
+  S.x = reinterpret_cast<float*>(s_cidx + ncl_side * ncl_side);
   S.y = S.x + nv_band;
   S.z = S.y + nv_band;
-  S.sx = reinterpret_cast<int32_t*>(S.z + nv_band);
-  S.sy = S.sx + nv_band;
-  S.fl = reinterpret_cast<uint8_t*>(S.sy + nv_band);
-  __shared__ int s_warp[BLOCK / 32];
-  __shared__ long long s_base;
+  S.oc = reinterpret_cast<uint8_t*>(S.z + nv_band);
+  __shared__ int s_warp[NW];
+  __shared__ long long s_tri_base, s_cl_base;
 
   SetupCtx C;
-  C.fx = __double2float_rn(E.fx); C.fy = __double2float_rn(E.fy);
-  C.cx = __double2float_rn(E.cx); C.cy = __double2float_rn(E.cy);
+  C.fx = EF.fx; C.fy = EF.fy; C.cx = EF.cx; C.cy = EF.cy;
   C.zn = A.z_near; C.W = E.W; C.H = E.H;
   C.bb0 = bb0; C.bb1 = bb1; C.bb2 = bb2; C.bb3 = bb3;
+  // outcode planes in the form fx*x <op> (edge - cx) * z, padded by 2 pixels
+  const float oxl = (float)bb0 - 2.0f - C.cx, oxr = (float)bb2 + 3.0f - C.cx;
+  const float oyt = (float)bb1 - 2.0f - C.cy, oyb = (float)bb3 + 3.0f - C.cy;
   float Mf[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) Mf[k] = R.Mf[k];
   const float* ta = A.tables.a + (int64_t)v * G;
   const float* tb = A.tables.b + (int64_t)v * G;
   const ViewStatic& V = A.views[v];
-  const int n_cell_rows = G - 1;
-  const int n_bands = (n_cell_rows + band_rows - 1) / band_rows;
+  const int n_cell = G - 1;
+  const int ncl = (n_cell + kClusterCells - 1) / kClusterCells;  // clusters per side
+  const int n_bands = (n_cell + band_rows - 1) / band_rows;
 
   auto load_band = [&](int k0, int k1) {  // vertex rows k0 .. k1 inclusive
-    int nrow = k1 - k0 + 1;
-    for (int q = threadIdx.x; q < nrow * G; q += BLOCK) {
-      int k = k0 + q / G, j = q % G;
-      int64_t gi = ((int64_t)v * G + k) * G + j;
+    const int nq = (k1 - k0 + 1) * G;
+#pragma unroll 4
+    for (int q = threadIdx.x; q < nq; q += BLOCK) {
+      const int k = k0 + q / G, j = q % G;
+      const int64_t gi = ((int64_t)v * G + k) * G + j;
       float z;
       if (A.mesh_format == LF_MESH_F16_OFFSET)
         z = __fadd_rn(V.depth_origin, __half2float(reinterpret_cast<const __half*>(A.depth)[gi]));
       else
-        z = reinterpret_cast<const float*>(A.depth)[gi];
-      float X = __fmul_rn(z, ta[j]), Y = __fmul_rn(z, tb[k]), Z = z;
-      float ex = __fmaf_rn(Mf[0], X, __fmaf_rn(Mf[1], Y, __fmaf_rn(Mf[2], Z, Mf[9])));
-      float ey = __fmaf_rn(Mf[3], X, __fmaf_rn(Mf[4], Y, __fmaf_rn(Mf[5], Z, Mf[10])));
-      float ez = __fmaf_rn(Mf[6], X, __fmaf_rn(Mf[7], Y, __fmaf_rn(Mf[8], Z, Mf[11])));
-      uint8_t fl = 0;
-      int32_t sx = 0, sy = 0;
+        z = __ldg(reinterpret_cast<const float*>(A.depth) + gi);
+      const float X = __fmul_rn(z, __ldg(ta + j)), Y = __fmul_rn(z, __ldg(tb + k)), Z = z;
+      const float ex = __fmaf_rn(Mf[0], X, __fmaf_rn(Mf[1], Y, __fmaf_rn(Mf[2], Z, Mf[9])));
+      const float ey = __fmaf_rn(Mf[3], X, __fmaf_rn(Mf[4], Y, __fmaf_rn(Mf[5], Z, Mf[10])));
+      const float ez = __fmaf_rn(Mf[6], X, __fmaf_rn(Mf[7], Y, __fmaf_rn(Mf[8], Z, Mf[11])));
+      uint8_t oc = kOcBehind;
       if (ez >= C.zn) {
-        fl = 1;
-        if (!snap_rn(ex, ey, ez, C.fx, C.fy, C.cx, C.cy, sx, sy)) fl |= 2;
+        const float ux = C.fx * ex, uy = C.fy * ey;
+        oc = (uint8_t)((ux < oxl * ez ? 1 : 0) | (ux > oxr * ez ? 2 : 0) | (uy < oyt * ez ? 4 : 0) |
+                       (uy > oyb * ez ? 8 : 0));
       }
-      S.x[q] = ex; S.y[q] = ey; S.z[q] = ez;
-      S.sx[q] = sx; S.sy[q] = sy; S.fl[q] = fl;
+      const int slot = (k - k0) * RS + j;
+      S.x[slot] = ex; S.y[slot] = ey; S.z[slot] = ez;
+      S.oc[slot] = oc;
     }
   };
+  // Lane l of a warp owns triangle (cell l/2 of the 4x4 block, half l%2) of cluster c.
+  auto cluster_tri = [&](int c, int k0, TriRec* tmp) -> int {
+    const int cl_x = c % ncl, cl_y = c / ncl;
+    const int cell = lane >> 1, half = lane & 1;
+    const int j = cl_x * kClusterCells + (cell & 3), k = cl_y * kClusterCells + (cell >> 2);
+    if (j >= n_cell || k >= n_cell) return 0;
+    const int id = 2 * (k * n_cell + j) + half;
+    const int r0 = (k - k0) * RS;
+    if (half == 0) return setup_parent(id, r0 + j, r0 + j + 1, r0 + RS + j, S, C, tmp);
+    return setup_parent(id, r0 + j + 1, r0 + RS + j + 1, r0 + RS + j, S, C, tmp);
+  };
 
-  // Pass 1 counts kept records; pass 2 writes them in id order.
-  int my_count = 0;
+  // Pass 1: kept triangles per cluster.
   for (int bnd = 0; bnd < n_bands; ++bnd) {
-    int k0 = bnd * band_rows, k1 = min(k0 + band_rows, n_cell_rows);
+    const int k0 = bnd * band_rows, k1 = min(k0 + band_rows, n_cell);
     __syncthreads();
     load_band(k0, k1);
     __syncthreads();
-    int n_tri = 2 * (G - 1) * (k1 - k0);
-    for (int q = threadIdx.x; q < n_tri; q += BLOCK) {
-      int cell = q >> 1, half = q & 1;
-      int kk = cell / (G - 1), j = cell % (G - 1);
-      int id = 2 * ((k0 + kk) * (G - 1) + j) + half;
-      int r0 = kk * G;
+    const int c0 = (k0 / kClusterCells) * ncl, c1 = ((k1 + kClusterCells - 1) / kClusterCells) * ncl;
+    for (int c = c0 + warp; c < c1; c += NW) {
       TriRec tmp[2];
-      if (half == 0) my_count += setup_parent(id, r0 + j, r0 + j + 1, r0 + G + j, S, C, tmp);
-      else my_count += setup_parent(id, r0 + j + 1, r0 + G + j + 1, r0 + G + j, S, C, tmp);
+      const int n = cluster_tri(c, k0, tmp);
+      const int tot = __reduce_add_sync(0xffffffffu, n);
+      if (lane == 0) {
+        s_cnt[c] = tot;
+        s_cidx[c] = tot > 0 ? 1 : 0;
+      }
     }
-  }
-  int total;
-  block_exclusive_scan(my_count, s_warp, total);
-  if (threadIdx.x == 0) {
-    long long base = -1;
-    if (total > 0) {
-      unsigned long long b = atomicAdd(A.pool_counter, (unsigned long long)total);
-      if ((long long)b + total <= A.pool_capacity) base = (long long)b;
-      else atomicOr(A.error_word, kErrPoolOverflow);
-    }
-    s_base = base;
-    R.seg_base = base < 0 ? 0 : (int32_t)base;
-    R.seg_count = base < 0 ? 0 : total;
   }
   __syncthreads();
-  const long long base = s_base;
-  if (base < 0) return;
-  long long run = 0;
+  // Exclusive prefix over the clusters (each thread owns a contiguous run).
+  const int n_cl = ncl * ncl;
+  const int per = (n_cl + BLOCK - 1) / BLOCK;
+  const int r0 = threadIdx.x * per, r1 = min(r0 + per, n_cl);
+  int st = 0, sc = 0;
+  for (int c = r0; c < r1; ++c) { st += s_cnt[c]; sc += s_cidx[c]; }
+  int tot_t, tot_c;
+  int ot = block_exclusive_scan(st, s_warp, tot_t);
+  int oc = block_exclusive_scan(sc, s_warp, tot_c);
+  for (int c = r0; c < r1; ++c) {
+    const int nt = s_cnt[c], ne = s_cidx[c];
+    s_cnt[c] = ot;
+    s_cidx[c] = ne ? oc : -1;
+    ot += nt;
+    oc += ne;
+  }
+  if (threadIdx.x == 0) {
+    long long tb_ = -1, cb_ = -1;
+    if (tot_t > 0) {
+      const unsigned long long b = atomicAdd(A.pool_counter, (unsigned long long)tot_t);
+      const unsigned long long cb = atomicAdd(A.cluster_counter, (unsigned long long)tot_c);
+      if ((long long)b + tot_t <= A.pool_capacity && (long long)cb + tot_c <= A.cluster_capacity) {
+        tb_ = (long long)b;
+        cb_ = (long long)cb;
+      } else {
+        atomicOr(A.error_word, kErrPoolOverflow);
+      }
+    }
+    s_tri_base = tb_;
+    s_cl_base = cb_;
+    R.cl_base = cb_ < 0 ? 0 : (int32_t)cb_;
+    R.cl_count = cb_ < 0 ? 0 : tot_c;
+    R.tri_count = cb_ < 0 ? 0 : tot_t;
+  }
+  __syncthreads();
+  const long long tri_base = s_tri_base, cl_base = s_cl_base;
+  if (tri_base < 0) return;
+  // Pass 2: write each non-empty cluster's triangles and its bounding box.
   for (int bnd = 0; bnd < n_bands; ++bnd) {
-    int k0 = bnd * band_rows, k1 = min(k0 + band_rows, n_cell_rows);
+    const int k0 = bnd * band_rows, k1 = min(k0 + band_rows, n_cell);
     if (n_bands > 1) {
       __syncthreads();
       load_band(k0, k1);
       __syncthreads();
     }
-    int n_tri = 2 * (G - 1) * (k1 - k0);
-    for (int q0 = 0; q0 < n_tri; q0 += BLOCK) {
-      int q = q0 + threadIdx.x;
+    const int c0 = (k0 / kClusterCells) * ncl, c1 = ((k1 + kClusterCells - 1) / kClusterCells) * ncl;
+    for (int c = c0 + warp; c < c1; c += NW) {
+      const int ci = s_cidx[c];
+      if (ci < 0) continue;
       TriRec tmp[2];
-      int n = 0;
-      if (q < n_tri) {
-        int cell = q >> 1, half = q & 1;
-        int kk = cell / (G - 1), j = cell % (G - 1);
-        int id = 2 * ((k0 + kk) * (G - 1) + j) + half;
-        int r0 = kk * G;
-        if (half == 0) n = setup_parent(id, r0 + j, r0 + j + 1, r0 + G + j, S, C, tmp);
-        else n = setup_parent(id, r0 + j + 1, r0 + G + j + 1, r0 + G + j, S, C, tmp);
+      const int n = cluster_tri(c, k0, tmp);
+      int incl = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      int chunk_total;
-      int off = block_exclusive_scan(n, s_warp, chunk_total);
-      for (int k = 0; k < n; ++k) A.pool[base + run + off + k] = tmp[k];
-      run += chunk_total;
+      const long long dst = tri_base + s_cnt[c] + (incl - n);
+      int x0 = 0x7fffffff, y0 = 0x7fffffff, x1 = -1, y1 = -1;
+      for (int k = 0; k < n; ++k) {
+        A.pool[dst + k] = tmp[k];
+        x0 = min(x0, (int)tmp[k].bx0); y0 = min(y0, (int)tmp[k].by0);
+        x1 = max(x1, (int)tmp[k].bx1); y1 = max(y1, (int)tmp[k].by1);
+      }
+      x0 = __reduce_min_sync(0xffffffffu, x0);
+      y0 = __reduce_min_sync(0xffffffffu, y0);
+      x1 = __reduce_max_sync(0xffffffffu, x1);
+      y1 = __reduce_max_sync(0xffffffffu, y1);
+      const int tot = __shfl_sync(0xffffffffu, incl, 31);
+      if (lane == 0) {
+        ClusterRec cr;
+        cr.bx0 = (int16_t)x0; cr.by0 = (int16_t)y0; cr.bx1 = (int16_t)x1; cr.by1 = (int16_t)y1;
+        cr.tri_base = (int32_t)(tri_base + s_cnt[c]);
+        cr.tri_count = tot;
+        A.clusters[cl_base + ci] = cr;
+      }
     }
   }
 }
 
 constexpr int kSetupBlock = 256;
-constexpr size_t kVtxBytes = 21;  // x, y, z, sx, sy (4 B each) + flags
+constexpr size_t kVtxBytes = 13;  // x, y, z (4 B each) + outcode
 
+// Cell rows per band: the whole grid when it fits, else a multiple of the cluster size.
 static int setup_band_rows(int G, size_t smem_limit) {
-  int rows = (int)(smem_limit / (kVtxBytes * (size_t)G)) - 1;
-  if (rows > G - 1) rows = G - 1;
-  if (rows < 1) rows = 1;
-  return rows;
+  int rows = (int)(smem_limit / (kVtxBytes * (size_t)vertex_row_stride(G))) - 1;
+  if (rows >= G - 1) return G - 1;
+  rows = (rows / kClusterCells) * kClusterCells;
+  return rows < kClusterCells ? kClusterCells : rows;
 }
 
 cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s) {
-  const size_t limit = 160 * 1024;
+  const size_t limit = 96 * 1024;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t err = cudaFuncSetAttribute(tri_setup_kernel<kSetupBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -552,8 +683,9 @@ cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s) {
     if (err != cudaSuccess) return err;
     attr_done = true;
   }
-  int rows = setup_band_rows(a.G, limit);
-  size_t bytes = (size_t)(rows + 1) * a.G * kVtxBytes + 64;
+  const int rows = setup_band_rows(a.G, limit - 2 * sizeof(int) * 4096);
+  const int ncl = (a.G - 1 + kClusterCells - 1) / kClusterCells;
+  const size_t bytes = 2 * sizeof(int) * (size_t)ncl * ncl + (size_t)(rows + 1) * vertex_row_stride(a.G) * kVtxBytes + 64;
   dim3 grid(a.n_views, a.n_eyes);
   tri_setup_kernel<kSetupBlock><<<grid, kSetupBlock, bytes, s>>>(a, rows);
   return cudaGetLastError();
