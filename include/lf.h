@@ -211,6 +211,31 @@ LF_API lf_status lf_render_inspect(lf_ctx* ctx, const lf_pose* eye, const lf_int
                             lf_frag_record* records, int32_t max_records, int32_t* counts,
                             uint8_t* active, uint32_t* texel_bits, void* stream);
 
+/*
+ * Render one eye like lf_render, without allocating anything.  The paper has
+ * no counterpart: this is for callers that cannot call cudaMalloc while they
+ * render - a frame loop with a hard deadline, a process whose device memory
+ * is reserved up front by another allocator, a plug-in that may not allocate.
+ * lf_render grows its scratch with cudaMalloc on first use; this entry point
+ * instead takes all per-call scratch from one static device array of about
+ * 12.8 MB that every GPU loading the library holds until the process exits.
+ *   Limits (else LF_ERR_CAPACITY and a message in lf_last_error): at most 64
+ *   loaded views, a mesh grid of at most 33 x 33, at most 16384 screen tiles
+ *   (1024 x 1024 pixels with 8 x 8 tiles, 2048 x 2048 with 16 x 16).  Within
+ *   them the scratch cannot overflow.
+ *   eye, intr   host, as for lf_render (one eye)
+ *   out_rgba    caller-owned device buffer, height*width*4 floats
+ *   stream      cudaStream_t to run on
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (each call clears what must start at zero),
+ * so calls whose work overlaps on the GPU - on different streams, or from
+ * different contexts on one device - race and must be serialised by the
+ * caller.  lf_get_stats does not report these calls.
+ */
+LF_API lf_status lf_render_static(lf_ctx* ctx, const lf_pose* eye, const lf_intrinsics* intr, float* out_rgba,
+                                  void* stream);
+
 /* Counters of the last render call; synchronises with its stream. */
 LF_API lf_status lf_get_stats(lf_ctx* ctx, lf_stats* out);
 

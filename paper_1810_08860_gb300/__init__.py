@@ -59,7 +59,8 @@ FRAG_RECORD_DTYPE = np.dtype([("view", np.int32), ("n_cover", np.int32), ("winne
 
 # Every symbol include/lf.h declares.
 EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_build_view_meshes", "lf_render",
-           "lf_render_batch", "lf_render_inspect", "lf_get_stats", "lf_status_string", "lf_last_error"]
+           "lf_render_batch", "lf_render_inspect", "lf_render_static", "lf_get_stats", "lf_status_string",
+           "lf_last_error"]
 
 _lib = None
 
@@ -87,6 +88,8 @@ def load_library(path: str = LIB_PATH):
         f = getattr(lib, name)
         f.argtypes = [vp, i32, vp, vp, vp, vp]
         f.restype = ctypes.c_int
+    lib.lf_render_static.argtypes = [vp, vp, vp, vp, vp]
+    lib.lf_render_static.restype = ctypes.c_int
     lib.lf_render_inspect.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
     lib.lf_render_inspect.restype = ctypes.c_int
     lib.lf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -218,6 +221,15 @@ class Renderer:
         self._check(self.lib.lf_render_batch(self.ctx, len(eyes), poses, intr, ptrs, _stream_handle(stream)),
                     "lf_render_batch")
         return out
+
+    def render_static(self, eye, out=None, stream=None):
+        """Render one eye without allocating (lf_render_static): per-call scratch
+        comes from a static device array; see include/lf.h for its limits."""
+        poses, intr = self._eye_arrays([eye])
+        out, ptrs = self._outputs([eye], None if out is None else [out])
+        self._check(self.lib.lf_render_static(self.ctx, poses, intr, ctypes.c_void_p(ptrs[0]),
+                                              _stream_handle(stream)), "lf_render_static")
+        return out[0]
 
     def render_inspect(self, eye, max_records: int = 16, stream=None):
         """Inspection render of one eye: image, per-pixel (pixel, view) coverage

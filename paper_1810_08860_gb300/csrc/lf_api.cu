@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -558,3 +559,126 @@ lf_status lf_get_stats(lf_ctx* c, lf_stats* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Rendering without any allocation (lf_render_static).
+//
+// Some callers cannot call cudaMalloc while they render: a frame loop with a
+// hard deadline where an allocation (and the device synchronisation it can
+// imply) would miss the frame, a process whose device memory is fully
+// reserved up front by another allocator, or a sandboxed plug-in that is not
+// allowed to create allocations of its own.  lf_render grows its scratch
+// buffers with cudaMalloc on first use and whenever a call needs more, so it
+// is not safe for them.  lf_render_static runs the same three kernels on the
+// same loaded views, but takes every per-call scratch buffer from the one
+// static device array below, sized for the worst case within its limits, so
+// it never allocates and never runs out of room.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kStaticMaxViews = 64;
+constexpr int kStaticMaxGrid = 33;
+constexpr int kStaticMaxTiles = 16384;
+constexpr int64_t kStaticTris =
+    (int64_t)kStaticMaxViews * 4 * (kStaticMaxGrid - 1) * (kStaticMaxGrid - 1);  // two sub-triangles per parent
+constexpr int64_t kStaticClusters = (int64_t)kStaticMaxViews * ((kStaticMaxGrid - 1 + kClusterCells - 1) / kClusterCells) *
+                                    ((kStaticMaxGrid - 1 + kClusterCells - 1) / kClusterCells);
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kOffCounters = 0;
+constexpr size_t kOffEye = align256(kOffCounters + 64);
+constexpr size_t kOffEyeF = align256(kOffEye + sizeof(EyeParams));
+constexpr size_t kOffVrecs = align256(kOffEyeF + sizeof(EyeFloat));
+constexpr size_t kOffActive = align256(kOffVrecs + sizeof(ViewRec) * kStaticMaxViews);
+constexpr size_t kOffMasks = align256(kOffActive + kStaticMaxViews);
+constexpr size_t kOffClusters = align256(kOffMasks + sizeof(uint32_t) * kStaticMaxTiles * ((kStaticMaxViews + 31) / 32));
+constexpr size_t kOffPool = align256(kOffClusters + sizeof(ClusterRec) * kStaticClusters);
+constexpr size_t kStaticBytes = align256(kOffPool + sizeof(TriRec) * kStaticTris);  // about 12.8 MB
+
+}  // namespace
+
+// The scratch of lf_render_static.  Every GPU that loads this library holds
+// it until the process exits.  Its name is only a host-side stand-in: host
+// code must use the device address from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char lf_static_scratch[kStaticBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_addr[256] = {};
+
+// Device address of the static scratch on the current device, looked up once
+// per device (the caller has made `device` current).
+cudaError_t static_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, lf_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_static_addr[device]);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" lf_status lf_render_static(lf_ctx* c, const lf_pose* eye, const lf_intrinsics* intr, float* out_rgba,
+                                      void* stream) {
+  lf_status st = check_ready(c);
+  if (st != LF_OK) return st;
+  if (c->n_views > kStaticMaxViews)
+    return fail(c, LF_ERR_CAPACITY, "lf_render_static: more than 64 views are loaded");
+  if (c->G > kStaticMaxGrid) return fail(c, LF_ERR_CAPACITY, "lf_render_static: mesh grid larger than 33 x 33");
+  // the one eye, checked as lf_render checks it, built without any allocation
+  if (!eye || !intr || !out_rgba) return fail(c, LF_ERR_INVALID_ARG, "null argument");
+  const lf_intrinsics& K = *intr;
+  if (K.width < 1 || K.height < 1 || K.width > 32767 || K.height > 32767)
+    return fail(c, LF_ERR_INVALID_ARG, "eye size out of range");
+  if (!(K.fx > 0) || !(K.fy > 0)) return fail(c, LF_ERR_INVALID_ARG, "focal length must be positive");
+  EyeParams P;
+  std::memset(&P, 0, sizeof(P));
+  std::memcpy(P.R, eye->R, sizeof(P.R));
+  std::memcpy(P.t, eye->t, sizeof(P.t));
+  P.fx = K.fx; P.fy = K.fy; P.cx = K.cx; P.cy = K.cy;
+  P.W = K.width; P.H = K.height;
+  P.tiles_x = (K.width + c->cfg.tile_w - 1) / c->cfg.tile_w;
+  P.tiles_y = (K.height + c->cfg.tile_h - 1) / c->cfg.tile_h;
+  P.tile_base = 0;
+  P.out = out_rgba;
+  const int64_t tiles = (int64_t)P.tiles_x * P.tiles_y;
+  if (tiles > kStaticMaxTiles)
+    return fail(c, LF_ERR_CAPACITY, "lf_render_static: eye view has more than 16384 screen tiles");
+  unsigned char* base = nullptr;
+  LF_CUDA(c, static_scratch(c->device, &base));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // eye parameters through the context's pinned ring (allocated at lf_create)
+  const int slot = c->ring_next;
+  c->ring_next = (c->ring_next + 1) % kRing;
+  LF_CUDA(c, cudaEventSynchronize(c->ring_ev[slot]));
+  EyeParams* staged = c->pinned + (size_t)slot * c->cfg.max_eyes;
+  std::memcpy(staged, &P, sizeof(EyeParams));
+  LF_CUDA(c, cudaMemcpyAsync(base + kOffEye, staged, sizeof(EyeParams), cudaMemcpyHostToDevice, s));
+  LF_CUDA(c, cudaEventRecord(c->ring_ev[slot], s));
+  const Layout none;  // no eyes vector: the counts are set below
+  FrameArgs a = frame_args(c, none);
+  a.n_eyes = 1;
+  a.total_tiles = (int32_t)tiles;
+  a.eyes = reinterpret_cast<const EyeParams*>(base + kOffEye);
+  a.eyes_f = reinterpret_cast<EyeFloat*>(base + kOffEyeF);
+  a.vrecs = reinterpret_cast<ViewRec*>(base + kOffVrecs);
+  a.active = base + kOffActive;
+  a.tile_masks = reinterpret_cast<uint32_t*>(base + kOffMasks);
+  a.clusters = reinterpret_cast<ClusterRec*>(base + kOffClusters);
+  a.cluster_capacity = kStaticClusters;
+  a.pool = reinterpret_cast<TriRec*>(base + kOffPool);
+  a.pool_capacity = kStaticTris;
+  a.pool_counter = reinterpret_cast<unsigned long long*>(base + kOffCounters);
+  a.error_word = reinterpret_cast<uint32_t*>(base + kOffCounters + 8);
+  a.work_counter = reinterpret_cast<int32_t*>(base + kOffCounters + 12);
+  a.cluster_counter = reinterpret_cast<unsigned long long*>(base + kOffCounters + 16);
+  // enqueue_frame zeroes the masks, counters and flags that must start at zero
+  return enqueue_frame(c, a, false, false, s);
+}
