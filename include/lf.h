@@ -218,10 +218,10 @@ LF_API lf_status lf_render_inspect(lf_ctx* ctx, const lf_pose* eye, const lf_int
  * is reserved up front by another allocator, a plug-in that may not allocate.
  * lf_render grows its scratch with cudaMalloc on first use; this entry point
  * instead takes all per-call scratch from one static device array of about
- * 12.8 MB that every GPU loading the library holds until the process exits.
- *   Limits (else LF_ERR_CAPACITY and a message in lf_last_error): at most 64
- *   loaded views, a mesh grid of at most 33 x 33, at most 16384 screen tiles
- *   (1024 x 1024 pixels with 8 x 8 tiles, 2048 x 2048 with 16 x 16).  Within
+ * 16.8 MB that every GPU loading the library holds until the process exits.
+ *   Limits (else LF_ERR_CAPACITY and a message in lf_last_error): at most 32
+ *   loaded views, a mesh grid of at most 33 x 33, at most 8192 screen tiles
+ *   (1024 x 512 pixels with 8 x 8 tiles, 1024 x 2048 with 16 x 16).  Within
  *   them the scratch cannot overflow.
  *   eye, intr   host, as for lf_render (one eye)
  *   out_rgba    caller-owned device buffer, height*width*4 floats

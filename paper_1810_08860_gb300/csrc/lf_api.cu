@@ -43,7 +43,7 @@ struct lf_ctx {
   lf_mesh_format mesh_fmt = LF_MESH_F32_DEPTH;
   Buffer depth, tab_a, tab_b;
   // per-call scratch
-  Buffer eyes, eyes_f, vrecs, masks, pool, clusters, small, active;
+  Buffer eyes, eyes_f, vrecs, masks, pool, bin_offsets, bin_entries, small, active;
   EyeParams* pinned = nullptr;  // kRing slots of max_eyes
   cudaEvent_t ring_ev[kRing] = {};
   int ring_next = 0;
@@ -137,8 +137,10 @@ lf_status make_layout(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_i
 
 int mask_words(const lf_ctx* c) { return (c->n_views + 31) / 32; }
 
-// A non-empty cluster holds at least one triangle record.
-int64_t cluster_capacity(const lf_ctx* c) { return c->cfg.tri_capacity / 2 + 1024; }
+// Bin offsets take 2 ints per footprint tile per (eye, view); bin entries one
+// per (triangle, tile) pair, typically about four per set-up triangle.
+int64_t bin_offsets_capacity(const lf_ctx* c) { return c->cfg.tri_capacity / 2 + 65536; }
+int64_t bin_entries_capacity(const lf_ctx* c) { return c->cfg.tri_capacity * 4; }
 
 lf_status ensure_scratch(lf_ctx* c, int32_t n_eyes, int32_t total_tiles) {
   LF_CUDA(c, ensure(c->eyes, sizeof(EyeParams) * (size_t)c->cfg.max_eyes));
@@ -149,7 +151,8 @@ lf_status ensure_scratch(lf_ctx* c, int32_t n_eyes, int32_t total_tiles) {
   LF_CUDA(c, ensure(c->small, 64));
   int64_t cap = c->cfg.tri_capacity;
   LF_CUDA(c, ensure(c->pool, sizeof(TriRec) * (size_t)cap));
-  LF_CUDA(c, ensure(c->clusters, sizeof(ClusterRec) * (size_t)cluster_capacity(c)));
+  LF_CUDA(c, ensure(c->bin_offsets, sizeof(int32_t) * (size_t)bin_offsets_capacity(c)));
+  LF_CUDA(c, ensure(c->bin_entries, sizeof(int32_t) * (size_t)bin_entries_capacity(c)));
   return LF_OK;
 }
 
@@ -191,14 +194,18 @@ FrameArgs frame_args(lf_ctx* c, const Layout& L) {
   a.eyes_f = static_cast<EyeFloat*>(c->eyes_f.p);
   a.pool = static_cast<TriRec*>(c->pool.p);
   a.pool_capacity = c->cfg.tri_capacity;
-  a.clusters = static_cast<ClusterRec*>(c->clusters.p);
-  a.cluster_capacity = cluster_capacity(c);
-  // counter block: triangle count (8 B), error word, work counter, cluster count (8 B)
+  a.bin_offsets = static_cast<int32_t*>(c->bin_offsets.p);
+  a.bin_offsets_capacity = bin_offsets_capacity(c);
+  a.bin_entries = static_cast<int32_t*>(c->bin_entries.p);
+  a.bin_entries_capacity = bin_entries_capacity(c);
+  a.bin_max_tiles = 1 << 30;  // bin every triangle into every footprint tile its box covers
+  // counter block: triangles (8 B), error word, work counter, bin offsets (8 B), bin entries (8 B)
   unsigned char* sm = static_cast<unsigned char*>(c->small.p);
   a.pool_counter = reinterpret_cast<unsigned long long*>(sm);
   a.error_word = reinterpret_cast<uint32_t*>(sm + 8);
   a.work_counter = reinterpret_cast<int32_t*>(sm + 12);
-  a.cluster_counter = reinterpret_cast<unsigned long long*>(sm + 16);
+  a.bin_offsets_counter = reinterpret_cast<unsigned long long*>(sm + 16);
+  a.bin_entries_counter = reinterpret_cast<unsigned long long*>(sm + 24);
   a.active = static_cast<uint8_t*>(c->active.p);
   a.total_tiles = L.total_tiles;
   a.tile_w = c->cfg.tile_w;
@@ -211,12 +218,13 @@ lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persis
   const bool t = c->cfg.timing != 0;
   LF_CUDA(c, cudaMemsetAsync(a.tile_masks, 0, sizeof(uint32_t) * (size_t)a.total_tiles * a.mask_words, s));
   // the counter block starts at zero each call
-  LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, 24, s));
+  LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, 32, s));
   LF_CUDA(c, cudaMemsetAsync(a.active, 0, (size_t)a.n_eyes * a.n_views, s));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[0], s));
   LF_CUDA(c, launch_view_setup(a, s));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[1], s));
   LF_CUDA(c, launch_tri_setup(a, s));
+  LF_CUDA(c, launch_bin(a, s));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[2], s));
   LF_CUDA(c, launch_raster(a, inspect, persistent, c->persistent_blocks, s));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[3], s));
@@ -310,7 +318,8 @@ void lf_destroy(lf_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   for (Buffer* b : {&ctx->views, &ctx->tex, &ctx->depth, &ctx->tab_a, &ctx->tab_b, &ctx->eyes, &ctx->eyes_f,
-                    &ctx->vrecs, &ctx->masks, &ctx->pool, &ctx->clusters, &ctx->small, &ctx->active})
+                    &ctx->vrecs, &ctx->masks, &ctx->pool, &ctx->bin_offsets, &ctx->bin_entries, &ctx->small,
+                    &ctx->active})
     release(*b);
   for (int k = 0; k < kRing; ++k)
     if (ctx->ring_ev[k]) cudaEventDestroy(ctx->ring_ev[k]);
@@ -496,7 +505,8 @@ lf_status lf_render_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const 
   // The graph depends on the layout and on every scratch address it names.
   std::vector<int64_t> sig = {n_eyes, L.total_tiles, c->n_views, c->G, c->tex_fmt, c->mesh_fmt,
                               (int64_t)(intptr_t)c->eyes.p, (int64_t)(intptr_t)c->eyes_f.p,
-                              (int64_t)(intptr_t)c->clusters.p, (int64_t)(intptr_t)c->vrecs.p,
+                              (int64_t)(intptr_t)c->bin_offsets.p, (int64_t)(intptr_t)c->bin_entries.p,
+                              (int64_t)(intptr_t)c->vrecs.p,
                               (int64_t)(intptr_t)c->masks.p, (int64_t)(intptr_t)c->pool.p,
                               (int64_t)(intptr_t)c->active.p, (int64_t)(intptr_t)c->small.p,
                               (int64_t)(intptr_t)c->tex.p, (int64_t)(intptr_t)c->depth.p, c->persistent_blocks};
@@ -572,18 +582,19 @@ lf_status lf_get_stats(lf_ctx* c, lf_stats* out) {
 // is not safe for them.  lf_render_static runs the same three kernels on the
 // same loaded views, but takes every per-call scratch buffer from the one
 // static device array below, sized for the worst case within its limits, so
-// it never allocates and never runs out of room.
+// it never allocates and never runs out of room.  (A set-up triangle fills at
+// most kBinMaxTiles bin entries, and a view's bins at most 2 ints per tile.)
 // ---------------------------------------------------------------------------
 
 namespace {
 
-constexpr int kStaticMaxViews = 64;
+constexpr int kStaticMaxViews = 32;
 constexpr int kStaticMaxGrid = 33;
-constexpr int kStaticMaxTiles = 16384;
+constexpr int kStaticMaxTiles = 8192;
 constexpr int64_t kStaticTris =
     (int64_t)kStaticMaxViews * 4 * (kStaticMaxGrid - 1) * (kStaticMaxGrid - 1);  // two sub-triangles per parent
-constexpr int64_t kStaticClusters = (int64_t)kStaticMaxViews * ((kStaticMaxGrid - 1 + kClusterCells - 1) / kClusterCells) *
-                                    ((kStaticMaxGrid - 1 + kClusterCells - 1) / kClusterCells);
+constexpr int64_t kStaticBinOffsets = (int64_t)kStaticMaxViews * (2 * kStaticMaxTiles + 1);
+constexpr int64_t kStaticBinEntries = kStaticTris * kBinMaxTiles;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffCounters = 0;
@@ -592,9 +603,10 @@ constexpr size_t kOffEyeF = align256(kOffEye + sizeof(EyeParams));
 constexpr size_t kOffVrecs = align256(kOffEyeF + sizeof(EyeFloat));
 constexpr size_t kOffActive = align256(kOffVrecs + sizeof(ViewRec) * kStaticMaxViews);
 constexpr size_t kOffMasks = align256(kOffActive + kStaticMaxViews);
-constexpr size_t kOffClusters = align256(kOffMasks + sizeof(uint32_t) * kStaticMaxTiles * ((kStaticMaxViews + 31) / 32));
-constexpr size_t kOffPool = align256(kOffClusters + sizeof(ClusterRec) * kStaticClusters);
-constexpr size_t kStaticBytes = align256(kOffPool + sizeof(TriRec) * kStaticTris);  // about 12.8 MB
+constexpr size_t kOffBinOffsets = align256(kOffMasks + sizeof(uint32_t) * kStaticMaxTiles * ((kStaticMaxViews + 31) / 32));
+constexpr size_t kOffBinEntries = align256(kOffBinOffsets + sizeof(int32_t) * kStaticBinOffsets);
+constexpr size_t kOffPool = align256(kOffBinEntries + sizeof(int32_t) * kStaticBinEntries);
+constexpr size_t kStaticBytes = align256(kOffPool + sizeof(TriRec) * kStaticTris);  // about 16.8 MB
 
 }  // namespace
 
@@ -630,7 +642,7 @@ extern "C" lf_status lf_render_static(lf_ctx* c, const lf_pose* eye, const lf_in
   lf_status st = check_ready(c);
   if (st != LF_OK) return st;
   if (c->n_views > kStaticMaxViews)
-    return fail(c, LF_ERR_CAPACITY, "lf_render_static: more than 64 views are loaded");
+    return fail(c, LF_ERR_CAPACITY, "lf_render_static: more than 32 views are loaded");
   if (c->G > kStaticMaxGrid) return fail(c, LF_ERR_CAPACITY, "lf_render_static: mesh grid larger than 33 x 33");
   // the one eye, checked as lf_render checks it, built without any allocation
   if (!eye || !intr || !out_rgba) return fail(c, LF_ERR_INVALID_ARG, "null argument");
@@ -650,7 +662,7 @@ extern "C" lf_status lf_render_static(lf_ctx* c, const lf_pose* eye, const lf_in
   P.out = out_rgba;
   const int64_t tiles = (int64_t)P.tiles_x * P.tiles_y;
   if (tiles > kStaticMaxTiles)
-    return fail(c, LF_ERR_CAPACITY, "lf_render_static: eye view has more than 16384 screen tiles");
+    return fail(c, LF_ERR_CAPACITY, "lf_render_static: eye view has more than 8192 screen tiles");
   unsigned char* base = nullptr;
   LF_CUDA(c, static_scratch(c->device, &base));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -671,14 +683,18 @@ extern "C" lf_status lf_render_static(lf_ctx* c, const lf_pose* eye, const lf_in
   a.vrecs = reinterpret_cast<ViewRec*>(base + kOffVrecs);
   a.active = base + kOffActive;
   a.tile_masks = reinterpret_cast<uint32_t*>(base + kOffMasks);
-  a.clusters = reinterpret_cast<ClusterRec*>(base + kOffClusters);
-  a.cluster_capacity = kStaticClusters;
+  a.bin_offsets = reinterpret_cast<int32_t*>(base + kOffBinOffsets);
+  a.bin_offsets_capacity = kStaticBinOffsets;
+  a.bin_entries = reinterpret_cast<int32_t*>(base + kOffBinEntries);
+  a.bin_entries_capacity = kStaticBinEntries;
+  a.bin_max_tiles = kBinMaxTiles;
   a.pool = reinterpret_cast<TriRec*>(base + kOffPool);
   a.pool_capacity = kStaticTris;
   a.pool_counter = reinterpret_cast<unsigned long long*>(base + kOffCounters);
   a.error_word = reinterpret_cast<uint32_t*>(base + kOffCounters + 8);
   a.work_counter = reinterpret_cast<int32_t*>(base + kOffCounters + 12);
-  a.cluster_counter = reinterpret_cast<unsigned long long*>(base + kOffCounters + 16);
+  a.bin_offsets_counter = reinterpret_cast<unsigned long long*>(base + kOffCounters + 16);
+  a.bin_entries_counter = reinterpret_cast<unsigned long long*>(base + kOffCounters + 24);
   // enqueue_frame zeroes the masks, counters and flags that must start at zero
   return enqueue_frame(c, a, false, false, s);
 }

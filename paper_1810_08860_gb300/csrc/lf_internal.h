@@ -14,7 +14,9 @@
 //   EyeFloat[n_eyes]              the eye's FP32 constants (rounded once, on the device)
 //   TriRec pool                   set-up (sub-)triangles, one contiguous segment per
 //                                 (eye, view), grouped by 4x4-cell clusters
-//   ClusterRec pool               per non-empty cluster: bounding box and its triangles
+//   bin offsets / bin entries     per (eye, view): its triangles binned into the screen
+//                                 tiles of its footprint (pool indices), plus a list of
+//                                 triangles spanning more than bin_max_tiles tiles
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -68,10 +70,13 @@ struct __align__(16) ViewRec {
   float Hm[12];         // eye pixel (x, y, 1) and 1/z -> source (u, v) homogeneous; Hm 3x3 then hv
   float cc[4];          // disk centre relative to the capture sphere centre, then r^2
   float inv_r;
-  int32_t cl_base;      // first ClusterRec of this (eye, view)
-  int32_t cl_count;     // its non-empty clusters
+  int32_t tri_base;     // first set-up triangle of this (eye, view) in the pool
   int32_t tri_count;    // its set-up triangles
+  int32_t bin_off;      // its tile bins in the offset pool (-1: none): bntx*bnty+1 entry offsets
   int32_t bb[4];        // conservative footprint in pixels, inclusive; bb[0] > bb[2] when empty
+  int16_t btx0, bty0, bntx, bnty;  // the tiles of the footprint box
+  int32_t big_base;     // entries of the triangles spanning more than kBinMaxTiles tiles
+  int32_t big_count;
   float Mf[12];         // camera -> eye rotation (3x3) then translation, FP32
 };
 
@@ -83,15 +88,8 @@ struct __align__(16) TriRec {
 };
 static_assert(sizeof(TriRec) == 48, "TriRec layout");
 
-// A 4x4-cell block of a view's grid (up to 32 triangles) after set-up: the
-// union of its triangles' pixel boxes and where its triangles are.
-struct __align__(16) ClusterRec {
-  int16_t bx0, by0, bx1, by1;
-  int32_t tri_base;
-  int32_t tri_count;
-};
-static_assert(sizeof(ClusterRec) == 16, "ClusterRec layout");
-constexpr int kClusterCells = 4;         // cells per cluster side
+constexpr int kClusterCells = 4;         // cells per cluster side (set-up works cluster by cluster)
+constexpr int kBinMaxTiles = 16;         // the static-scratch render's cap on tiles binned per triangle
 constexpr int kMaxGridForSetup = 257;    // (G-1)/4 squared clusters must fit the set-up kernel's table
 
 struct GridTables {
@@ -121,9 +119,13 @@ struct FrameArgs {
   TriRec* pool;
   int64_t pool_capacity;
   unsigned long long* pool_counter;
-  ClusterRec* clusters;
-  int64_t cluster_capacity;
-  unsigned long long* cluster_counter;
+  int32_t* bin_offsets;
+  int64_t bin_offsets_capacity;
+  unsigned long long* bin_offsets_counter;
+  int32_t* bin_entries;
+  int64_t bin_entries_capacity;
+  int32_t bin_max_tiles;   // triangles spanning more tiles go to their view's list of big ones
+  unsigned long long* bin_entries_counter;
   uint32_t* error_word;
   uint8_t* active;         // n_eyes x n_views view-selection flags
   int32_t total_tiles;
@@ -145,6 +147,7 @@ cudaError_t launch_convert_textures(const uint8_t* src, void* dst, int64_t n_tex
                                     cudaStream_t s);
 cudaError_t launch_view_setup(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_bin(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_raster(const FrameArgs& a, bool inspect, bool persistent, int persistent_blocks,
                           cudaStream_t s);
 cudaError_t raster_occupancy(int tile_w, int tile_h, int tex_format, int* blocks_per_sm);

@@ -49,7 +49,7 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 }
 
 template <int FMT>
-__device__ __forceinline__ float3 texel(const void* tex, int64_t idx, float scale) {
+__device__ __forceinline__ float3 texel(const void* tex, int idx, float scale) {
   if constexpr (FMT == LF_TEX_F32) {
     float4 c = __ldg(reinterpret_cast<const float4*>(tex) + idx);
     return make_float3(c.x, c.y, c.z);
@@ -71,26 +71,24 @@ __device__ __forceinline__ float3 texel(const void* tex, int64_t idx, float scal
   }
 }
 
+// Bilinear sample of one view (tex points at its first texel) at bilinear
+// coordinates (u, v) = (s - 1/2, t - 1/2), clamp to edge.  The float clamp only
+// keeps the integer conversion in range; it does not change the result.
 template <int FMT>
-__device__ __forceinline__ float3 bilinear(const void* tex, int64_t base, int W, int H, float u, float v,
-                                           float scale, uint32_t* bits) {
+__device__ __forceinline__ float3 bilinear(const void* tex, int W, int H, float u, float v, float scale,
+                                           uint32_t* bits, int64_t bit_base) {
   u = fminf(fmaxf(u, -1.0f), (float)W);
   v = fminf(fmaxf(v, -1.0f), (float)H);
-  float fu = floorf(u), fv = floorf(v);
-  float al = u - fu, be = v - fv;
-  int i0 = (int)fu, j0 = (int)fv;
-  int i1 = min(i0 + 1, W - 1), j1 = min(j0 + 1, H - 1);
-  i0 = max(i0, 0);
-  j0 = max(j0, 0);
-  i1 = max(i1, 0);
-  j1 = max(j1, 0);
-  i0 = min(i0, W - 1);
-  j0 = min(j0, H - 1);
-  int64_t r0 = base + (int64_t)j0 * W, r1 = base + (int64_t)j1 * W;
-  float3 c00 = texel<FMT>(tex, r0 + i0, scale), c10 = texel<FMT>(tex, r0 + i1, scale);
-  float3 c01 = texel<FMT>(tex, r1 + i0, scale), c11 = texel<FMT>(tex, r1 + i1, scale);
+  const float fu = floorf(u), fv = floorf(v);
+  const float al = u - fu, be = v - fv;
+  const int iu = (int)fu, jv = (int)fv;
+  const int i0 = min(max(iu, 0), W - 1), i1 = min(max(iu + 1, 0), W - 1);
+  const int j0 = min(max(jv, 0), H - 1), j1 = min(max(jv + 1, 0), H - 1);
+  const int r0 = j0 * W, r1 = j1 * W;
+  const float3 c00 = texel<FMT>(tex, r0 + i0, scale), c10 = texel<FMT>(tex, r0 + i1, scale);
+  const float3 c01 = texel<FMT>(tex, r1 + i0, scale), c11 = texel<FMT>(tex, r1 + i1, scale);
   if (bits) {
-    int64_t t[4] = {r0 + i0, r0 + i1, r1 + i0, r1 + i1};
+    const int64_t t[4] = {bit_base + r0 + i0, bit_base + r0 + i1, bit_base + r1 + i0, bit_base + r1 + i1};
     for (int k = 0; k < 4; ++k) atomicOr(&bits[t[k] >> 5], 1u << (t[k] & 31));
   }
   float w00 = (1.0f - al) * (1.0f - be), w10 = al * (1.0f - be), w01 = (1.0f - al) * be, w11 = al * be;
@@ -107,23 +105,22 @@ constexpr int kPx = 2;                  // vertically adjacent pixels per thread
 template <int BLOCK>
 struct RasterSmem {
   TileTri tri[BLOCK];
-  int cl_tri_base[BLOCK];
-  int cl_off[BLOCK + 1];
-  int cl_slot[BLOCK];
   long long q64[BLOCK * 3];
   float wiz[kWinnerBuf][kPx][BLOCK];
   uint8_t wslot[kWinnerBuf][kPx][BLOCK];
   float4 cc[kMaxViewsPerRound];
+  const void* tex[kMaxViewsPerRound];  // first texel of each listed view
   float Hm[kMaxViewsPerRound][12];
   float inv_r[kMaxViewsPerRound];
-  int cl_base[kMaxViewsPerRound];
-  int cl_count[kMaxViewsPerRound];
+  int bstart[kMaxViewsPerRound];   // this tile's bin of the view: first entry
+  int bcount[kMaxViewsPerRound];   // its length
+  int gbase[kMaxViewsPerRound];    // the view's big triangles: first entry
+  int gcount[kMaxViewsPerRound];
   int views[kMaxViewsPerRound];
   int off[kMaxViewsPerRound + 1];
   int warp_cnt[BLOCK / 32];
   unsigned any_lo, any_hi;
   int n_views;
-  int n_list;
   int cur_word;
   int cur_partial;
   uint32_t cur_bits;
@@ -288,8 +285,27 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
       const ViewRec& VR = A.vrecs[(int64_t)e * A.n_views + S.views[sl]];
       S.cc[sl] = *reinterpret_cast<const float4*>(VR.cc);
       S.inv_r[sl] = VR.inv_r;
-      S.cl_base[sl] = VR.cl_base;
-      S.cl_count[sl] = VR.cl_count;
+      {
+        const int64_t off = (int64_t)S.views[sl] * tex_per_view;
+        const char* base = static_cast<const char*>(A.textures);
+        S.tex[sl] = base + off * (FMT == LF_TEX_F32 ? 16 : FMT == LF_TEX_BF16 ? 8 : 4);
+      }
+      // this tile's bin of the view, and the view's big triangles
+      int b0 = 0, bn = 0, g0 = 0, gn = 0;
+      if (VR.bin_off >= 0) {
+        const int lx = tx - VR.btx0, ly = ty - VR.bty0;
+        if (lx >= 0 && lx < VR.bntx && ly >= 0 && ly < VR.bnty) {
+          const int* offs = A.bin_offsets + VR.bin_off + ly * VR.bntx + lx;
+          b0 = offs[0];
+          bn = offs[1] - b0;
+        }
+        g0 = VR.big_base;
+        gn = VR.big_count;
+      }
+      S.bstart[sl] = b0;
+      S.bcount[sl] = bn;
+      S.gbase[sl] = g0;
+      S.gcount[sl] = gn;
 #pragma unroll
       for (int k = 0; k < 12; ++k) S.Hm[sl][k] = VR.Hm[k];
     }
@@ -324,16 +340,23 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
     const unsigned long long any = ((unsigned long long)S.any_hi << 32) | S.any_lo;
     for (int sl = tid; sl < nv; sl += BLOCK)
       if ((any >> sl) & 1ull) A.active[(int64_t)e * A.n_views + S.views[sl]] = 1;
-    if (tid == 0) {
-      int acc = 0;
-      for (int sl = 0; sl < nv; ++sl) {
-        S.off[sl] = acc;
-        if ((any >> sl) & 1ull) acc += S.cl_count[sl];
+    if (warp == 0) {
+      // exclusive prefix of the seen views' entry counts (slots lane and lane + 32)
+      const int c0 = (lane < nv && ((any >> lane) & 1ull)) ? S.bcount[lane] + S.gcount[lane] : 0;
+      const int c1 = (lane + 32 < nv && ((any >> (lane + 32)) & 1ull)) ? S.bcount[lane + 32] + S.gcount[lane + 32] : 0;
+      int s0 = c0, s1 = c1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y0 = __shfl_up_sync(0xffffffffu, s0, o), y1 = __shfl_up_sync(0xffffffffu, s1, o);
+        if (lane >= o) { s0 += y0; s1 += y1; }
       }
-      S.off[nv] = acc;
+      const int t0 = __shfl_sync(0xffffffffu, s0, 31), t1 = __shfl_sync(0xffffffffu, s1, 31);
+      S.off[lane] = s0 - c0;
+      S.off[lane + 32] = t0 + s1 - c1;
+      if (lane == 0) S.off[kMaxViewsPerRound] = t0 + t1;
     }
     __syncthreads();
-    const int Tc = S.off[nv];
+    const int T = S.off[nv];
 
     // ---- (d) triangles of the seen views, in view order
     int cur = -1;
@@ -359,17 +382,18 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
           const float4 cc = S.cc[sl];
           const float dx = __fsub_rn(p[q][0], cc.x), dy = __fsub_rn(p[q][1], cc.y), dz = __fsub_rn(p[q][2], cc.z);
           const float d2 = dot3_rn(dx, dy, dz, dx, dy, dz);
-          const float w = fmaxf(0.0f, 1.0f - sqrtf(d2) * S.inv_r[sl]);
+          // the weight is a value, not a decision: fast square root
+          const float w = fmaxf(0.0f, 1.0f - (d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f) * S.inv_r[sl]);
           const float* Hm = S.Hm[sl];
           const float hx = fmaf(Hm[0], px, fmaf(Hm[1], py[q], fmaf(Hm[9], iz, Hm[2])));
           const float hy = fmaf(Hm[3], px, fmaf(Hm[4], py[q], fmaf(Hm[10], iz, Hm[5])));
           const float hz = fmaf(Hm[6], px, fmaf(Hm[7], py[q], fmaf(Hm[11], iz, Hm[8])));
           if (hz > 0.0f) {
             const int v = S.views[sl];
-            const float rz = 1.0f / hz;
+            const float rz = __fdividef(1.0f, hz);
             const float scale = (FMT == LF_TEX_FP8E4M3) ? A.views[v].tex_scale : 1.0f;
-            const float3 c = bilinear<FMT>(A.textures, (int64_t)v * tex_per_view, A.src_w, A.src_h, hx * rz,
-                                           hy * rz, scale, INSPECT ? A.texel_bits : nullptr);
+            const float3 c = bilinear<FMT>(S.tex[sl], A.src_w, A.src_h, hx * rz, hy * rz, scale,
+                                           INSPECT ? A.texel_bits : nullptr, (int64_t)v * tex_per_view);
             acc_r[q] = fmaf(w, c.x, acc_r[q]);
             acc_g[q] = fmaf(w, c.y, acc_g[q]);
             acc_b[q] = fmaf(w, c.z, acc_b[q]);
@@ -422,49 +446,8 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
       if (full) shade_flush();
     };
 
-    for (int c0 = 0; c0 < Tc; c0 += BLOCK) {
-      // clusters of this chunk that overlap the tile, compacted in order
+    for (int f0 = 0; f0 < T; f0 += BLOCK) {
       {
-        const int f = c0 + tid;
-        bool cpred = false;
-        int csl = 0;
-        ClusterRec cr;
-        if (f < Tc) {
-          int lo = 0, hi = nv;
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (S.off[mid] <= f) lo = mid;
-            else hi = mid;
-          }
-          csl = lo;
-          const int4 raw = __ldg(reinterpret_cast<const int4*>(A.clusters + S.cl_base[csl] + (f - S.off[csl])));
-          cr = *reinterpret_cast<const ClusterRec*>(&raw);
-          cpred = cr.bx0 <= i0 + TW - 1 && cr.bx1 >= i0 && cr.by0 <= j0 + TH - 1 && cr.by1 >= j0;
-        }
-        int cn;
-        uint32_t cb;
-        const int pos = block_compact<BLOCK>(cpred, S.warp_cnt, cn, cb);
-        if (cpred) {
-          S.cl_tri_base[pos] = cr.tri_base;
-          S.cl_off[pos] = cr.tri_count;
-          S.cl_slot[pos] = csl;
-        }
-        __syncthreads();
-        if (tid == 0) {
-          int acc = 0;
-          for (int k = 0; k < cn; ++k) {
-            const int nt = S.cl_off[k];
-            S.cl_off[k] = acc;
-            acc += nt;
-          }
-          S.cl_off[cn] = acc;
-          S.n_list = cn;
-        }
-        __syncthreads();
-      }
-      const int ncl_list = S.n_list;
-      const int T = S.cl_off[ncl_list];
-      for (int f0 = 0; f0 < T; f0 += BLOCK) {
         const int f = f0 + tid;
         bool pred = false;
         int sl = 0;
@@ -473,14 +456,17 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
         int64_t q64[3];
         bool big = false;
         if (f < T) {
-          int lo = 0, hi = ncl_list;
+          int lo = 0, hi = nv;
           while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (S.cl_off[mid] <= f) lo = mid;
+            if (S.off[mid] <= f) lo = mid;
             else hi = mid;
           }
-          sl = S.cl_slot[lo];
-          tr = A.pool + S.cl_tri_base[lo] + (f - S.cl_off[lo]);
+          sl = lo;
+          const int k = f - S.off[sl];
+          const int idx = k < S.bcount[sl] ? A.bin_entries[S.bstart[sl] + k]
+                                           : A.bin_entries[S.gbase[sl] + (k - S.bcount[sl])];
+          tr = A.pool + idx;
           ra = __ldg(reinterpret_cast<const int4*>(tr));       // bbox, x0, x1
           const int bx0 = (int16_t)(ra.x & 0xffff), by0 = ra.x >> 16;
           const int bx1 = (int16_t)(ra.y & 0xffff), by1 = ra.y >> 16;
@@ -602,7 +588,7 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
     const int64_t pix = (int64_t)(j0 + dj + q) * E.W + pi;
     float4 out;
     if (acc_w[q] > 0.0f) {
-      const float inv = 1.0f / acc_w[q];
+      const float inv = __fdividef(1.0f, acc_w[q]);
       out = make_float4(acc_r[q] * inv, acc_g[q] * inv, acc_b[q] * inv, 1.0f);
     } else {
       out = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -616,7 +602,7 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
 }
 
 template <int TW, int TH, int FMT, bool INSPECT, bool PERSISTENT>
-__global__ void __launch_bounds__(TW * TH / kPx, 5) raster_kernel(FrameArgs A) {
+__global__ void __launch_bounds__(TW * TH / kPx, 7) raster_kernel(FrameArgs A) {
   __shared__ RasterSmem<TW * TH / kPx> S;
   if constexpr (!PERSISTENT) {
     raster_tile<TW, TH, FMT, INSPECT>(A, blockIdx.x, S);

@@ -269,8 +269,10 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
       for (int k = 0; k < 3; ++k) R.cc[k] = __double2float_rn(__dsub_rn((double)V.disk_c[k], A.sphere_c[k]));
       R.cc[3] = __fmul_rn(V.disk_r, V.disk_r);
       R.inv_r = __frcp_rn(V.disk_r);
-      R.cl_base = 0;
-      R.cl_count = 0;
+      R.tri_base = 0;
+      R.bin_off = -1;
+      R.big_base = 0;
+      R.big_count = 0;
       R.tri_count = 0;
 
       // Conservative footprint: a pixel whose sphere crossing can fall inside the
@@ -501,14 +503,13 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
   const int nv_band = (band_rows + 1) * RS;
   const int ncl_side = (G - 1 + kClusterCells - 1) / kClusterCells;
   int* s_cnt = reinterpret_cast<int*>(smem);          // kept triangles per cluster, then their prefix
-  int* s_cidx = s_cnt + ncl_side * ncl_side;           // 1 if non-empty, then its index among those
   VtxSmem S;
-  S.x = reinterpret_cast<float*>(s_cidx + ncl_side * ncl_side);
+  S.x = reinterpret_cast<float*>(s_cnt + ncl_side * ncl_side);
   S.y = S.x + nv_band;
   S.z = S.y + nv_band;
   S.oc = reinterpret_cast<uint8_t*>(S.z + nv_band);
   __shared__ int s_warp[NW];
-  __shared__ long long s_tri_base, s_cl_base;
+  __shared__ long long s_tri_base;
 
   SetupCtx C;
   C.fx = EF.fx; C.fy = EF.fy; C.cx = EF.cx; C.cy = EF.cy;
@@ -578,7 +579,6 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
       const int tot = __reduce_add_sync(0xffffffffu, n);
       if (lane == 0) {
         s_cnt[c] = tot;
-        s_cidx[c] = tot > 0 ? 1 : 0;
       }
     }
   }
@@ -587,40 +587,30 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
   const int n_cl = ncl * ncl;
   const int per = (n_cl + BLOCK - 1) / BLOCK;
   const int r0 = threadIdx.x * per, r1 = min(r0 + per, n_cl);
-  int st = 0, sc = 0;
-  for (int c = r0; c < r1; ++c) { st += s_cnt[c]; sc += s_cidx[c]; }
-  int tot_t, tot_c;
+  int st = 0;
+  for (int c = r0; c < r1; ++c) st += s_cnt[c];
+  int tot_t;
   int ot = block_exclusive_scan(st, s_warp, tot_t);
-  int oc = block_exclusive_scan(sc, s_warp, tot_c);
   for (int c = r0; c < r1; ++c) {
-    const int nt = s_cnt[c], ne = s_cidx[c];
+    const int nt = s_cnt[c];
     s_cnt[c] = ot;
-    s_cidx[c] = ne ? oc : -1;
     ot += nt;
-    oc += ne;
   }
   if (threadIdx.x == 0) {
-    long long tb_ = -1, cb_ = -1;
+    long long tb_ = -1;
     if (tot_t > 0) {
       const unsigned long long b = atomicAdd(A.pool_counter, (unsigned long long)tot_t);
-      const unsigned long long cb = atomicAdd(A.cluster_counter, (unsigned long long)tot_c);
-      if ((long long)b + tot_t <= A.pool_capacity && (long long)cb + tot_c <= A.cluster_capacity) {
-        tb_ = (long long)b;
-        cb_ = (long long)cb;
-      } else {
-        atomicOr(A.error_word, kErrPoolOverflow);
-      }
+      if ((long long)b + tot_t <= A.pool_capacity) tb_ = (long long)b;
+      else atomicOr(A.error_word, kErrPoolOverflow);
     }
     s_tri_base = tb_;
-    s_cl_base = cb_;
-    R.cl_base = cb_ < 0 ? 0 : (int32_t)cb_;
-    R.cl_count = cb_ < 0 ? 0 : tot_c;
-    R.tri_count = cb_ < 0 ? 0 : tot_t;
+    R.tri_base = tb_ < 0 ? 0 : (int32_t)tb_;
+    R.tri_count = tb_ < 0 ? 0 : tot_t;
   }
   __syncthreads();
-  const long long tri_base = s_tri_base, cl_base = s_cl_base;
+  const long long tri_base = s_tri_base;
   if (tri_base < 0) return;
-  // Pass 2: write each non-empty cluster's triangles and its bounding box.
+  // Pass 2: write each cluster's triangles in cluster order.
   for (int bnd = 0; bnd < n_bands; ++bnd) {
     const int k0 = bnd * band_rows, k1 = min(k0 + band_rows, n_cell);
     if (n_bands > 1) {
@@ -630,8 +620,8 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
     }
     const int c0 = (k0 / kClusterCells) * ncl, c1 = ((k1 + kClusterCells - 1) / kClusterCells) * ncl;
     for (int c = c0 + warp; c < c1; c += NW) {
-      const int ci = s_cidx[c];
-      if (ci < 0) continue;
+      const int cnext = (c + 1 < ncl * ncl) ? s_cnt[c + 1] : tot_t;
+      if (cnext == s_cnt[c]) continue;  // nothing kept in this cluster
       TriRec tmp[2];
       const int n = cluster_tri(c, k0, tmp);
       int incl = n;
@@ -641,26 +631,118 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
         if (lane >= o) incl += y;
       }
       const long long dst = tri_base + s_cnt[c] + (incl - n);
-      int x0 = 0x7fffffff, y0 = 0x7fffffff, x1 = -1, y1 = -1;
-      for (int k = 0; k < n; ++k) {
-        A.pool[dst + k] = tmp[k];
-        x0 = min(x0, (int)tmp[k].bx0); y0 = min(y0, (int)tmp[k].by0);
-        x1 = max(x1, (int)tmp[k].bx1); y1 = max(y1, (int)tmp[k].by1);
-      }
-      x0 = __reduce_min_sync(0xffffffffu, x0);
-      y0 = __reduce_min_sync(0xffffffffu, y0);
-      x1 = __reduce_max_sync(0xffffffffu, x1);
-      y1 = __reduce_max_sync(0xffffffffu, y1);
-      const int tot = __shfl_sync(0xffffffffu, incl, 31);
-      if (lane == 0) {
-        ClusterRec cr;
-        cr.bx0 = (int16_t)x0; cr.by0 = (int16_t)y0; cr.bx1 = (int16_t)x1; cr.by1 = (int16_t)y1;
-        cr.tri_base = (int32_t)(tri_base + s_cnt[c]);
-        cr.tri_count = tot;
-        A.clusters[cl_base + ci] = cr;
-      }
+      for (int k = 0; k < n; ++k) A.pool[dst + k] = tmp[k];
     }
   }
+}
+
+// ------------------------------------------------------------------ binning
+
+// One CTA per (eye, view) with triangles: bins the view's triangles into the
+// screen tiles of its footprint box.  Per tile the bin holds pool indices of
+// the triangles whose pixel box overlaps it, in no particular order (the
+// per-view depth decision does not depend on order); triangles whose box
+// spans more than A.bin_max_tiles tiles go to the view's list of big ones,
+// which every tile of the view scans (only the static-scratch render caps it).  Counts, offsets and cursors live in the
+// offset pool: [ntiles + 1 absolute entry offsets][ntiles cursors].
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) bin_kernel(FrameArgs A) {
+  const int v = blockIdx.x, e = blockIdx.y;
+  ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
+  const int n = R.tri_count;
+  if (n <= 0) return;
+  __shared__ int s_warp[BLOCK / 32];
+  __shared__ long long s_off, s_ent;
+  __shared__ int s_big;
+  const int tw = A.tile_w, th = A.tile_h;
+  const int tx0 = R.bb[0] / tw, ty0 = R.bb[1] / th;
+  const int ntx = R.bb[2] / tw - tx0 + 1, nty = R.bb[3] / th - ty0 + 1;
+  const int nt = ntx * nty;
+  if (threadIdx.x == 0) {
+    const unsigned long long o = atomicAdd(A.bin_offsets_counter, (unsigned long long)(2 * nt + 1));
+    s_off = ((long long)o + 2 * nt + 1 <= A.bin_offsets_capacity) ? (long long)o : -1;
+    if (s_off < 0) atomicOr(A.error_word, kErrPoolOverflow);
+    s_big = 0;
+  }
+  __syncthreads();
+  if (s_off < 0) return;
+  int* offs = A.bin_offsets + s_off;
+  int* curs = offs + nt + 1;
+  for (int k = threadIdx.x; k <= nt; k += BLOCK) offs[k] = 0;
+  __syncthreads();
+  const TriRec* tris = A.pool + R.tri_base;
+  auto span = [&](int t, int& x0, int& y0, int& x1, int& y1) {
+    const int2 bb = *reinterpret_cast<const int2*>(tris + t);
+    x0 = max((int)(int16_t)(bb.x & 0xffff) / tw - tx0, 0);
+    y0 = max((bb.x >> 16) / th - ty0, 0);
+    x1 = min((int)(int16_t)(bb.y & 0xffff) / tw - tx0, ntx - 1);
+    y1 = min((bb.y >> 16) / th - ty0, nty - 1);
+  };
+  int my_big = 0;
+  for (int t = threadIdx.x; t < n; t += BLOCK) {
+    int x0, y0, x1, y1;
+    span(t, x0, y0, x1, y1);
+    if (x0 > x1 || y0 > y1) continue;
+    if ((x1 - x0 + 1) * (y1 - y0 + 1) > A.bin_max_tiles) { ++my_big; continue; }
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) atomicAdd(&offs[y * ntx + x], 1);
+  }
+  if (my_big) atomicAdd(&s_big, my_big);
+  __syncthreads();
+  // exclusive scan of the counts in place; each thread owns a contiguous run
+  const int per = (nt + BLOCK - 1) / BLOCK;
+  const int r0 = threadIdx.x * per, r1 = min(r0 + per, nt);
+  int run = 0;
+  for (int k = r0; k < r1; ++k) run += offs[k];
+  int total;
+  int o = block_exclusive_scan(run, s_warp, total);
+  if (threadIdx.x == 0) {
+    const int need = total + s_big;
+    const unsigned long long b = atomicAdd(A.bin_entries_counter, (unsigned long long)need);
+    s_ent = ((long long)b + need <= A.bin_entries_capacity) ? (long long)b : -1;
+    if (s_ent < 0) atomicOr(A.error_word, kErrPoolOverflow);
+  }
+  __syncthreads();
+  const long long ent = s_ent;
+  if (ent < 0) return;
+  for (int k = r0; k < r1; ++k) {
+    const int c = offs[k];
+    offs[k] = (int)(ent + o);
+    curs[k] = (int)(ent + o);
+    o += c;
+  }
+  if (threadIdx.x == 0) {
+    offs[nt] = (int)(ent + total);
+    s_big = 0;
+  }
+  __syncthreads();
+  const int big_base = (int)(ent + total);
+  for (int t = threadIdx.x; t < n; t += BLOCK) {
+    int x0, y0, x1, y1;
+    span(t, x0, y0, x1, y1);
+    if (x0 > x1 || y0 > y1) continue;
+    const int idx = R.tri_base + t;
+    if ((x1 - x0 + 1) * (y1 - y0 + 1) > A.bin_max_tiles) {
+      A.bin_entries[big_base + atomicAdd(&s_big, 1)] = idx;
+      continue;
+    }
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) A.bin_entries[atomicAdd(&curs[y * ntx + x], 1)] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R.bin_off = (int32_t)s_off;
+    R.btx0 = (int16_t)tx0; R.bty0 = (int16_t)ty0;
+    R.bntx = (int16_t)ntx; R.bnty = (int16_t)nty;
+    R.big_base = big_base;
+    R.big_count = s_big;
+  }
+}
+
+cudaError_t launch_bin(const FrameArgs& a, cudaStream_t s) {
+  dim3 grid(a.n_views, a.n_eyes);
+  bin_kernel<256><<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 constexpr int kSetupBlock = 256;

@@ -75,10 +75,10 @@ def test_static_scratch_rejects_sizes_beyond_its_limits(lfmod):
     big = scene.Eye(field.eyes[0].pose, np.array([1500.0, 1500.0, 1500.0, 1500.0]), 3000, 3000)
     out = torch.empty((3000, 3000, 4), dtype=torch.float32, device="cuda")
     assert _call_static(lfmod, r, big, out) == 7  # LF_ERR_CAPACITY
-    assert b"16384" in r.lib.lf_last_error(r.ctx)
+    assert b"8192" in r.lib.lf_last_error(r.ctx)
     r.close()
     # more views than the static scratch holds
-    n = 65
+    n = 33
     rng = np.random.default_rng(1)
     poses = np.stack([scene.pose_array(np.eye(3), (0.0, 0.0, 0.01 * k)) for k in range(n)])
     intr = np.tile(scene.intrinsics_for_fov(8, 8, 90.0), (n, 1))
@@ -91,5 +91,5 @@ def test_static_scratch_rejects_sizes_beyond_its_limits(lfmod):
     small = scene.Eye(scene.pose_array(np.eye(3), (0.0, 0.0, 0.0)), np.array([8.0, 8.0, 8.0, 8.0]), 16, 16)
     out = torch.empty((16, 16, 4), dtype=torch.float32, device="cuda")
     assert _call_static(lfmod, r, small, out) == 7
-    assert b"64 views" in r.lib.lf_last_error(r.ctx)
+    assert b"32 views" in r.lib.lf_last_error(r.ctx)
     r.close()
