@@ -487,6 +487,15 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& tot
 // the 4x4 cells of a cluster read 16 different banks.
 __host__ __device__ inline int vertex_row_stride(int G) { return G + ((36 - G % 32) % 32); }
 
+// One CTA per (eye, view) whose disk footprint reaches the eye.  Per band of
+// grid rows: (1) the band's vertices go to eye space with outcodes against the
+// padded footprint; (2) warps walk the 4x4-cell clusters, skip clusters whose
+// vertices all lie beyond one side (or behind the eye), and append the
+// triangles that pass their own outcode test to a candidate list; (3) all
+// threads share the candidates for the full set-up (snap, clip, orientation,
+// fill rule).  Pass 1 counts the records, one atomic reserves the view's
+// segment, pass 2 writes them.  The order inside a segment does not matter:
+// the raster's depth decision within a view is order-independent.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_rows) {
   constexpr int NW = BLOCK / 32;
@@ -501,14 +510,15 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
   extern __shared__ __align__(16) unsigned char smem[];
   const int RS = vertex_row_stride(G);
   const int nv_band = (band_rows + 1) * RS;
-  const int ncl_side = (G - 1 + kClusterCells - 1) / kClusterCells;
-  int* s_cnt = reinterpret_cast<int*>(smem);          // kept triangles per cluster, then their prefix
+  const int n_cell = G - 1;
   VtxSmem S;
-  S.x = reinterpret_cast<float*>(s_cnt + ncl_side * ncl_side);
+  S.x = reinterpret_cast<float*>(smem);
   S.y = S.x + nv_band;
   S.z = S.y + nv_band;
-  S.oc = reinterpret_cast<uint8_t*>(S.z + nv_band);
+  uint16_t* s_cand = reinterpret_cast<uint16_t*>(S.z + nv_band);  // candidate triangles of the band
+  S.oc = reinterpret_cast<uint8_t*>(s_cand + 2 * n_cell * band_rows);
   __shared__ int s_warp[NW];
+  __shared__ int s_ncand, s_pos;
   __shared__ long long s_tri_base;
 
   SetupCtx C;
@@ -524,15 +534,19 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
   const float* ta = A.tables.a + (int64_t)v * G;
   const float* tb = A.tables.b + (int64_t)v * G;
   const ViewStatic& V = A.views[v];
-  const int n_cell = G - 1;
   const int ncl = (n_cell + kClusterCells - 1) / kClusterCells;  // clusters per side
   const int n_bands = (n_cell + band_rows - 1) / band_rows;
 
+  // q / G without an integer division: (q + 1/2) / G is at least 1/(2G) away
+  // from an integer and the float product errs by under 3e-5 for q < 2^17.
+  const float inv_G = 1.0f / (float)G;
+  const float inv_ncl = 1.0f / (float)ncl;
   auto load_band = [&](int k0, int k1) {  // vertex rows k0 .. k1 inclusive
     const int nq = (k1 - k0 + 1) * G;
 #pragma unroll 4
     for (int q = threadIdx.x; q < nq; q += BLOCK) {
-      const int k = k0 + q / G, j = q % G;
+      const int kq = (int)(((float)q + 0.5f) * inv_G);
+      const int k = k0 + kq, j = q - kq * G;
       const int64_t gi = ((int64_t)v * G + k) * G + j;
       float z;
       if (A.mesh_format == LF_MESH_F16_OFFSET)
@@ -549,91 +563,123 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
         oc = (uint8_t)((ux < oxl * ez ? 1 : 0) | (ux > oxr * ez ? 2 : 0) | (uy < oyt * ez ? 4 : 0) |
                        (uy > oyb * ez ? 8 : 0));
       }
-      const int slot = (k - k0) * RS + j;
+      const int slot = kq * RS + j;
       S.x[slot] = ex; S.y[slot] = ey; S.z[slot] = ez;
       S.oc[slot] = oc;
     }
   };
-  // Lane l of a warp owns triangle (cell l/2 of the 4x4 block, half l%2) of cluster c.
-  auto cluster_tri = [&](int c, int k0, TriRec* tmp) -> int {
-    const int cl_x = c % ncl, cl_y = c / ncl;
-    const int cell = lane >> 1, half = lane & 1;
-    const int j = cl_x * kClusterCells + (cell & 3), k = cl_y * kClusterCells + (cell >> 2);
-    if (j >= n_cell || k >= n_cell) return 0;
-    const int id = 2 * (k * n_cell + j) + half;
-    const int r0 = (k - k0) * RS;
-    if (half == 0) return setup_parent(id, r0 + j, r0 + j + 1, r0 + RS + j, S, C, tmp);
-    return setup_parent(id, r0 + j + 1, r0 + RS + j + 1, r0 + RS + j, S, C, tmp);
+  // vertex slots of band-local triangle (kk, j, half)
+  auto tri_slots = [&](int kk, int j, int half, int& q0, int& q1, int& q2) {
+    const int r0 = kk * RS;
+    if (half == 0) { q0 = r0 + j; q1 = r0 + j + 1; q2 = r0 + RS + j; }
+    else { q0 = r0 + j + 1; q1 = r0 + RS + j + 1; q2 = r0 + RS + j; }
+  };
+  // Warps walk the band's clusters; surviving triangles join the candidate list.
+  auto gather = [&](int k0, int k1) {
+    if (threadIdx.x == 0) s_ncand = 0;
+    __syncthreads();
+    const int cy0 = k0 / kClusterCells, cy1 = (k1 + kClusterCells - 1) / kClusterCells;
+    const int c0 = cy0 * ncl, c1 = cy1 * ncl;
+    for (int c = c0 + warp; c < c1; c += NW) {
+      const int cl_y = (int)(((float)c + 0.5f) * inv_ncl), cl_x = c - cl_y * ncl;
+      // AND of the outcodes of the cluster's (up to) 5 x 5 vertices: a bit set
+      // here is set on every vertex of every triangle of the cluster
+      uint32_t oca = 0xffu;
+      if (lane < 25) {
+        const int k = min(cl_y * kClusterCells + lane / 5, n_cell), j = min(cl_x * kClusterCells + lane % 5, n_cell);
+        oca = S.oc[(k - k0) * RS + j];
+      }
+      if (__reduce_and_sync(0xffffffffu, oca) != 0u) continue;
+      const int cell = lane >> 1, half = lane & 1;
+      const int j = cl_x * kClusterCells + (cell & 3), k = cl_y * kClusterCells + (cell >> 2);
+      bool keep = false;
+      if (j < n_cell && k < k1) {
+        int q0, q1, q2;
+        tri_slots(k - k0, j, half, q0, q1, q2);
+        keep = (S.oc[q0] & S.oc[q1] & S.oc[q2]) == 0;
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      int base = 0;
+      if (lane == 0 && bal) base = atomicAdd(&s_ncand, __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (keep) s_cand[base + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)((((k - k0) * n_cell + j) << 1) | half);
+    }
+    __syncthreads();
+  };
+  auto setup_cand = [&](int k0, int code, TriRec* tmp) -> int {
+    const int half = code & 1, cell = code >> 1;
+    const int kk = (int)(((float)cell + 0.5f) / (float)n_cell);
+    const int j = cell - kk * n_cell;
+    int q0, q1, q2;
+    tri_slots(kk, j, half, q0, q1, q2);
+    const int id = 2 * ((k0 + kk) * n_cell + j) + half;
+    return setup_parent(id, q0, q1, q2, S, C, tmp);
   };
 
-  // Pass 1: kept triangles per cluster.
+  // Pass 1: count the kept records.
+  int my_count = 0;
   for (int bnd = 0; bnd < n_bands; ++bnd) {
     const int k0 = bnd * band_rows, k1 = min(k0 + band_rows, n_cell);
     __syncthreads();
     load_band(k0, k1);
     __syncthreads();
-    const int c0 = (k0 / kClusterCells) * ncl, c1 = ((k1 + kClusterCells - 1) / kClusterCells) * ncl;
-    for (int c = c0 + warp; c < c1; c += NW) {
+    gather(k0, k1);
+    const int nc = s_ncand;
+    for (int i = threadIdx.x; i < nc; i += BLOCK) {
       TriRec tmp[2];
-      const int n = cluster_tri(c, k0, tmp);
-      const int tot = __reduce_add_sync(0xffffffffu, n);
-      if (lane == 0) {
-        s_cnt[c] = tot;
-      }
+      my_count += setup_cand(k0, s_cand[i], tmp);
     }
   }
-  __syncthreads();
-  // Exclusive prefix over the clusters (each thread owns a contiguous run).
-  const int n_cl = ncl * ncl;
-  const int per = (n_cl + BLOCK - 1) / BLOCK;
-  const int r0 = threadIdx.x * per, r1 = min(r0 + per, n_cl);
-  int st = 0;
-  for (int c = r0; c < r1; ++c) st += s_cnt[c];
-  int tot_t;
-  int ot = block_exclusive_scan(st, s_warp, tot_t);
-  for (int c = r0; c < r1; ++c) {
-    const int nt = s_cnt[c];
-    s_cnt[c] = ot;
-    ot += nt;
-  }
+  int total;
+  block_exclusive_scan(my_count, s_warp, total);
   if (threadIdx.x == 0) {
     long long tb_ = -1;
-    if (tot_t > 0) {
-      const unsigned long long b = atomicAdd(A.pool_counter, (unsigned long long)tot_t);
-      if ((long long)b + tot_t <= A.pool_capacity) tb_ = (long long)b;
+    if (total > 0) {
+      const unsigned long long b = atomicAdd(A.pool_counter, (unsigned long long)total);
+      if ((long long)b + total <= A.pool_capacity) tb_ = (long long)b;
       else atomicOr(A.error_word, kErrPoolOverflow);
     }
     s_tri_base = tb_;
+    s_pos = 0;
     R.tri_base = tb_ < 0 ? 0 : (int32_t)tb_;
-    R.tri_count = tb_ < 0 ? 0 : tot_t;
+    R.tri_count = tb_ < 0 ? 0 : total;
   }
   __syncthreads();
   const long long tri_base = s_tri_base;
   if (tri_base < 0) return;
-  // Pass 2: write each cluster's triangles in cluster order.
+  // Pass 2: write the records (candidates of a single band are reused).
   for (int bnd = 0; bnd < n_bands; ++bnd) {
     const int k0 = bnd * band_rows, k1 = min(k0 + band_rows, n_cell);
     if (n_bands > 1) {
       __syncthreads();
       load_band(k0, k1);
       __syncthreads();
+      gather(k0, k1);
     }
-    const int c0 = (k0 / kClusterCells) * ncl, c1 = ((k1 + kClusterCells - 1) / kClusterCells) * ncl;
-    for (int c = c0 + warp; c < c1; c += NW) {
-      const int cnext = (c + 1 < ncl * ncl) ? s_cnt[c + 1] : tot_t;
-      if (cnext == s_cnt[c]) continue;  // nothing kept in this cluster
+    const int nc = s_ncand;
+    for (int i = threadIdx.x; i < nc; i += BLOCK) {
       TriRec tmp[2];
-      const int n = cluster_tri(c, k0, tmp);
-      int incl = n;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+      const int n = setup_cand(k0, s_cand[i], tmp);
+      if (n) {
+        const int pos = atomicAdd(&s_pos, n);
+        for (int k = 0; k < n; ++k) A.pool[tri_base + pos + k] = tmp[k];
       }
-      const long long dst = tri_base + s_cnt[c] + (incl - n);
-      for (int k = 0; k < n; ++k) A.pool[dst + k] = tmp[k];
     }
   }
+}
+
+constexpr int kSetupBlock = 256;
+constexpr size_t kVtxBytes = 13;  // x, y, z (4 B each) + outcode
+
+// Cell rows per band: the whole grid when it fits (vertex arrays plus a 16-bit
+// candidate per triangle), else a multiple of the cluster size.
+static int setup_band_rows(int G, size_t smem_limit) {
+  const size_t per_row = kVtxBytes * (size_t)vertex_row_stride(G) + 2 * 2 * (size_t)(G - 1);
+  int rows = (int)((smem_limit - kVtxBytes * (size_t)vertex_row_stride(G)) / per_row);
+  rows = min(rows, 32767 / max(1, G - 1));  // band-local triangle codes fit 16 bits
+  if (rows >= G - 1) return G - 1;
+  rows = (rows / kClusterCells) * kClusterCells;
+  return rows < kClusterCells ? kClusterCells : rows;
 }
 
 // ------------------------------------------------------------------ binning
@@ -745,17 +791,6 @@ cudaError_t launch_bin(const FrameArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-constexpr int kSetupBlock = 256;
-constexpr size_t kVtxBytes = 13;  // x, y, z (4 B each) + outcode
-
-// Cell rows per band: the whole grid when it fits, else a multiple of the cluster size.
-static int setup_band_rows(int G, size_t smem_limit) {
-  int rows = (int)(smem_limit / (kVtxBytes * (size_t)vertex_row_stride(G))) - 1;
-  if (rows >= G - 1) return G - 1;
-  rows = (rows / kClusterCells) * kClusterCells;
-  return rows < kClusterCells ? kClusterCells : rows;
-}
-
 cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s) {
   const size_t limit = 96 * 1024;
   static bool attr_done = false;
@@ -765,9 +800,8 @@ cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s) {
     if (err != cudaSuccess) return err;
     attr_done = true;
   }
-  const int rows = setup_band_rows(a.G, limit - 2 * sizeof(int) * 4096);
-  const int ncl = (a.G - 1 + kClusterCells - 1) / kClusterCells;
-  const size_t bytes = 2 * sizeof(int) * (size_t)ncl * ncl + (size_t)(rows + 1) * vertex_row_stride(a.G) * kVtxBytes + 64;
+  const int rows = setup_band_rows(a.G, limit);
+  const size_t bytes = (size_t)(rows + 1) * vertex_row_stride(a.G) * kVtxBytes + 2 * 2 * (size_t)(a.G - 1) * rows + 64;
   dim3 grid(a.n_views, a.n_eyes);
   tri_setup_kernel<kSetupBlock><<<grid, kSetupBlock, bytes, s>>>(a, rows);
   return cudaGetLastError();
