@@ -45,6 +45,9 @@ def parse_args():
     p.add_argument("--workload", choices=["rig", "rig256", "tiny"], default="rig")
     p.add_argument("--poses", type=int, default=8, help="distinct head poses cycled through")
     p.add_argument("--tex", choices=["f32", "u8", "bf16", "fp8"], default="f32")
+    p.add_argument("--mesh", choices=["f32", "f16"], default="f32")
+    p.add_argument("--quality-pixels", type=int, default=3000,
+                   help="random pixels per eye compared with the FP64 oracle (0 to skip)")
     p.add_argument("--tile", default="16x16")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound on the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -196,6 +199,31 @@ def cpu_baseline(lf, eye, seconds: float):
                       "per-view meshes it needs), %.1f s" % (total_pix, eye.width, eye.height, total_t)}
 
 
+def quality_vs_oracle(r, lf, head, n_pixels):
+    """Max-abs and PSNR of this storage form against the FP64 oracle on random
+    pixels of both eyes of one head pose (RGB, peak 1, pixels valid on both)."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    rng = np.random.default_rng(3)
+    out = r.render(head)
+    torch.cuda.synchronize()
+    diffs, mism = [], 0
+    for eye, img in zip(head, out):
+        pix = np.stack([rng.integers(0, eye.width, n_pixels), rng.integers(0, eye.height, n_pixels)], axis=1)
+        ref = oracle.render(lf, eye, pixels=pix)["rgba"]
+        g = img.cpu().numpy().astype(np.float64)[pix[:, 1], pix[:, 0]]
+        valid = (ref[:, 3] > 0) & (g[:, 3] > 0)
+        mism += int(np.sum((ref[:, 3] > 0) != (g[:, 3] > 0)))
+        diffs.append(g[valid][:, :3] - ref[valid][:, :3])
+    d = np.concatenate(diffs)
+    mse = float(np.mean(d * d)) if d.size else 0.0
+    return {"vs": "FP64 oracle", "pixels": int(d.shape[0]), "max_abs": float(np.abs(d).max()) if d.size else 0.0,
+            "psnr_db": (10.0 * math.log10(1.0 / mse)) if mse > 0 else float("inf"), "valid_mask_mismatches": mism}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -251,12 +279,13 @@ def run_ours(args):
     lf, heads, desc = make_workload(args.workload, max(args.poses, 1), rank)
     r = lfm.Renderer(local, tile=(tw, th), timing=True)
     r.load_views(lf, tex_format=args.tex)
-    r.build_meshes(lf)
+    r.build_meshes(lf, mesh_format=args.mesh)
     stream = torch.cuda.current_stream()
     outs = [torch.empty((e.height, e.width, 4), dtype=torch.float32, device="cuda") for e in heads[0]]
     px_per_step = sum(e.width * e.height for e in heads[0])
     out_bytes = px_per_step * 16
     tex_bytes = {"f32": 16, "u8": 4, "bf16": 8, "fp8": 4}[args.tex]
+    vtx_bytes = 4 if args.mesh == "f32" else 2
 
     # Algorithmic bytes: distinct texels each stereo frame reads, plus its output.
     uniq = [r.unique_texels(h, lf.width, lf.height) for h in heads]
@@ -265,7 +294,7 @@ def run_ours(args):
         r.render(h, out=outs)
         active.append(sum(r.stats()["active_views"]))
     mean_u = statistics.mean(uniq)
-    mesh_bytes = statistics.mean(active) / 2.0 * 2 * lf.grid_n ** 2 * 4  # per eye, both eyes
+    mesh_bytes = statistics.mean(active) * lf.grid_n ** 2 * vtx_bytes  # depth grids of the active views
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -339,7 +368,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "texture_storage": args.tex, "tile": args.tile,
+        "config": {"workload": desc, "texture_storage": args.tex, "mesh_storage": args.mesh, "tile": args.tile,
                    "head_poses": len(heads), "l2": "flushed (256 MiB write) between steps, outside the timed events",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -357,6 +386,8 @@ def run_ours(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
+    if rank == 0 and args.quality_pixels > 0:
+        result["quality"] = quality_vs_oracle(r, lf, heads[0], args.quality_pixels)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(lf, heads[0][0], args.cpu_seconds)
     if rank == 0:
