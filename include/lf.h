@@ -95,7 +95,8 @@ typedef struct {
   int32_t tile_w, tile_h;   /* screen tile in pixels: 16x16, 32x8 or 8x8 [16x16] */
   int32_t max_eyes;         /* eyes per lf_render / lf_render_batch call [2] */
   int32_t timing;           /* 1: bracket each kernel with CUDA events on the call's stream [0] */
-  int64_t tri_capacity;     /* set-up triangle records per call [8 Mi] */
+  int64_t tri_capacity;     /* set-up triangle records per call [8 Mi]; the triangle
+                               bins get max(4 x this, 32 per screen tile) entries */
   float z_near;             /* eye-space near clip plane in metres [0.1] */
   int32_t pad1;
   int64_t wait_limit;       /* iteration bound on device spin waits [1<<24] */
@@ -191,7 +192,9 @@ LF_API lf_status lf_render(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, con
  * raster kernel takes (eye, tile) work items from a device queue, and the
  * whole sequence is replayed as a CUDA graph captured once per batch layout.
  * Same arguments and output as lf_render; n_eyes up to lf_config.max_eyes.
- * The graph is re-captured when the number or sizes of the eyes change.
+ * The graph is re-captured when the number or sizes of the eyes change.  With
+ * lf_config.timing set, the sequence is launched without the graph (events
+ * inside a captured graph cannot be timed) so lf_get_stats can report it.
  */
 LF_API lf_status lf_render_batch(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
                           float* const* out_rgba, void* stream);
@@ -235,6 +238,34 @@ LF_API lf_status lf_render_inspect(lf_ctx* ctx, const lf_pose* eye, const lf_int
  */
 LF_API lf_status lf_render_static(lf_ctx* ctx, const lf_pose* eye, const lf_intrinsics* intr, float* out_rgba,
                                   void* stream);
+
+/* Outcome of lf_tune_batch. */
+typedef struct {
+  int32_t tile_w, tile_h;     /* the chosen screen tile (also the size of the per-view bins) */
+  int32_t blocks_per_sm;      /* the chosen persistent raster CTAs per SM */
+  int32_t n_tried;
+  float ms;                   /* mean replay time of the chosen configuration */
+  int32_t tried_tile_w[16];
+  int32_t tried_tile_h[16];
+  int32_t tried_blocks[16];
+  float tried_ms[16];         /* mean replay time of each candidate; -1 if it overflowed */
+} lf_tuning;
+
+/*
+ * Autotune lf_render_batch for one batch layout (the number and sizes of the
+ * eyes): for each screen tile shape (16x16, 32x8, 8x8), which also sets the
+ * size of the per-view triangle bins, and each persistent raster grid (1, 2,
+ * 4 or the occupancy limit of CTAs per SM), capture the batch graph and time
+ * `replays` replays with CUDA events on `stream`; keep the fastest on the
+ * context (later lf_render, lf_render_batch and lf_render_inspect calls use
+ * its tile shape).  A candidate whose replay overflowed the per-call scratch
+ * (error word set) is recorded with time -1 and never chosen; if every one
+ * overflowed, returns LF_ERR_CAPACITY.  Arguments as for lf_render_batch; the
+ * outputs hold the last render.  Blocks until done.  No counterpart in the paper, whose tile
+ * size (64x64 image tiles, Sec. 4.2.1) is a fixed streaming unit.
+ */
+LF_API lf_status lf_tune_batch(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                               float* const* out_rgba, int32_t replays, void* stream, lf_tuning* out);
 
 /* Counters of the last render call; synchronises with its stream. */
 LF_API lf_status lf_get_stats(lf_ctx* ctx, lf_stats* out);

@@ -49,6 +49,13 @@ class Stats(ctypes.Structure):
                 ("ms_view_setup", ctypes.c_float), ("ms_tri_setup", ctypes.c_float), ("ms_raster", ctypes.c_float)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("n_tried", ctypes.c_int32), ("ms", ctypes.c_float), ("tried_tile_w", ctypes.c_int32 * 16),
+                ("tried_tile_h", ctypes.c_int32 * 16), ("tried_blocks", ctypes.c_int32 * 16),
+                ("tried_ms", ctypes.c_float * 16)]
+
+
 class FragRecord(ctypes.Structure):
     _fields_ = [("view", ctypes.c_int32), ("n_cover", ctypes.c_int32), ("winner", ctypes.c_int32),
                 ("min_id", ctypes.c_int32), ("max_id", ctypes.c_int32), ("id_hash", ctypes.c_uint32)]
@@ -59,8 +66,8 @@ FRAG_RECORD_DTYPE = np.dtype([("view", np.int32), ("n_cover", np.int32), ("winne
 
 # Every symbol include/lf.h declares.
 EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_build_view_meshes", "lf_render",
-           "lf_render_batch", "lf_render_inspect", "lf_render_static", "lf_get_stats", "lf_status_string",
-           "lf_last_error"]
+           "lf_render_batch", "lf_render_inspect", "lf_render_static", "lf_tune_batch", "lf_get_stats",
+           "lf_status_string", "lf_last_error"]
 
 _lib = None
 
@@ -88,6 +95,8 @@ def load_library(path: str = LIB_PATH):
         f = getattr(lib, name)
         f.argtypes = [vp, i32, vp, vp, vp, vp]
         f.restype = ctypes.c_int
+    lib.lf_tune_batch.argtypes = [vp, i32, vp, vp, vp, i32, vp, ctypes.POINTER(Tuning)]
+    lib.lf_tune_batch.restype = ctypes.c_int
     lib.lf_render_static.argtypes = [vp, vp, vp, vp, vp]
     lib.lf_render_static.restype = ctypes.c_int
     lib.lf_render_inspect.argtypes = [vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
@@ -221,6 +230,18 @@ class Renderer:
         self._check(self.lib.lf_render_batch(self.ctx, len(eyes), poses, intr, ptrs, _stream_handle(stream)),
                     "lf_render_batch")
         return out
+
+    def tune_batch(self, eyes, out=None, replays: int = 3, stream=None) -> dict:
+        """Autotune the batched render for this batch layout (lf_tune_batch)."""
+        poses, intr = self._eye_arrays(eyes)
+        out, ptrs = self._outputs(eyes, out)
+        t = Tuning()
+        self._check(self.lib.lf_tune_batch(self.ctx, len(eyes), poses, intr, ptrs, int(replays),
+                                           _stream_handle(stream), ctypes.byref(t)), "lf_tune_batch")
+        tried = [{"tile": (t.tried_tile_w[k], t.tried_tile_h[k]), "blocks_per_sm": t.tried_blocks[k],
+                  "ms": t.tried_ms[k]} for k in range(t.n_tried)]
+        return {"tile": (t.tile_w, t.tile_h), "blocks_per_sm": t.blocks_per_sm, "ms": t.ms, "tried": tried,
+                "out": out}
 
     def render_static(self, eye, out=None, stream=None):
         """Render one eye without allocating (lf_render_static): per-call scratch

@@ -138,9 +138,16 @@ lf_status make_layout(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_i
 int mask_words(const lf_ctx* c) { return (c->n_views + 31) / 32; }
 
 // Bin offsets take 2 ints per footprint tile per (eye, view); bin entries one
-// per (triangle, tile) pair, typically about four per set-up triangle.
-int64_t bin_offsets_capacity(const lf_ctx* c) { return c->cfg.tri_capacity / 2 + 65536; }
-int64_t bin_entries_capacity(const lf_ctx* c) { return c->cfg.tri_capacity * 4; }
+// per (triangle, tile) pair, typically about four per set-up triangle.  Both
+// also scale with the screen tiles of the call: a tile lies in the footprints
+// of about six views on the rig workloads and gathers 10-20 entries, more
+// with small tiles, so 24 offsets and 32 entries per tile leave headroom.
+int64_t bin_offsets_capacity(const lf_ctx* c, int64_t total_tiles) {
+  return std::max(c->cfg.tri_capacity / 2, 24 * total_tiles) + 65536;
+}
+int64_t bin_entries_capacity(const lf_ctx* c, int64_t total_tiles) {
+  return std::max(c->cfg.tri_capacity * 4, 32 * total_tiles);
+}
 
 lf_status ensure_scratch(lf_ctx* c, int32_t n_eyes, int32_t total_tiles) {
   LF_CUDA(c, ensure(c->eyes, sizeof(EyeParams) * (size_t)c->cfg.max_eyes));
@@ -151,8 +158,8 @@ lf_status ensure_scratch(lf_ctx* c, int32_t n_eyes, int32_t total_tiles) {
   LF_CUDA(c, ensure(c->small, 64));
   int64_t cap = c->cfg.tri_capacity;
   LF_CUDA(c, ensure(c->pool, sizeof(TriRec) * (size_t)cap));
-  LF_CUDA(c, ensure(c->bin_offsets, sizeof(int32_t) * (size_t)bin_offsets_capacity(c)));
-  LF_CUDA(c, ensure(c->bin_entries, sizeof(int32_t) * (size_t)bin_entries_capacity(c)));
+  LF_CUDA(c, ensure(c->bin_offsets, sizeof(int32_t) * (size_t)bin_offsets_capacity(c, total_tiles)));
+  LF_CUDA(c, ensure(c->bin_entries, sizeof(int32_t) * (size_t)bin_entries_capacity(c, total_tiles)));
   return LF_OK;
 }
 
@@ -195,9 +202,9 @@ FrameArgs frame_args(lf_ctx* c, const Layout& L) {
   a.pool = static_cast<TriRec*>(c->pool.p);
   a.pool_capacity = c->cfg.tri_capacity;
   a.bin_offsets = static_cast<int32_t*>(c->bin_offsets.p);
-  a.bin_offsets_capacity = bin_offsets_capacity(c);
+  a.bin_offsets_capacity = bin_offsets_capacity(c, L.total_tiles);
   a.bin_entries = static_cast<int32_t*>(c->bin_entries.p);
-  a.bin_entries_capacity = bin_entries_capacity(c);
+  a.bin_entries_capacity = bin_entries_capacity(c, L.total_tiles);
   a.bin_max_tiles = 1 << 30;  // bin every triangle into every footprint tile its box covers
   // counter block: triangles (8 B), error word, work counter, bin offsets (8 B), bin entries (8 B)
   unsigned char* sm = static_cast<unsigned char*>(c->small.p);
@@ -244,6 +251,78 @@ lf_status check_ready(lf_ctx* c) {
 }  // namespace
 
 extern "C" {
+
+lf_status lf_tune_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                        float* const* out_rgba, int32_t replays, void* stream, lf_tuning* out) {
+  lf_status st = check_ready(c);
+  if (st != LF_OK) return st;
+  if (!out || replays < 1 || replays > 1000) return fail(c, LF_ERR_INVALID_ARG, "bad tuning arguments");
+  std::memset(out, 0, sizeof(*out));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LF_CUDA(c, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(c, ce, "cudaEventCreate"); }
+  const int tiles[3][2] = {{16, 16}, {32, 8}, {8, 8}};
+  const lf_config saved = c->cfg;
+  const int saved_blocks = c->persistent_blocks;
+  float best = -1.0f;
+  int best_k = -1;
+  for (int ti = 0; ti < 3 && st == LF_OK; ++ti) {
+    int per_sm = 0;
+    cudaError_t e = raster_occupancy(tiles[ti][0], tiles[ti][1], c->tex_fmt, &per_sm);
+    if (e != cudaSuccess) { st = cuda_fail(c, e, "raster_occupancy"); break; }
+    per_sm = std::max(1, per_sm);
+    const int cand[4] = {1, 2, 4, per_sm};
+    for (int ci = 0; ci < 4 && st == LF_OK && out->n_tried < 16; ++ci) {
+      const int bps = cand[ci];
+      if (bps > per_sm || (ci < 3 && bps == per_sm)) continue;  // each block count once
+      c->cfg.tile_w = tiles[ti][0];
+      c->cfg.tile_h = tiles[ti][1];
+      c->persistent_blocks = bps * c->sm_count;
+      // the first call captures this layout's graph; then time `replays` replays
+      if ((st = lf_render_batch(c, n_eyes, eyes, intr, out_rgba, stream)) != LF_OK) break;
+      if ((e = cudaEventRecord(e0, s)) != cudaSuccess) { st = cuda_fail(c, e, "cudaEventRecord"); break; }
+      for (int r = 0; r < replays && st == LF_OK; ++r) st = lf_render_batch(c, n_eyes, eyes, intr, out_rgba, stream);
+      if (st != LF_OK) break;
+      if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+        st = cuda_fail(c, e, "timing");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= (float)replays;
+      // a replay that overflowed its scratch skipped work: it is not a candidate
+      uint32_t err = 0;
+      if ((e = cudaMemcpy(&err, static_cast<unsigned char*>(c->small.p) + 8, 4, cudaMemcpyDeviceToHost)) !=
+          cudaSuccess) {
+        st = cuda_fail(c, e, "cudaMemcpy");
+        break;
+      }
+      const bool overflow = (err & kErrPoolOverflow) != 0;
+      const int k = out->n_tried++;
+      out->tried_tile_w[k] = tiles[ti][0];
+      out->tried_tile_h[k] = tiles[ti][1];
+      out->tried_blocks[k] = bps;
+      out->tried_ms[k] = overflow ? -1.0f : ms;
+      if (!overflow && (best < 0.0f || ms < best)) { best = ms; best_k = k; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LF_OK || best_k < 0) {
+    c->cfg = saved;
+    c->persistent_blocks = saved_blocks;
+    return st != LF_OK ? st : fail(c, LF_ERR_CAPACITY, "every configuration overflowed its scratch");
+  }
+  c->cfg.tile_w = out->tile_w = out->tried_tile_w[best_k];
+  c->cfg.tile_h = out->tile_h = out->tried_tile_h[best_k];
+  out->blocks_per_sm = out->tried_blocks[best_k];
+  c->persistent_blocks = out->blocks_per_sm * c->sm_count;
+  out->ms = best;
+  // leave the chosen layout's graph captured (and the outputs rendered with it)
+  return lf_render_batch(c, n_eyes, eyes, intr, out_rgba, stream);
+}
 
 void lf_config_default(lf_config* cfg) {
   if (!cfg) return;
@@ -502,6 +581,7 @@ lf_status lf_render_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const 
     LF_CUDA(c, raster_occupancy(c->cfg.tile_w, c->cfg.tile_h, c->tex_fmt, &per_sm));
     c->persistent_blocks = std::max(1, per_sm) * c->sm_count;
   }
+  c->persistent_blocks = std::min(c->persistent_blocks, std::max(1, L.total_tiles));
   // The graph depends on the layout and on every scratch address it names.
   std::vector<int64_t> sig = {n_eyes, L.total_tiles, c->n_views, c->G, c->tex_fmt, c->mesh_fmt,
                               (int64_t)(intptr_t)c->eyes.p, (int64_t)(intptr_t)c->eyes_f.p,
@@ -509,9 +589,22 @@ lf_status lf_render_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const 
                               (int64_t)(intptr_t)c->vrecs.p,
                               (int64_t)(intptr_t)c->masks.p, (int64_t)(intptr_t)c->pool.p,
                               (int64_t)(intptr_t)c->active.p, (int64_t)(intptr_t)c->small.p,
-                              (int64_t)(intptr_t)c->tex.p, (int64_t)(intptr_t)c->depth.p, c->persistent_blocks};
+                              (int64_t)(intptr_t)c->tex.p, (int64_t)(intptr_t)c->depth.p, c->persistent_blocks,
+                              c->cfg.tile_w, c->cfg.tile_h, c->cfg.timing};
   for (int e = 0; e < n_eyes; ++e) { sig.push_back(intr[e].width); sig.push_back(intr[e].height); }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (c->cfg.timing) {
+    // Timing mode: the same persistent sequence, launched eagerly, because CUDA
+    // events recorded inside a captured graph cannot be queried for elapsed time.
+    if ((st = stage_eyes(c, L, s)) != LF_OK) return st;
+    FrameArgs a = frame_args(c, L);
+    if ((st = enqueue_frame(c, a, false, true, s)) != LF_OK) return st;
+    c->last_stream = s;
+    c->last_eyes = n_eyes;
+    c->last_tiles = L.total_tiles;
+    c->has_call = true;
+    return LF_OK;
+  }
   if (!c->graph || sig != c->graph_sig) {
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     FrameArgs a = frame_args(c, L);

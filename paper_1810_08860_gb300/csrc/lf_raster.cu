@@ -56,7 +56,7 @@ __device__ __forceinline__ float3 texel(const void* tex, int idx, float scale) {
   } else if constexpr (FMT == LF_TEX_U8) {
     uchar4 c = __ldg(reinterpret_cast<const uchar4*>(tex) + idx);
     const float k = 1.0f / 255.0f;
-    return make_float3(c.x * k, c.y * k, c.z * k);
+    return make_float3(__fmul_rn(c.x, k), __fmul_rn(c.y, k), __fmul_rn(c.z, k));
   } else if constexpr (FMT == LF_TEX_BF16) {
     uint2 p = __ldg(reinterpret_cast<const uint2*>(tex) + idx);
     return make_float3(__uint_as_float(p.x << 16), __uint_as_float(p.x & 0xffff0000u), __uint_as_float(p.y << 16));
@@ -67,7 +67,7 @@ __device__ __forceinline__ float3 texel(const void* tex, int idx, float scale) {
     hi.__x = (__nv_fp8x2_storage_t)(p >> 16);
     float2 a = static_cast<float2>(lo);
     float2 b = static_cast<float2>(hi);
-    return make_float3(a.x * scale, a.y * scale, b.x * scale);
+    return make_float3(__fmul_rn(a.x, scale), __fmul_rn(a.y, scale), __fmul_rn(b.x, scale));
   }
 }
 
@@ -80,7 +80,7 @@ __device__ __forceinline__ float3 bilinear(const void* tex, int W, int H, float 
   u = fminf(fmaxf(u, -1.0f), (float)W);
   v = fminf(fmaxf(v, -1.0f), (float)H);
   const float fu = floorf(u), fv = floorf(v);
-  const float al = u - fu, be = v - fv;
+  const float al = __fsub_rn(u, fu), be = __fsub_rn(v, fv);
   const int iu = (int)fu, jv = (int)fv;
   const int i0 = min(max(iu, 0), W - 1), i1 = min(max(iu + 1, 0), W - 1);
   const int j0 = min(max(jv, 0), H - 1), j1 = min(max(jv + 1, 0), H - 1);
@@ -91,63 +91,54 @@ __device__ __forceinline__ float3 bilinear(const void* tex, int W, int H, float 
     const int64_t t[4] = {bit_base + r0 + i0, bit_base + r0 + i1, bit_base + r1 + i0, bit_base + r1 + i1};
     for (int k = 0; k < 4; ++k) atomicOr(&bits[t[k] >> 5], 1u << (t[k] & 31));
   }
-  float w00 = (1.0f - al) * (1.0f - be), w10 = al * (1.0f - be), w01 = (1.0f - al) * be, w11 = al * be;
-  return make_float3(w00 * c00.x + w10 * c10.x + w01 * c01.x + w11 * c11.x,
-                     w00 * c00.y + w10 * c10.y + w01 * c01.y + w11 * c11.y,
-                     w00 * c00.z + w10 * c10.z + w01 * c01.z + w11 * c11.z);
+  // explicit roundings: the same image whatever code the caller is compiled into
+  const float nal = __fsub_rn(1.0f, al), nbe = __fsub_rn(1.0f, be);
+  const float w00 = __fmul_rn(nal, nbe), w10 = __fmul_rn(al, nbe), w01 = __fmul_rn(nal, be), w11 = __fmul_rn(al, be);
+  return make_float3(__fmaf_rn(w11, c11.x, __fmaf_rn(w01, c01.x, __fmaf_rn(w10, c10.x, __fmul_rn(w00, c00.x)))),
+                     __fmaf_rn(w11, c11.y, __fmaf_rn(w01, c01.y, __fmaf_rn(w10, c10.y, __fmul_rn(w00, c00.y)))),
+                     __fmaf_rn(w11, c11.z, __fmaf_rn(w01, c01.z, __fmaf_rn(w10, c10.z, __fmul_rn(w00, c00.z)))));
 }
 
 
-constexpr int kMaxViewsPerRound = 64;   // views of one tile handled per round (bits of a 64-bit mask)
-constexpr int kWinnerBuf = 8;           // buffered depth-test winners per pixel before shading
-constexpr int kPx = 2;                  // vertically adjacent pixels per thread
+constexpr int kViewsPerRound = 32;  // views a warp handles per round (one per lane)
+constexpr int kWinnerBuf = 8;       // buffered depth-test winners per pixel before shading
+constexpr int kPx = 2;              // vertically adjacent pixels per lane
 
-template <int BLOCK>
-struct RasterSmem {
-  TileTri tri[BLOCK];
-  long long q64[BLOCK * 3];
-  float wiz[kWinnerBuf][kPx][BLOCK];
-  uint8_t wslot[kWinnerBuf][kPx][BLOCK];
-  float4 cc[kMaxViewsPerRound];
-  const void* tex[kMaxViewsPerRound];  // first texel of each listed view
-  float Hm[kMaxViewsPerRound][12];
-  float inv_r[kMaxViewsPerRound];
-  int bstart[kMaxViewsPerRound];   // this tile's bin of the view: first entry
-  int bcount[kMaxViewsPerRound];   // its length
-  int gbase[kMaxViewsPerRound];    // the view's big triangles: first entry
-  int gcount[kMaxViewsPerRound];
-  int views[kMaxViewsPerRound];
-  int off[kMaxViewsPerRound + 1];
-  int warp_cnt[BLOCK / 32];
-  unsigned any_lo, any_hi;
-  int n_views;
-  int cur_word;
-  int cur_partial;
-  uint32_t cur_bits;
-  int item;
+// A warp's private shared memory: its view table, its compacted triangles and
+// its pixels' buffered depth winners.
+struct WarpSmem {
+  TileTri tri[32];
+  long long q64[32 * 3];
+  float wiz[kWinnerBuf][kPx][32];
+  uint8_t wslot[kWinnerBuf][kPx][32];
+  float4 cc[kViewsPerRound];
+  float Hm[kViewsPerRound][12];
+  const void* tex[kViewsPerRound];
+  float inv_r[kViewsPerRound];
+  int bstart[kViewsPerRound], bcount[kViewsPerRound], gbase[kViewsPerRound], gcount[kViewsPerRound];
+  int views[kViewsPerRound];
+  int off[kViewsPerRound + 1];
 };
 
-// Warp 0: the next (up to 64) views of the tile's mask, in increasing order,
-// resuming from (cur_word, cur_bits) when the previous round stopped mid-word.
-__device__ __forceinline__ void collect_views(const uint32_t* mask, int mask_words, int* views, int& n_out,
-                                              int& cur_word, int& cur_partial, uint32_t& cur_bits) {
+// The next (up to 32) views of the tile's mask in increasing order, resuming
+// at (cur_word, cur_bits) when the previous round stopped inside a word.
+__device__ __forceinline__ int collect_views(const uint32_t* mask, int mask_words, int* views, int& cur_word,
+                                             bool& partial, uint32_t& pbits) {
   const int lane = threadIdx.x & 31;
-  int n = 0, w = cur_word;
-  bool partial = cur_partial != 0;
-  uint32_t pbits = cur_bits;
-  while (w < mask_words) {
-    const int wl = w + lane;
+  int n = 0;
+  while (cur_word < mask_words) {
+    const int wl = cur_word + lane;
     uint32_t b = 0;
-    if (wl < mask_words) b = (lane == 0 && partial) ? pbits : mask[wl];
+    if (wl < mask_words) b = (lane == 0 && partial) ? pbits : __ldg(mask + wl);
     const int c = __popc(b);
     int incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, incl, o);
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
     const int excl = incl - c;
-    const int room = kMaxViewsPerRound - n;
+    const int room = kViewsPerRound - n;
     const int take = min(max(room - excl, 0), c);
     uint32_t bb = b;
     for (int k = 0; k < take; ++k) {
@@ -158,59 +149,36 @@ __device__ __forceinline__ void collect_views(const uint32_t* mask, int mask_wor
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     if (total <= room) {
       n += total;
-      w += 32;
+      cur_word += 32;
       partial = false;
       continue;
     }
     const unsigned over = __ballot_sync(0xffffffffu, incl > room);
     const int L = __ffs(over) - 1;
     pbits = __shfl_sync(0xffffffffu, bb, L);
-    n = kMaxViewsPerRound;
-    w += L;
+    n = kViewsPerRound;
+    cur_word += L;
     partial = true;
     break;
   }
-  n_out = n;
-  cur_word = w;
-  cur_partial = partial ? 1 : 0;
-  cur_bits = pbits;
+  __syncwarp();
+  return n;
 }
 
-// Ordered compaction of a block-wide predicate: returns this thread's slot
-// (valid when pred) and the total, via warp ballots and one barrier.
-template <int BLOCK>
-__device__ __forceinline__ int block_compact(bool pred, int* warp_cnt, int& total, uint32_t& ballot) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  ballot = __ballot_sync(0xffffffffu, pred);
-  if (lane == 0) warp_cnt[warp] = __popc(ballot);
-  __syncthreads();
-  int off = 0;
-  total = 0;
-#pragma unroll
-  for (int w2 = 0; w2 < BLOCK / 32; ++w2) {
-    const int c = warp_cnt[w2];
-    off += (w2 < warp) ? c : 0;
-    total += c;
-  }
-  return off + __popc(ballot & ((1u << lane) - 1u));
-}
-
-// One tile.  Per round of up to 64 views: (a) warp 0 lists the views from the
-// tile mask; (b) their records are loaded in parallel; (c) every pixel tests
-// its sphere crossing against every listed disk (one bit per view); (d) the
-// clusters of the views some pixel sees are tested against the tile, and the
-// triangles of the overlapping clusters are streamed in view order, BLOCK at
-// a time: bounding-box and edge-function tests against the tile, ballot
-// compaction into shared memory, then each pixel tests the compacted
-// triangles (warps skip triangles outside their rows or views none of their
-// pixels see); when the view changes, each pixel's winner for the finished
-// view is buffered; (e) buffered winners are shaded (bilinear fetch, weight,
-// accumulate) with both pixels' texel loads in flight together.
+// One warp's strip of a tile: TW x (2 * 32/TW) pixels, two vertically adjacent
+// pixels per lane.  The warp works alone (no block barrier): per round of up
+// to 32 views from the tile mask it (a) loads their per-eye records and this
+// tile's bin range for each, (b) tests every pixel's sphere crossing against
+// each disk (one bit per view), (c) gathers the bin entries of the views some
+// pixel of the strip sees, keeps the triangles whose box and edge functions
+// reach the strip, compacts them with a ballot and tests each against both
+// pixels, keeping the nearest fragment per view; (d) when the view changes, a
+// pixel's winner is buffered, and buffered winners are shaded (bilinear
+// fetch, weight, accumulate) with both pixels' texel loads in flight.
 template <int TW, int TH, int FMT, bool INSPECT>
-__device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * TH / kPx>& S) {
-  constexpr int BLOCK = TW * TH / kPx;
-  constexpr int ROWS_PER_WARP = (32 / TW) * kPx;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ void raster_strip(const FrameArgs& A, const int item, const int strip, WarpSmem& S) {
+  constexpr int ROWS = (32 / TW) * kPx;
+  const int lane = threadIdx.x & 31;
   int e = 0;
   while (e + 1 < A.n_eyes && A.eyes[e + 1].tile_base <= item) ++e;
   const EyeParams& E = A.eyes[e];
@@ -218,8 +186,9 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
   const int tx = tile % E.tiles_x, ty = tile / E.tiles_x;
   const int i0 = tx * TW, j0 = ty * TH;
   const int di = lane % TW;
-  const int dj = warp * ROWS_PER_WARP + (lane / TW) * kPx;  // first of this thread's pixel rows
-  const int wrow0 = j0 + warp * ROWS_PER_WARP, wrow1 = wrow0 + ROWS_PER_WARP - 1;
+  const int dj0 = strip * ROWS;                      // strip rows, tile-relative
+  const int dj = dj0 + (lane / TW) * kPx;            // this lane's first row, tile-relative
+  const int wrow0 = j0 + dj0, wrow1 = wrow0 + ROWS - 1;
   const int pi = i0 + di;
   const EyeFloat& EF = A.eyes_f[e];
   const float ex = __fdiv_rn(__fsub_rn(__fadd_rn((float)pi, 0.5f), EF.cx), EF.fx);
@@ -260,37 +229,19 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
     n_rec[q] = 0;
   }
 
-  if (tid == 0) {
-    S.cur_word = 0;
-    S.cur_partial = 0;
-    S.cur_bits = 0;
-  }
-  __syncthreads();
+  int cur_word = 0;
+  bool partial = false;
+  uint32_t pbits = 0;
   for (;;) {
-    // ---- (a) views of this round, in increasing id order
-    if (warp == 0) {
-      int n, w = S.cur_word, part = S.cur_partial;
-      uint32_t bits = S.cur_bits;
-      collect_views(mask, A.mask_words, S.views, n, w, part, bits);
-      if (lane == 0) {
-        S.n_views = n; S.cur_word = w; S.cur_partial = part; S.cur_bits = bits;
-        S.any_lo = 0u; S.any_hi = 0u;
-      }
-    }
-    __syncthreads();
-    const int nv = S.n_views;
+    // ---- the next round of views, and their records
+    const int nv = collect_views(mask, A.mask_words, S.views, cur_word, partial, pbits);
     if (nv == 0) break;
-    // ---- (b) their per-eye records
-    for (int sl = tid; sl < nv; sl += BLOCK) {
-      const ViewRec& VR = A.vrecs[(int64_t)e * A.n_views + S.views[sl]];
-      S.cc[sl] = *reinterpret_cast<const float4*>(VR.cc);
-      S.inv_r[sl] = VR.inv_r;
-      {
-        const int64_t off = (int64_t)S.views[sl] * tex_per_view;
-        const char* base = static_cast<const char*>(A.textures);
-        S.tex[sl] = base + off * (FMT == LF_TEX_F32 ? 16 : FMT == LF_TEX_BF16 ? 8 : 4);
-      }
-      // this tile's bin of the view, and the view's big triangles
+    if (lane < nv) {
+      const ViewRec& VR = A.vrecs[(int64_t)e * A.n_views + S.views[lane]];
+      S.cc[lane] = *reinterpret_cast<const float4*>(VR.cc);
+      S.inv_r[lane] = VR.inv_r;
+      const char* base = static_cast<const char*>(A.textures);
+      S.tex[lane] = base + (int64_t)S.views[lane] * tex_per_view * (FMT == LF_TEX_F32 ? 16 : FMT == LF_TEX_BF16 ? 8 : 4);
       int b0 = 0, bn = 0, g0 = 0, gn = 0;
       if (VR.bin_off >= 0) {
         const int lx = tx - VR.btx0, ly = ty - VR.bty0;
@@ -302,63 +253,47 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
         g0 = VR.big_base;
         gn = VR.big_count;
       }
-      S.bstart[sl] = b0;
-      S.bcount[sl] = bn;
-      S.gbase[sl] = g0;
-      S.gcount[sl] = gn;
+      S.bstart[lane] = b0;
+      S.bcount[lane] = bn;
+      S.gbase[lane] = g0;
+      S.gcount[lane] = gn;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) S.Hm[sl][k] = VR.Hm[k];
+      for (int k = 0; k < 12; ++k) S.Hm[lane][k] = VR.Hm[k];
     }
-    __syncthreads();
-    // ---- (c) disk membership of each pixel's sphere crossing, one bit per view
-    unsigned long long inmask[kPx];
+    __syncwarp();
+    // ---- disk membership of each pixel's sphere crossing, one bit per view
+    uint32_t inmask[kPx];
 #pragma unroll
     for (int q = 0; q < kPx; ++q) {
-      inmask[q] = 0ull;
+      inmask[q] = 0u;
       if (has_p[q]) {
         for (int sl = 0; sl < nv; ++sl) {
           const float4 cc = S.cc[sl];
           const float dx = __fsub_rn(p[q][0], cc.x), dy = __fsub_rn(p[q][1], cc.y), dz = __fsub_rn(p[q][2], cc.z);
-          if (dot3_rn(dx, dy, dz, dx, dy, dz) < cc.w) inmask[q] |= 1ull << sl;
+          if (dot3_rn(dx, dy, dz, dx, dy, dz) < cc.w) inmask[q] |= 1u << sl;
         }
       }
     }
-    unsigned long long wmask;  // views some pixel of this warp sees
-    {
-      unsigned long long m = 0ull;
+    uint32_t wmask = inmask[0];
 #pragma unroll
-      for (int q = 0; q < kPx; ++q) m |= inmask[q];
-      const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)m);
-      const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(m >> 32));
-      wmask = ((unsigned long long)hi << 32) | lo;
-      if (lane == 0) {
-        if (lo) atomicOr(&S.any_lo, lo);
-        if (hi) atomicOr(&S.any_hi, hi);
-      }
-    }
-    __syncthreads();
-    const unsigned long long any = ((unsigned long long)S.any_hi << 32) | S.any_lo;
-    for (int sl = tid; sl < nv; sl += BLOCK)
-      if ((any >> sl) & 1ull) A.active[(int64_t)e * A.n_views + S.views[sl]] = 1;
-    if (warp == 0) {
-      // exclusive prefix of the seen views' entry counts (slots lane and lane + 32)
-      const int c0 = (lane < nv && ((any >> lane) & 1ull)) ? S.bcount[lane] + S.gcount[lane] : 0;
-      const int c1 = (lane + 32 < nv && ((any >> (lane + 32)) & 1ull)) ? S.bcount[lane + 32] + S.gcount[lane + 32] : 0;
-      int s0 = c0, s1 = c1;
+    for (int q = 1; q < kPx; ++q) wmask |= inmask[q];
+    wmask = __reduce_or_sync(0xffffffffu, wmask);  // views some pixel of the strip sees
+    if (lane < nv && ((wmask >> lane) & 1u)) A.active[(int64_t)e * A.n_views + S.views[lane]] = 1;
+    {
+      // exclusive prefix of the seen views' entry counts
+      const int c = (lane < nv && ((wmask >> lane) & 1u)) ? S.bcount[lane] + S.gcount[lane] : 0;
+      int incl = c;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const int y0 = __shfl_up_sync(0xffffffffu, s0, o), y1 = __shfl_up_sync(0xffffffffu, s1, o);
-        if (lane >= o) { s0 += y0; s1 += y1; }
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
       }
-      const int t0 = __shfl_sync(0xffffffffu, s0, 31), t1 = __shfl_sync(0xffffffffu, s1, 31);
-      S.off[lane] = s0 - c0;
-      S.off[lane + 32] = t0 + s1 - c1;
-      if (lane == 0) S.off[kMaxViewsPerRound] = t0 + t1;
+      S.off[lane] = incl - c;
+      if (lane == 31) S.off[32] = incl;
     }
-    __syncthreads();
-    const int T = S.off[nv];
+    __syncwarp();
+    const int T = S.off[32];
 
-    // ---- (d) triangles of the seen views, in view order
     int cur = -1;
     int best_id[kPx], wcount[kPx], next_emit[kPx];
     float best_iz[kPx];
@@ -369,21 +304,20 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
       best_id[q] = -1; best_iz[q] = 0.0f; wcount[q] = 0; next_emit[q] = 0;
       n_cover[q] = 0; min_id[q] = 0x7fffffff; max_id[q] = -1; hash[q] = 0u;
     }
-
-    // (e) shade the buffered winners in view order, both pixels together
     auto shade_flush = [&]() {
       const int kmax = max(wcount[0], wcount[kPx - 1]);
       for (int k = 0; k < kmax; ++k) {
 #pragma unroll
         for (int q = 0; q < kPx; ++q) {
           if (k >= wcount[q]) continue;
-          const int sl = S.wslot[k][q][tid];
-          const float iz = S.wiz[k][q][tid];
+          const int sl = S.wslot[k][q][lane];
+          const float iz = S.wiz[k][q][lane];
           const float4 cc = S.cc[sl];
           const float dx = __fsub_rn(p[q][0], cc.x), dy = __fsub_rn(p[q][1], cc.y), dz = __fsub_rn(p[q][2], cc.z);
           const float d2 = dot3_rn(dx, dy, dz, dx, dy, dz);
           // the weight is a value, not a decision: fast square root
-          const float w = fmaxf(0.0f, 1.0f - (d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f) * S.inv_r[sl]);
+          const float dist = d2 > 0.0f ? __fmul_rn(d2, rsqrtf(d2)) : 0.0f;
+          const float w = fmaxf(0.0f, __fmaf_rn(-dist, S.inv_r[sl], 1.0f));
           const float* Hm = S.Hm[sl];
           const float hx = fmaf(Hm[0], px, fmaf(Hm[1], py[q], fmaf(Hm[9], iz, Hm[2])));
           const float hy = fmaf(Hm[3], px, fmaf(Hm[4], py[q], fmaf(Hm[10], iz, Hm[5])));
@@ -392,12 +326,12 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
             const int v = S.views[sl];
             const float rz = __fdividef(1.0f, hz);
             const float scale = (FMT == LF_TEX_FP8E4M3) ? A.views[v].tex_scale : 1.0f;
-            const float3 c = bilinear<FMT>(S.tex[sl], A.src_w, A.src_h, hx * rz, hy * rz, scale,
-                                           INSPECT ? A.texel_bits : nullptr, (int64_t)v * tex_per_view);
-            acc_r[q] = fmaf(w, c.x, acc_r[q]);
-            acc_g[q] = fmaf(w, c.y, acc_g[q]);
-            acc_b[q] = fmaf(w, c.z, acc_b[q]);
-            acc_w[q] += w;
+            const float3 c = bilinear<FMT>(S.tex[sl], A.src_w, A.src_h, __fmul_rn(hx, rz), __fmul_rn(hy, rz),
+                                           scale, INSPECT ? A.texel_bits : nullptr, (int64_t)v * tex_per_view);
+            acc_r[q] = __fmaf_rn(w, c.x, acc_r[q]);
+            acc_g[q] = __fmaf_rn(w, c.y, acc_g[q]);
+            acc_b[q] = __fmaf_rn(w, c.z, acc_b[q]);
+            acc_w[q] = __fadd_rn(acc_w[q], w);
           }
         }
       }
@@ -424,163 +358,157 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
       bool full = false;
 #pragma unroll
       for (int q = 0; q < kPx; ++q) {
-        if (cur >= 0 && ((inmask[q] >> cur) & 1ull)) {
+        if (cur >= 0 && ((inmask[q] >> cur) & 1u)) {
           if constexpr (INSPECT) {
             for (int sl = next_emit[q]; sl < cur; ++sl)
-              if ((inmask[q] >> sl) & 1ull) emit(q, sl, 0, -1, 0, 0, 0u);
+              if ((inmask[q] >> sl) & 1u) emit(q, sl, 0, -1, 0, 0, 0u);
             emit(q, cur, n_cover[q], best_id[q], min_id[q], max_id[q], hash[q]);
             next_emit[q] = cur + 1;
           }
           if (best_id[q] >= 0) {
-            S.wslot[wcount[q]][q][tid] = (uint8_t)cur;
-            S.wiz[wcount[q]][q][tid] = best_iz[q];
+            S.wslot[wcount[q]][q][lane] = (uint8_t)cur;
+            S.wiz[wcount[q]][q][lane] = best_iz[q];
             full |= (++wcount[q] == kWinnerBuf);
           }
         }
         if constexpr (INSPECT) {
           for (int sl = next_emit[q]; sl < upto; ++sl)
-            if ((inmask[q] >> sl) & 1ull) emit(q, sl, 0, -1, 0, 0, 0u);
+            if ((inmask[q] >> sl) & 1u) emit(q, sl, 0, -1, 0, 0, 0u);
           if (upto > next_emit[q]) next_emit[q] = upto;
         }
       }
       if (full) shade_flush();
     };
 
-    for (int f0 = 0; f0 < T; f0 += BLOCK) {
-      {
-        const int f = f0 + tid;
-        bool pred = false;
-        int sl = 0;
-        const TriRec* tr = A.pool;
-        int4 ra, rb, rc;
-        int64_t q64[3];
-        bool big = false;
-        if (f < T) {
-          int lo = 0, hi = nv;
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (S.off[mid] <= f) lo = mid;
-            else hi = mid;
-          }
-          sl = lo;
-          const int k = f - S.off[sl];
-          const int idx = k < S.bcount[sl] ? A.bin_entries[S.bstart[sl] + k]
-                                           : A.bin_entries[S.gbase[sl] + (k - S.bcount[sl])];
-          tr = A.pool + idx;
-          ra = __ldg(reinterpret_cast<const int4*>(tr));       // bbox, x0, x1
-          const int bx0 = (int16_t)(ra.x & 0xffff), by0 = ra.x >> 16;
-          const int bx1 = (int16_t)(ra.y & 0xffff), by1 = ra.y >> 16;
-          pred = bx0 <= i0 + TW - 1 && bx1 >= i0 && by0 <= j0 + TH - 1 && by1 >= j0;
-          if (pred) {
-            rb = __ldg(reinterpret_cast<const int4*>(tr) + 1);   // x2, y0, y1, y2
-            rc = __ldg(reinterpret_cast<const int4*>(tr) + 2);   // ia, ib, ic, id_tl
-            const int32_t X[3] = {ra.z, ra.w, rb.x};
-            const int32_t Y[3] = {rb.y, rb.z, rb.w};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              const int k1 = (k + 1) % 3;
-              const int64_t DX = (int64_t)X[k1] - X[k], DY = (int64_t)Y[k1] - Y[k];
-              const int64_t Ev = DX * (P0y - Y[k]) - DY * (P0x - X[k]) + ((rc.w >> k) & 1) - 1;
-              q64[k] = Ev >> 8;  // floor division by 256
-              big |= (DX >= kBigEdge || DX <= -kBigEdge || DY >= kBigEdge || DY <= -kBigEdge);
-              // largest value of this edge over the tile's pixel centres; < 0 rejects the tile
-              const int64_t emax = q64[k] + max((int64_t)0, -DY * (TW - 1)) + max((int64_t)0, DX * (TH - 1));
-              pred &= emax >= 0;
-            }
-          }
+    // ---- triangles of the seen views from this tile's bins, in view order
+    for (int f0 = 0; f0 < T; f0 += 32) {
+      const int f = f0 + lane;
+      bool pred = false;
+      int sl = 0;
+      int4 ra, rb, rc;
+      int64_t q64[3];
+      bool big = false;
+      if (f < T) {
+        int lo = 0, hi = nv;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (S.off[mid] <= f) lo = mid;
+          else hi = mid;
         }
-        int n_list;
-        uint32_t ballot;
-        const int pos = block_compact<BLOCK>(pred, S.warp_cnt, n_list, ballot);
+        sl = lo;
+        const int k = f - S.off[sl];
+        const int idx = k < S.bcount[sl] ? __ldg(A.bin_entries + S.bstart[sl] + k)
+                                         : __ldg(A.bin_entries + S.gbase[sl] + (k - S.bcount[sl]));
+        const TriRec* tr = A.pool + idx;
+        ra = __ldg(reinterpret_cast<const int4*>(tr));       // bbox, x0, x1
+        const int bx0 = (int16_t)(ra.x & 0xffff), by0 = ra.x >> 16;
+        const int bx1 = (int16_t)(ra.y & 0xffff), by1 = ra.y >> 16;
+        pred = bx0 <= i0 + TW - 1 && bx1 >= i0 && by0 <= wrow1 && by1 >= wrow0;
         if (pred) {
+          rb = __ldg(reinterpret_cast<const int4*>(tr) + 1);   // x2, y0, y1, y2
+          rc = __ldg(reinterpret_cast<const int4*>(tr) + 2);   // ia, ib, ic, id_tl
           const int32_t X[3] = {ra.z, ra.w, rb.x};
           const int32_t Y[3] = {rb.y, rb.z, rb.w};
-          TileTri tt;
-          tt.q0 = (int32_t)max(min(q64[0], (int64_t)kQClamp), -(int64_t)kQClamp);
-          tt.q1 = (int32_t)max(min(q64[1], (int64_t)kQClamp), -(int64_t)kQClamp);
-          tt.q2 = (int32_t)max(min(q64[2], (int64_t)kQClamp), -(int64_t)kQClamp);
-          tt.id = (rc.w >> 3) | (big ? (int32_t)0x80000000 : 0);
-          tt.a0 = Y[0] - Y[1]; tt.b0 = X[1] - X[0];
-          tt.a1 = Y[1] - Y[2]; tt.b1 = X[2] - X[1];
-          tt.a2 = Y[2] - Y[0]; tt.b2 = X[0] - X[2];
-          tt.ia = __int_as_float(rc.x); tt.ib = __int_as_float(rc.y); tt.ic = __int_as_float(rc.z);
-          tt.pad[0] = sl;
-          tt.pad[1] = ra.x >> 16;                 // first bbox row
-          tt.pad[2] = ra.y >> 16;                 // last bbox row
-          S.tri[pos] = tt;
-          if (big) {
-            S.q64[pos * 3 + 0] = q64[0];
-            S.q64[pos * 3 + 1] = q64[1];
-            S.q64[pos * 3 + 2] = q64[2];
+#pragma unroll
+          for (int k2 = 0; k2 < 3; ++k2) {
+            const int k1 = (k2 + 1) % 3;
+            const int64_t DX = (int64_t)X[k1] - X[k2], DY = (int64_t)Y[k1] - Y[k2];
+            const int64_t Ev = DX * (P0y - Y[k2]) - DY * (P0x - X[k2]) + ((rc.w >> k2) & 1) - 1;
+            q64[k2] = Ev >> 8;  // floor division by 256
+            big |= (DX >= kBigEdge || DX <= -kBigEdge || DY >= kBigEdge || DY <= -kBigEdge);
+            // largest value of this edge over the strip's pixel centres; < 0 rejects the strip
+            const int64_t emax = q64[k2] + max((int64_t)0, -DY * (TW - 1)) +
+                                 max(DX * (int64_t)dj0, DX * (int64_t)(dj0 + ROWS - 1));
+            pred &= emax >= 0;
           }
         }
-        __syncthreads();
-        for (int t = 0; t < n_list; ++t) {
-          const int4 w0 = *reinterpret_cast<const int4*>(&S.tri[t]);           // q0 q1 q2 id
-          const int4 w3 = *(reinterpret_cast<const int4*>(&S.tri[t]) + 3);     // ic, slot, row0, row1
-          const int tsl = w3.y;
-          if (tsl != cur) {
-            finalize(tsl);
-            cur = tsl;
-#pragma unroll
-            for (int q = 0; q < kPx; ++q) {
-              best_id[q] = -1;
-              best_iz[q] = 0.0f;
-              if constexpr (INSPECT) {
-                n_cover[q] = 0; min_id[q] = 0x7fffffff; max_id[q] = -1; hash[q] = 0u;
-              }
-            }
-          }
-          // warp-uniform skips: no pixel of the warp sees the view, or the
-          // triangle's rows miss the warp's rows
-          if (!((wmask >> tsl) & 1ull) || w3.w < wrow0 || w3.z > wrow1) continue;
-          const int4 w1 = *(reinterpret_cast<const int4*>(&S.tri[t]) + 1);     // a0 b0 a1 b1
-          const int4 w2 = *(reinterpret_cast<const int4*>(&S.tri[t]) + 2);     // a2 b2 ia ib
-          const int id = w0.w & 0x7fffffff;
-          const float ia = __int_as_float(w2.z), ib = __int_as_float(w2.w), ic = __int_as_float(w3.x);
-          bool cov[kPx];
-          if (w0.w >= 0) {
-            int k0 = w0.x + w1.x * di + w1.y * dj;
-            int k1 = w0.y + w1.z * di + w1.w * dj;
-            int k2 = w0.z + w2.x * di + w2.y * dj;
-#pragma unroll
-            for (int q = 0; q < kPx; ++q) {
-              cov[q] = (k0 | k1 | k2) >= 0;
-              k0 += w1.y; k1 += w1.w; k2 += w2.y;
-            }
-          } else {
-            int64_t k0 = S.q64[t * 3 + 0] + (int64_t)w1.x * di + (int64_t)w1.y * dj;
-            int64_t k1 = S.q64[t * 3 + 1] + (int64_t)w1.z * di + (int64_t)w1.w * dj;
-            int64_t k2 = S.q64[t * 3 + 2] + (int64_t)w2.x * di + (int64_t)w2.y * dj;
-#pragma unroll
-            for (int q = 0; q < kPx; ++q) {
-              cov[q] = (k0 | k1 | k2) >= 0;
-              k0 += w1.y; k1 += w1.w; k2 += w2.y;
-            }
-          }
+      }
+      const uint32_t ballot = __ballot_sync(0xffffffffu, pred);
+      const int n_list = __popc(ballot);
+      if (pred) {
+        const int pos = __popc(ballot & ((1u << lane) - 1u));
+        const int32_t X[3] = {ra.z, ra.w, rb.x};
+        const int32_t Y[3] = {rb.y, rb.z, rb.w};
+        TileTri tt;
+        tt.q0 = (int32_t)max(min(q64[0], (int64_t)kQClamp), -(int64_t)kQClamp);
+        tt.q1 = (int32_t)max(min(q64[1], (int64_t)kQClamp), -(int64_t)kQClamp);
+        tt.q2 = (int32_t)max(min(q64[2], (int64_t)kQClamp), -(int64_t)kQClamp);
+        tt.id = (rc.w >> 3) | (big ? (int32_t)0x80000000 : 0);
+        tt.a0 = Y[0] - Y[1]; tt.b0 = X[1] - X[0];
+        tt.a1 = Y[1] - Y[2]; tt.b1 = X[2] - X[1];
+        tt.a2 = Y[2] - Y[0]; tt.b2 = X[0] - X[2];
+        tt.ia = __int_as_float(rc.x); tt.ib = __int_as_float(rc.y); tt.ic = __int_as_float(rc.z);
+        tt.pad[0] = sl;
+        S.tri[pos] = tt;
+        if (big) {
+          S.q64[pos * 3 + 0] = q64[0];
+          S.q64[pos * 3 + 1] = q64[1];
+          S.q64[pos * 3 + 2] = q64[2];
+        }
+      }
+      __syncwarp();
+      for (int t = 0; t < n_list; ++t) {
+        const int4 w0 = *reinterpret_cast<const int4*>(&S.tri[t]);           // q0 q1 q2 id
+        const int4 w3 = *(reinterpret_cast<const int4*>(&S.tri[t]) + 3);     // ic, slot, -, -
+        const int tsl = w3.y;
+        if (tsl != cur) {
+          finalize(tsl);
+          cur = tsl;
 #pragma unroll
           for (int q = 0; q < kPx; ++q) {
-            if (!cov[q] || !((inmask[q] >> tsl) & 1ull)) continue;
+            best_id[q] = -1;
+            best_iz[q] = 0.0f;
             if constexpr (INSPECT) {
-              ++n_cover[q];
-              min_id[q] = min(min_id[q], id);
-              max_id[q] = max(max_id[q], id);
-              hash[q] ^= mix32((uint32_t)id);
-            }
-            const float iz = __fmaf_rn(ia, ex, __fmaf_rn(ib, ey[q], ic));
-            // nearest wins; equal depths go to the lower id, whatever the visiting order
-            if (iz > 0.0f && (best_id[q] < 0 || iz > best_iz[q] || (iz == best_iz[q] && id < best_id[q]))) {
-              best_iz[q] = iz;
-              best_id[q] = id;
+              n_cover[q] = 0; min_id[q] = 0x7fffffff; max_id[q] = -1; hash[q] = 0u;
             }
           }
         }
-        __syncthreads();
+        const int4 w1 = *(reinterpret_cast<const int4*>(&S.tri[t]) + 1);     // a0 b0 a1 b1
+        const int4 w2 = *(reinterpret_cast<const int4*>(&S.tri[t]) + 2);     // a2 b2 ia ib
+        const int id = w0.w & 0x7fffffff;
+        const float ia = __int_as_float(w2.z), ib = __int_as_float(w2.w), ic = __int_as_float(w3.x);
+        bool cov[kPx];
+        if (w0.w >= 0) {
+          int k0 = w0.x + w1.x * di + w1.y * dj;
+          int k1 = w0.y + w1.z * di + w1.w * dj;
+          int k2 = w0.z + w2.x * di + w2.y * dj;
+#pragma unroll
+          for (int q = 0; q < kPx; ++q) {
+            cov[q] = (k0 | k1 | k2) >= 0;
+            k0 += w1.y; k1 += w1.w; k2 += w2.y;
+          }
+        } else {
+          int64_t k0 = S.q64[t * 3 + 0] + (int64_t)w1.x * di + (int64_t)w1.y * dj;
+          int64_t k1 = S.q64[t * 3 + 1] + (int64_t)w1.z * di + (int64_t)w1.w * dj;
+          int64_t k2 = S.q64[t * 3 + 2] + (int64_t)w2.x * di + (int64_t)w2.y * dj;
+#pragma unroll
+          for (int q = 0; q < kPx; ++q) {
+            cov[q] = (k0 | k1 | k2) >= 0;
+            k0 += w1.y; k1 += w1.w; k2 += w2.y;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kPx; ++q) {
+          if (!cov[q] || !((inmask[q] >> tsl) & 1u)) continue;
+          if constexpr (INSPECT) {
+            ++n_cover[q];
+            min_id[q] = min(min_id[q], id);
+            max_id[q] = max(max_id[q], id);
+            hash[q] ^= mix32((uint32_t)id);
+          }
+          const float iz = __fmaf_rn(ia, ex, __fmaf_rn(ib, ey[q], ic));
+          // nearest wins; equal depths go to the lower id, whatever the visiting order
+          if (iz > 0.0f && (best_id[q] < 0 || iz > best_iz[q] || (iz == best_iz[q] && id < best_id[q]))) {
+            best_iz[q] = iz;
+            best_id[q] = id;
+          }
+        }
       }
+      __syncwarp();
     }
     finalize(nv);
     shade_flush();
-    __syncthreads();  // the view table is rewritten by the next round
+    __syncwarp();  // the view table is rewritten by the next round
   }
 #pragma unroll
   for (int q = 0; q < kPx; ++q) {
@@ -588,8 +516,8 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
     const int64_t pix = (int64_t)(j0 + dj + q) * E.W + pi;
     float4 out;
     if (acc_w[q] > 0.0f) {
-      const float inv = __fdividef(1.0f, acc_w[q]);
-      out = make_float4(acc_r[q] * inv, acc_g[q] * inv, acc_b[q] * inv, 1.0f);
+      const float inv = __frcp_rn(acc_w[q]);
+      out = make_float4(__fmul_rn(acc_r[q], inv), __fmul_rn(acc_g[q], inv), __fmul_rn(acc_b[q], inv), 1.0f);
     } else {
       out = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -601,19 +529,23 @@ __device__ void raster_tile(const FrameArgs& A, const int item, RasterSmem<TW * 
   }
 }
 
+// Non-persistent: one CTA per tile, warp w takes strip w.  Persistent: every
+// warp takes (tile, strip) work items from the device counter by itself.
 template <int TW, int TH, int FMT, bool INSPECT, bool PERSISTENT>
-__global__ void __launch_bounds__(TW * TH / kPx, 7) raster_kernel(FrameArgs A) {
-  __shared__ RasterSmem<TW * TH / kPx> S;
+__global__ void __launch_bounds__(TW * TH / kPx, 6) raster_kernel(FrameArgs A) {
+  constexpr int WARPS = TW * TH / kPx / 32;
+  __shared__ WarpSmem S[WARPS];
+  const int warp = threadIdx.x >> 5;
   if constexpr (!PERSISTENT) {
-    raster_tile<TW, TH, FMT, INSPECT>(A, blockIdx.x, S);
+    raster_strip<TW, TH, FMT, INSPECT>(A, blockIdx.x, warp, S[warp]);
   } else {
+    const int n_items = A.total_tiles * WARPS;
     for (;;) {
-      if (threadIdx.x == 0) S.item = atomicAdd(A.work_counter, 1);
-      __syncthreads();
-      const int item = S.item;
-      __syncthreads();
-      if (item >= A.total_tiles) break;
-      raster_tile<TW, TH, FMT, INSPECT>(A, item, S);
+      int item = 0;
+      if ((threadIdx.x & 31) == 0) item = atomicAdd(A.work_counter, 1);
+      item = __shfl_sync(0xffffffffu, item, 0);
+      if (item >= n_items) break;
+      raster_strip<TW, TH, FMT, INSPECT>(A, item / WARPS, item % WARPS, S[warp]);
     }
   }
 }

@@ -274,3 +274,51 @@ def test_rig_scale_sampled(lfmod, rig):
         assert st["active_views"][e] == int(sel.sum())
         assert (got["rgba"].cpu() == out[e].cpu()).all()
     r.close()
+
+
+# ---------------------------------------------------------------- batched render and its autotuner
+
+
+def test_tuned_batch_matches_per_eye_renders(lfmod, tiny):
+    import torch
+
+    rng = scene.SplitMix64(77)
+    sizes = [(64, 48), (100, 75), (33, 129), (256, 256), (17, 5), (128, 96)]
+    eyes = []
+    for (w, h) in sizes:
+        e = scene.head_pose_eyes(rng, w, h, 90.0, yaw_range=(-0.2, 0.2), pitch_deg=10.0, stereo=False)[0]
+        eyes.append(e)
+    r = lfmod.Renderer(0, max_eyes=8)
+    r.load_views(tiny)
+    r.build_meshes(tiny)
+    res = r.tune_batch(eyes, replays=2)
+    assert res["tile"] in [(16, 16), (32, 8), (8, 8)]
+    assert len(res["tried"]) >= 6 and all(t["ms"] > 0 for t in res["tried"])
+    assert res["ms"] == min(t["ms"] for t in res["tried"])
+    tuned = [o.clone() for o in res["out"]]
+    again = r.render_batch(eyes)
+    torch.cuda.synchronize()
+    for k, e in enumerate(eyes):
+        single = r.render([e])[0]
+        torch.cuda.synchronize()
+        assert torch.equal(single, tuned[k]) and torch.equal(single, again[k]), k
+    r.close()
+
+
+@pytest.mark.gpu
+def test_tuner_never_picks_an_overflowing_configuration(lfmod, tiny):
+    # a pool of one triangle record overflows in every configuration: each
+    # replay skips its set-up work, so none may be chosen however fast it ran
+    rng = scene.SplitMix64(78)
+    eyes = [scene.head_pose_eyes(rng, 96, 64, 90.0, yaw_range=(-0.2, 0.2), pitch_deg=10.0, stereo=False)[0]
+            for _ in range(3)]
+    r = lfmod.Renderer(0, max_eyes=4, tri_capacity=1)
+    r.load_views(tiny)
+    r.build_meshes(tiny)
+    with pytest.raises(lfmod.LFError) as info:
+        r.tune_batch(eyes, replays=1)
+    assert info.value.status == 7  # LF_ERR_CAPACITY
+    r.render(eyes[:1])
+    with pytest.raises(lfmod.LFError):
+        r.stats()
+    r.close()
