@@ -267,6 +267,74 @@ typedef struct {
 LF_API lf_status lf_tune_batch(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
                                float* const* out_rgba, int32_t replays, void* stream, lf_tuning* out);
 
+/* ------------------------------------------------------------------------
+ * Learned refinement.  Sec. 5 (Eq. 4-5) improves the real-time reconstruction
+ * by projecting a higher-quality offline reconstruction (denser light field
+ * images, depth maps before simplification) onto it.  A small network learns
+ * that projection in image space: for a normalised render x (RGB of an RGBA
+ * image from lf_render),
+ *     y = x + f(x),  f = conv3x3(3->32) . ReLU . conv3x3(32->32) . ReLU . conv3x3(32->3),
+ * zero padding at the image border; pixels with alpha 0 stay (0,0,0,0) and
+ * refined pixels get alpha 1.  Weights are used as BF16 on the tensor cores
+ * with FP32 accumulation; the context keeps FP32 master weights and Adam
+ * moments (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8).
+ *
+ * Parameter vector (host FP32, LF_REFINE_N_PARAMS entries, in this order):
+ *   W1[32][3][3][3], b1[32], W2[32][32][3][3], b2[32], W3[3][32][3][3], b3[3],
+ * where W[o][c][ky][kx] multiplies input channel c at pixel offset (ky-1, kx-1).
+ * Images are device pointers to n_images x height x width x 4 FP32 (RGBA,
+ * row-major, images back to back), owned by the caller.  All calls run on
+ * `stream` (NULL = legacy default stream) in order with the caller's work.
+ * ------------------------------------------------------------------------ */
+#define LF_REFINE_N_PARAMS 11011
+
+typedef enum {
+  LF_REFINE_FUSED_TC = 0,    /* one kernel, all three layers per tile, tcgen05 MMAs into TMEM */
+  LF_REFINE_MMA_LAYERS = 1   /* three launches (one per layer), mma.sync, hidden maps in HBM */
+} lf_refine_kernel;
+
+/* Load refinement weights (copied; the caller keeps `params`).  Resets the
+ * Adam moments and step to 0.  LF_ERR_INVALID_ARG on a NULL or non-finite
+ * parameter. */
+LF_API lf_status lf_load_refiner(lf_ctx* ctx, const float* params);
+
+/* Choose the inference kernel of lf_refine and lf_render_refined (default
+ * LF_REFINE_MMA_LAYERS).  Training always uses the per-layer kernels. */
+LF_API lf_status lf_refine_set_kernel(lf_ctx* ctx, lf_refine_kernel kernel);
+
+/* Copy the refiner state to host arrays of LF_REFINE_N_PARAMS floats (any may
+ * be NULL): FP32 master weights, the gradient of the last lf_refine_gradients
+ * or lf_refine_train_step call, the Adam moments; the Adam step count and the
+ * last loss.  Synchronises the device.  LF_ERR_STATE if no refiner is loaded;
+ * LF_ERR_TIMEOUT if a wait inside the fused kernel gave up since the refiner
+ * was loaded (its outputs are then incomplete). */
+LF_API lf_status lf_get_refiner(lf_ctx* ctx, float* params, float* grad, float* adam_m, float* adam_v,
+                                int32_t* step, float* last_loss);
+
+/* out = refined(in) for n_images images of width x height.  `in` and `out`
+ * must not overlap (the 3x3 windows read neighbouring tiles).  Sizes up to
+ * 2^28 pixels per image and 2^30 in all; 0 images or pixels is a no-op.
+ * LF_ERR_STATE if no refiner is loaded. */
+LF_API lf_status lf_refine(lf_ctx* ctx, int32_t n_images, int32_t width, int32_t height, const float* in_rgba,
+                           float* out_rgba, void* stream);
+
+/* Gradient of the loss with respect to the parameters, left on the context
+ * (read it with lf_get_refiner).  The loss is the mean squared error over the
+ * RGB channels of the pixels whose alpha is > 0 in both the input and the
+ * target, over all n_images pairs.  No pixel valid in both: loss 0, gradient 0. */
+LF_API lf_status lf_refine_gradients(lf_ctx* ctx, int32_t n_images, int32_t width, int32_t height,
+                                     const float* in_rgba, const float* target_rgba, void* stream);
+
+/* lf_refine_gradients followed by one Adam update with learning rate lr
+ * (0 <= lr <= 1) of the master weights and a refresh of their BF16 copies. */
+LF_API lf_status lf_refine_train_step(lf_ctx* ctx, int32_t n_images, int32_t width, int32_t height,
+                                      const float* in_rgba, const float* target_rgba, float lr, void* stream);
+
+/* lf_render followed by lf_refine of every eye (through a scratch image the
+ * context owns).  With no refiner loaded it is lf_render, the plain method. */
+LF_API lf_status lf_render_refined(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                                   float* const* out_rgba, void* stream);
+
 /* Counters of the last render call; synchronises with its stream. */
 LF_API lf_status lf_get_stats(lf_ctx* ctx, lf_stats* out);
 

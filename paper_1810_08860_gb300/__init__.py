@@ -67,7 +67,28 @@ FRAG_RECORD_DTYPE = np.dtype([("view", np.int32), ("n_cover", np.int32), ("winne
 # Every symbol include/lf.h declares.
 EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_build_view_meshes", "lf_render",
            "lf_render_batch", "lf_render_inspect", "lf_render_static", "lf_tune_batch", "lf_get_stats",
-           "lf_status_string", "lf_last_error"]
+           "lf_status_string", "lf_last_error", "lf_load_refiner", "lf_refine_set_kernel", "lf_get_refiner",
+           "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined"]
+
+REFINE_N_PARAMS = 11011
+REFINE_SHAPES = [("W1", (32, 3, 3, 3)), ("b1", (32,)), ("W2", (32, 32, 3, 3)), ("b2", (32,)),
+                 ("W3", (3, 32, 3, 3)), ("b3", (3,))]
+REFINE_KERNELS = {"fused": 0, "layers": 1}
+
+
+def init_refiner_params(seed: int, out_scale: float = 0.1) -> np.ndarray:
+    """Initial refinement weights: He-normal hidden layers, a last layer scaled
+    by out_scale (so y = x + f(x) starts close to x), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shape in REFINE_SHAPES:
+        if name.startswith("b"):
+            parts.append(np.zeros(shape))
+        else:
+            fan_in = shape[1] * 9
+            std = np.sqrt(2.0 / fan_in) * (out_scale if name == "W3" else 1.0)
+            parts.append(rng.normal(0.0, std, shape))
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
 
 _lib = None
 
@@ -103,6 +124,20 @@ def load_library(path: str = LIB_PATH):
     lib.lf_render_inspect.restype = ctypes.c_int
     lib.lf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.lf_get_stats.restype = ctypes.c_int
+    lib.lf_load_refiner.argtypes = [vp, vp]
+    lib.lf_load_refiner.restype = ctypes.c_int
+    lib.lf_refine_set_kernel.argtypes = [vp, ctypes.c_int]
+    lib.lf_refine_set_kernel.restype = ctypes.c_int
+    lib.lf_get_refiner.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.lf_get_refiner.restype = ctypes.c_int
+    lib.lf_refine.argtypes = [vp, i32, i32, i32, vp, vp, vp]
+    lib.lf_refine.restype = ctypes.c_int
+    lib.lf_refine_gradients.argtypes = [vp, i32, i32, i32, vp, vp, vp]
+    lib.lf_refine_gradients.restype = ctypes.c_int
+    lib.lf_refine_train_step.argtypes = [vp, i32, i32, i32, vp, vp, ctypes.c_float, vp]
+    lib.lf_refine_train_step.restype = ctypes.c_int
+    lib.lf_render_refined.argtypes = [vp, i32, vp, vp, vp, vp]
+    lib.lf_render_refined.restype = ctypes.c_int
     lib.lf_status_string.argtypes = [ctypes.c_int]
     lib.lf_status_string.restype = ctypes.c_char_p
     lib.lf_last_error.argtypes = [vp]
@@ -308,3 +343,70 @@ class Renderer:
         if st != LF_OK:
             raise LFError(st, "lf_get_stats: " + self.lib.lf_last_error(self.ctx).decode())
         return d
+
+    # ------------------------------------------------------------ learned refinement
+
+    def load_refiner(self, params):
+        """Load refinement weights (flat FP32 vector, REFINE_N_PARAMS) and reset Adam."""
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+        if p.size != REFINE_N_PARAMS:
+            raise ValueError("expected %d refiner parameters, got %d" % (REFINE_N_PARAMS, p.size))
+        self._check(self.lib.lf_load_refiner(self.ctx, p.ctypes.data_as(ctypes.c_void_p)), "lf_load_refiner")
+
+    def set_refine_kernel(self, kind: str):
+        """'fused' (one tcgen05 kernel per tile) or 'layers' (three mma.sync launches)."""
+        self._check(self.lib.lf_refine_set_kernel(self.ctx, REFINE_KERNELS[kind]), "lf_refine_set_kernel")
+
+    def get_refiner(self) -> dict:
+        arrs = {k: np.zeros(REFINE_N_PARAMS, np.float32) for k in ("params", "grad", "m", "v")}
+        step, loss = ctypes.c_int32(), ctypes.c_float()
+        self._check(self.lib.lf_get_refiner(self.ctx, *(arrs[k].ctypes.data_as(ctypes.c_void_p)
+                                                        for k in ("params", "grad", "m", "v")),
+                                            ctypes.byref(step), ctypes.byref(loss)), "lf_get_refiner")
+        arrs["step"], arrs["loss"] = step.value, loss.value
+        return arrs
+
+    @staticmethod
+    def _images(t):
+        import torch
+        if t.dim() == 3:
+            t = t.unsqueeze(0)
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.shape[-1] != 4:
+            raise ValueError("images must be contiguous CUDA float32 (n, H, W, 4)")
+        return t
+
+    def refine(self, images, out=None, stream=None):
+        """Refined copies of RGBA images (n, H, W, 4) or (H, W, 4) on this device (lf_refine)."""
+        import torch
+        x = self._images(images)
+        y = torch.empty_like(x) if out is None else self._images(out)
+        n, h, w, _ = x.shape
+        self._check(self.lib.lf_refine(self.ctx, n, w, h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       _stream_handle(stream)), "lf_refine")
+        return y if images.dim() == 4 else y[0]
+
+    def refine_gradients(self, inputs, targets, stream=None):
+        x, t = self._images(inputs), self._images(targets)
+        if x.shape != t.shape:
+            raise ValueError("inputs and targets differ in shape")
+        n, h, w, _ = x.shape
+        self._check(self.lib.lf_refine_gradients(self.ctx, n, w, h, ctypes.c_void_p(x.data_ptr()),
+                                                 ctypes.c_void_p(t.data_ptr()), _stream_handle(stream)),
+                    "lf_refine_gradients")
+
+    def refine_train_step(self, inputs, targets, lr: float, stream=None):
+        x, t = self._images(inputs), self._images(targets)
+        if x.shape != t.shape:
+            raise ValueError("inputs and targets differ in shape")
+        n, h, w, _ = x.shape
+        self._check(self.lib.lf_refine_train_step(self.ctx, n, w, h, ctypes.c_void_p(x.data_ptr()),
+                                                  ctypes.c_void_p(t.data_ptr()), float(lr), _stream_handle(stream)),
+                    "lf_refine_train_step")
+
+    def render_refined(self, eyes, out=None, stream=None):
+        """lf_render followed by the refinement (plain render if no refiner is loaded)."""
+        poses, intr = self._eye_arrays(eyes)
+        out, ptrs = self._outputs(eyes, out)
+        self._check(self.lib.lf_render_refined(self.ctx, len(eyes), poses, intr, ptrs, _stream_handle(stream)),
+                    "lf_render_refined")
+        return out

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -61,6 +62,16 @@ struct lf_ctx {
   // per-kernel timing of the last call (lf_config.timing)
   cudaEvent_t tev[4] = {};
   bool timed_call = false;
+  // learned refinement
+  struct Refine {
+    bool loaded = false;
+    int32_t step = 0;
+    lf_refine_kernel kernel = LF_REFINE_MMA_LAYERS;
+    Buffer state;     // FP32 params, grad, adam m, adam v (kRefineParams each)
+    Buffer packed;    // BF16 operand layouts
+    Buffer scal;      // loss (f32), valid count (i32)
+    Buffer a1, a2, gz2, gr, partial, frame;
+  } rf;
 };
 
 namespace {
@@ -404,6 +415,9 @@ void lf_destroy(lf_ctx* ctx) {
     if (ctx->ring_ev[k]) cudaEventDestroy(ctx->ring_ev[k]);
   for (int k = 0; k < 4; ++k)
     if (ctx->tev[k]) cudaEventDestroy(ctx->tev[k]);
+  for (Buffer* b : {&ctx->rf.state, &ctx->rf.packed, &ctx->rf.scal, &ctx->rf.a1, &ctx->rf.a2, &ctx->rf.gz2,
+                    &ctx->rf.gr, &ctx->rf.partial, &ctx->rf.frame})
+    release(*b);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->work_stream) cudaStreamDestroy(ctx->work_stream);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
@@ -791,3 +805,257 @@ extern "C" lf_status lf_render_static(lf_ctx* c, const lf_pose* eye, const lf_in
   // enqueue_frame zeroes the masks, counters and flags that must start at zero
   return enqueue_frame(c, a, false, false, s);
 }
+
+// ---------------------------------------------------------------------------
+// Learned refinement: y = x + f(x) on normalised renders (kernels in
+// lf_refine.cu and lf_refine_tc.cu).
+
+namespace {
+
+constexpr int kRefineSegs[3] = {896, 9248, 867};  // W1+b1, W2+b2, W3+b3
+constexpr int kRefineSegBase[3] = {kRefineOffW1, kRefineOffW2, kRefineOffW3};
+
+float* rf_params(lf_ctx* c) { return static_cast<float*>(c->rf.state.p); }
+float* rf_grad(lf_ctx* c) { return rf_params(c) + kRefineParams; }
+float* rf_m(lf_ctx* c) { return rf_params(c) + 2 * kRefineParams; }
+float* rf_v(lf_ctx* c) { return rf_params(c) + 3 * kRefineParams; }
+const __nv_bfloat16* rf_w(lf_ctx* c, int off) { return static_cast<const __nv_bfloat16*>(c->rf.packed.p) + off; }
+
+lf_status refine_check(lf_ctx* c, int32_t n, int32_t w, int32_t h, const void* a, const void* b) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (!c->rf.loaded) return fail(c, LF_ERR_STATE, "no refiner loaded");
+  if (n < 0 || w < 0 || h < 0 || (int64_t)w * h > ((int64_t)1 << 28) || (int64_t)n * w * h > ((int64_t)1 << 30))
+    return fail(c, LF_ERR_INVALID_ARG, "bad image sizes");
+  if ((int64_t)n * w * h > 0 && (!a || !b)) return fail(c, LF_ERR_INVALID_ARG, "null image pointer");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  return LF_OK;
+}
+
+lf_status refine_hidden(lf_ctx* c, int64_t n_pix, bool training) {
+  const size_t hb = sizeof(__nv_bfloat16) * 32 * (size_t)n_pix;
+  LF_CUDA(c, ensure(c->rf.a1, hb));
+  LF_CUDA(c, ensure(c->rf.a2, hb));
+  if (training) {
+    LF_CUDA(c, ensure(c->rf.gz2, hb));
+    LF_CUDA(c, ensure(c->rf.gr, sizeof(float) * 4 * (size_t)n_pix));
+  }
+  return LF_OK;
+}
+
+RefineConvArgs conv_args(int32_t n, int32_t w, int32_t h) {
+  RefineConvArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.W = w;
+  a.H = h;
+  return a;
+}
+
+// The three layer launches of the mma.sync path (inference).
+lf_status refine_layers(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float* in, float* out, cudaStream_t s) {
+  const float* prm = rf_params(c);
+  RefineConvArgs a = conv_args(n, w, h);
+  a.src_f = in;
+  a.wt = rf_w(c, kPackW1f);
+  a.bias = prm + kRefineOffB1;
+  a.out_h = static_cast<__nv_bfloat16*>(c->rf.a1.p);
+  LF_CUDA(c, launch_refine_conv(kConvInRGBA, 32, kEpiRelu, a, s));
+  a = conv_args(n, w, h);
+  a.src_h = static_cast<const __nv_bfloat16*>(c->rf.a1.p);
+  a.wt = rf_w(c, kPackW2f);
+  a.bias = prm + kRefineOffB2;
+  a.out_h = static_cast<__nv_bfloat16*>(c->rf.a2.p);
+  LF_CUDA(c, launch_refine_conv(kConvInBF16, 32, kEpiRelu, a, s));
+  a = conv_args(n, w, h);
+  a.src_h = static_cast<const __nv_bfloat16*>(c->rf.a2.p);
+  a.wt = rf_w(c, kPackW3f);
+  a.bias = prm + kRefineOffB3;
+  a.x = in;
+  a.out_f = out;
+  LF_CUDA(c, launch_refine_conv(kConvInBF16, 8, kEpiResid, a, s));
+  return LF_OK;
+}
+
+lf_status refine_apply(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float* in, float* out, cudaStream_t s) {
+  if ((int64_t)n * w * h == 0) return LF_OK;
+  if (c->rf.kernel == LF_REFINE_FUSED_TC) {
+    int32_t* err = reinterpret_cast<int32_t*>(static_cast<char*>(c->rf.scal.p) + 8);
+    LF_CUDA(c, launch_refine_fused(n, w, h, in, out, rf_params(c), static_cast<const __nv_bfloat16*>(c->rf.packed.p),
+                                   c->sm_count, err, s));
+    return LF_OK;
+  }
+  lf_status st = refine_hidden(c, (int64_t)n * w * h, false);
+  if (st != LF_OK) return st;
+  return refine_layers(c, n, w, h, in, out, s);
+}
+
+// Forward with the loss epilogue, then the backward pass into rf_grad.
+lf_status refine_backward(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float* in, const float* tgt,
+                          cudaStream_t s) {
+  const int64_t n_pix = (int64_t)n * w * h;
+  lf_status st = refine_hidden(c, n_pix, true);
+  if (st != LF_OK) return st;
+  const int tiles_x = (w + 31) / 32, tiles_y = (h + 7) / 8;
+  const int n_tiles = tiles_x * tiles_y * n;
+  const int n_ctas = std::max(1, std::min(n_tiles, 2 * c->sm_count));
+  LF_CUDA(c, ensure(c->rf.partial, sizeof(float) * (size_t)n_ctas * (896 + 9248 + 867)));
+  float* loss = static_cast<float*>(c->rf.scal.p);
+  int32_t* count = reinterpret_cast<int32_t*>(loss + 1);
+  LF_CUDA(c, cudaMemsetAsync(c->rf.scal.p, 0, 8, s));
+  LF_CUDA(c, cudaMemsetAsync(rf_grad(c), 0, sizeof(float) * kRefineParams, s));
+  if (n_pix == 0) return LF_OK;
+  LF_CUDA(c, launch_refine_count(in, tgt, n_pix, count, s));
+  const float* prm = rf_params(c);
+  auto* a1 = static_cast<__nv_bfloat16*>(c->rf.a1.p);
+  auto* a2 = static_cast<__nv_bfloat16*>(c->rf.a2.p);  // later dL/dz1
+  auto* gz2 = static_cast<__nv_bfloat16*>(c->rf.gz2.p);
+  float* gr = static_cast<float*>(c->rf.gr.p);
+  RefineConvArgs a = conv_args(n, w, h);
+  a.src_f = in; a.wt = rf_w(c, kPackW1f); a.bias = prm + kRefineOffB1; a.out_h = a1;
+  LF_CUDA(c, launch_refine_conv(kConvInRGBA, 32, kEpiRelu, a, s));
+  a = conv_args(n, w, h);
+  a.src_h = a1; a.wt = rf_w(c, kPackW2f); a.bias = prm + kRefineOffB2; a.out_h = a2;
+  LF_CUDA(c, launch_refine_conv(kConvInBF16, 32, kEpiRelu, a, s));
+  a = conv_args(n, w, h);
+  a.src_h = a2; a.wt = rf_w(c, kPackW3f); a.bias = prm + kRefineOffB3; a.x = in; a.target = tgt; a.out_f = gr;
+  a.loss = loss; a.count = count;
+  LF_CUDA(c, launch_refine_conv(kConvInBF16, 8, kEpiLoss, a, s));
+
+  RefineWgradArgs g;
+  std::memset(&g, 0, sizeof(g));
+  g.n = n; g.W = w; g.H = h; g.tiles_x = tiles_x; g.tiles_y = tiles_y; g.n_tiles = n_tiles; g.n_ctas = n_ctas;
+  float* part = static_cast<float*>(c->rf.partial.p);
+  float* part1 = part;
+  float* part2 = part1 + (size_t)n_ctas * kRefineSegs[0];
+  float* part3 = part2 + (size_t)n_ctas * kRefineSegs[1];
+  // layer 3 weights (dL/dr with a2), then dL/dz2 through layer 3's input
+  g.g_f = gr; g.a_h = a2; g.partial = part3;
+  LF_CUDA(c, launch_refine_wgrad(3, g, s));
+  a = conv_args(n, w, h);
+  a.src_f = gr; a.wt = rf_w(c, kPackW3b); a.mask = a2; a.out_h = gz2;
+  LF_CUDA(c, launch_refine_conv(kConvInRGBA, 32, kEpiMask, a, s));
+  // dL/dz1 through layer 2's input (into a2's buffer, no longer needed)
+  a = conv_args(n, w, h);
+  a.src_h = gz2; a.wt = rf_w(c, kPackW2b); a.mask = a1; a.out_h = a2;
+  LF_CUDA(c, launch_refine_conv(kConvInBF16, 32, kEpiMask, a, s));
+  g.g_f = nullptr; g.g_h = gz2; g.a_h = a1; g.partial = part2;
+  LF_CUDA(c, launch_refine_wgrad(2, g, s));
+  g.g_h = a2; g.a_h = nullptr; g.x = in; g.partial = part1;
+  LF_CUDA(c, launch_refine_wgrad(1, g, s));
+  float* parts[3] = {part1, part2, part3};
+  for (int k = 0; k < 3; ++k)
+    LF_CUDA(c, launch_refine_reduce(parts[k], n_ctas, kRefineSegs[k], rf_grad(c) + kRefineSegBase[k], s));
+  return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lf_status lf_load_refiner(lf_ctx* c, const float* params) {
+  if (!c || !params) return LF_ERR_INVALID_ARG;
+  for (int i = 0; i < kRefineParams; ++i)
+    if (!(params[i] == params[i]) || params[i] > 1e30f || params[i] < -1e30f)
+      return fail(c, LF_ERR_INVALID_ARG, "non-finite refiner parameter");
+  LF_CUDA(c, cudaSetDevice(c->device));
+  LF_CUDA(c, ensure(c->rf.state, sizeof(float) * 4 * kRefineParams));
+  LF_CUDA(c, ensure(c->rf.packed, sizeof(__nv_bfloat16) * kRefinePackedElems));
+  LF_CUDA(c, ensure(c->rf.scal, 64));
+  cudaStream_t s = c->work_stream;
+  LF_CUDA(c, cudaMemsetAsync(c->rf.state.p, 0, sizeof(float) * 4 * kRefineParams, s));
+  LF_CUDA(c, cudaMemcpyAsync(c->rf.state.p, params, sizeof(float) * kRefineParams, cudaMemcpyHostToDevice, s));
+  LF_CUDA(c, cudaMemsetAsync(c->rf.scal.p, 0, 64, s));
+  LF_CUDA(c, launch_refine_pack(rf_params(c), static_cast<__nv_bfloat16*>(c->rf.packed.p), s));
+  LF_CUDA(c, cudaStreamSynchronize(s));
+  c->rf.loaded = true;
+  c->rf.step = 0;
+  return LF_OK;
+}
+
+lf_status lf_refine_set_kernel(lf_ctx* c, lf_refine_kernel k) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (k != LF_REFINE_FUSED_TC && k != LF_REFINE_MMA_LAYERS) return fail(c, LF_ERR_INVALID_ARG, "unknown kernel");
+  c->rf.kernel = k;
+  return LF_OK;
+}
+
+lf_status lf_get_refiner(lf_ctx* c, float* params, float* grad, float* adam_m, float* adam_v, int32_t* step,
+                         float* last_loss) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (!c->rf.loaded) return fail(c, LF_ERR_STATE, "no refiner loaded");
+  LF_CUDA(c, cudaSetDevice(c->device));
+  LF_CUDA(c, cudaDeviceSynchronize());
+  float* dst[4] = {params, grad, adam_m, adam_v};
+  for (int k = 0; k < 4; ++k)
+    if (dst[k])
+      LF_CUDA(c, cudaMemcpy(dst[k], rf_params(c) + (size_t)k * kRefineParams, sizeof(float) * kRefineParams,
+                            cudaMemcpyDeviceToHost));
+  if (last_loss) LF_CUDA(c, cudaMemcpy(last_loss, c->rf.scal.p, sizeof(float), cudaMemcpyDeviceToHost));
+  if (step) *step = c->rf.step;
+  int32_t err = 0;
+  LF_CUDA(c, cudaMemcpy(&err, static_cast<char*>(c->rf.scal.p) + 8, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err) return fail(c, LF_ERR_TIMEOUT, "a wait of the fused refinement kernel gave up");
+  return LF_OK;
+}
+
+lf_status lf_refine(lf_ctx* c, int32_t n_images, int32_t width, int32_t height, const float* in_rgba,
+                    float* out_rgba, void* stream) {
+  lf_status st = refine_check(c, n_images, width, height, in_rgba, out_rgba);
+  if (st != LF_OK) return st;
+  if (in_rgba == out_rgba && (int64_t)n_images * width * height > 0)
+    return fail(c, LF_ERR_INVALID_ARG, "lf_refine cannot run in place");
+  return refine_apply(c, n_images, width, height, in_rgba, out_rgba, static_cast<cudaStream_t>(stream));
+}
+
+lf_status lf_refine_gradients(lf_ctx* c, int32_t n_images, int32_t width, int32_t height, const float* in_rgba,
+                              const float* target_rgba, void* stream) {
+  lf_status st = refine_check(c, n_images, width, height, in_rgba, target_rgba);
+  if (st != LF_OK) return st;
+  return refine_backward(c, n_images, width, height, in_rgba, target_rgba, static_cast<cudaStream_t>(stream));
+}
+
+lf_status lf_refine_train_step(lf_ctx* c, int32_t n_images, int32_t width, int32_t height, const float* in_rgba,
+                               const float* target_rgba, float lr, void* stream) {
+  lf_status st = refine_check(c, n_images, width, height, in_rgba, target_rgba);
+  if (st != LF_OK) return st;
+  if (!(lr >= 0.0f) || lr > 1.0f) return fail(c, LF_ERR_INVALID_ARG, "bad learning rate");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = refine_backward(c, n_images, width, height, in_rgba, target_rgba, s)) != LF_OK) return st;
+  const int t = c->rf.step + 1;
+  const double beta1 = 0.9, beta2 = 0.999;
+  const float c1 = (float)(1.0 / (1.0 - std::pow(beta1, t))), c2 = (float)(1.0 / (1.0 - std::pow(beta2, t)));
+  LF_CUDA(c, launch_refine_adam(rf_params(c), rf_m(c), rf_v(c), rf_grad(c), kRefineParams, lr, beta1, beta2, 1e-8f,
+                                c1, c2, s));
+  LF_CUDA(c, launch_refine_pack(rf_params(c), static_cast<__nv_bfloat16*>(c->rf.packed.p), s));
+  c->rf.step = t;
+  return LF_OK;
+}
+
+lf_status lf_render_refined(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                            float* const* out_rgba, void* stream) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (!c->rf.loaded) return lf_render(c, n_eyes, eyes, intr, out_rgba, stream);  // the plain method
+  if (n_eyes < 1 || n_eyes > c->cfg.max_eyes || !eyes || !intr || !out_rgba)
+    return fail(c, LF_ERR_INVALID_ARG, "bad eye arguments");
+  size_t total = 0;
+  std::vector<size_t> off(n_eyes);
+  for (int e = 0; e < n_eyes; ++e) {
+    if (intr[e].width < 0 || intr[e].height < 0) return fail(c, LF_ERR_INVALID_ARG, "bad eye size");
+    off[e] = total;
+    total += (size_t)intr[e].width * intr[e].height * 4;
+  }
+  LF_CUDA(c, cudaSetDevice(c->device));
+  LF_CUDA(c, ensure(c->rf.frame, sizeof(float) * std::max<size_t>(total, 4)));
+  std::vector<float*> tmp(n_eyes);
+  for (int e = 0; e < n_eyes; ++e) tmp[e] = static_cast<float*>(c->rf.frame.p) + off[e];
+  lf_status st = lf_render(c, n_eyes, eyes, intr, tmp.data(), stream);
+  if (st != LF_OK) return st;
+  for (int e = 0; e < n_eyes; ++e)
+    if ((st = refine_apply(c, 1, intr[e].width, intr[e].height, tmp[e], out_rgba[e],
+                           static_cast<cudaStream_t>(stream))) != LF_OK)
+      return st;
+  return LF_OK;
+}
+
+}  // extern "C"

@@ -19,6 +19,7 @@
 //                                 triangles spanning more than bin_max_tiles tiles
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lf.h"
@@ -157,5 +158,57 @@ cudaError_t launch_view_scale(const uint8_t* rgba8, int n_views, int64_t texels_
 // FP16-offset meshes: per-view origin z0 = min depth (views[v].depth_origin), half(z - z0) per vertex.
 cudaError_t launch_depth_offsets(const float* depth, int n_views, int per_view, void* dst_half, ViewStatic* views,
                                  cudaStream_t s);
+
+// ---------------------------------------------------------------- refinement
+// y = x + f(x), f = conv3x3(3->32) . ReLU . conv3x3(32->32) . ReLU . conv3x3(32->3).
+
+constexpr int kRefineParams = 11011;  // W1 864, b1 32, W2 9216, b2 32, W3 864, b3 3
+constexpr int kRefineOffW1 = 0, kRefineOffB1 = 864, kRefineOffW2 = 896, kRefineOffB2 = 10112;
+constexpr int kRefineOffW3 = 10144, kRefineOffB3 = 11008;
+// packed BF16 operands: w1f [32][32], w2f [9][32][32], w3f [9][8][32], w3b [32][32], w2b [9][32][32]
+// (mma.sync layers), then the tcgen05 K-major groups w1t [9][2][32][8], w2t [9][4][32][8],
+// w3t [9][4][16][8] (fused kernel)
+constexpr int kPackW1f = 0, kPackW2f = 1024, kPackW3f = 10240, kPackW3b = 12544, kPackW2b = 13568;
+constexpr int kPackTc = 22784;
+constexpr int kRefinePackedElems = 22784 + 18432;
+
+enum : int { kConvInRGBA = 0, kConvInBF16 = 1 };
+enum : int { kEpiRelu = 0, kEpiMask = 1, kEpiResid = 2, kEpiLoss = 3 };
+
+struct RefineConvArgs {
+  int32_t n, H, W;
+  const float* src_f;          // kConvInRGBA: n*H*W RGBA (channels 0..2 used)
+  const __nv_bfloat16* src_h;  // kConvInBF16: n*H*W*32
+  const __nv_bfloat16* wt;     // packed weights of this layer
+  const float* bias;           // kEpiRelu: 32; kEpiResid / kEpiLoss: 3
+  __nv_bfloat16* out_h;        // kEpiRelu / kEpiMask: n*H*W*32
+  const __nv_bfloat16* mask;   // kEpiMask: the ReLU output whose sign gates the gradient
+  const float* x;              // kEpiResid / kEpiLoss: the network input (RGBA)
+  const float* target;         // kEpiLoss: target RGBA
+  float* out_f;                // kEpiResid: refined RGBA; kEpiLoss: dL/dr (RGB, a = 0)
+  float* loss;                 // kEpiLoss: += sum of squared errors / (3 N)
+  const int32_t* count;        // kEpiLoss: N, pixels valid in input and target
+};
+
+struct RefineWgradArgs {
+  int32_t n, H, W;
+  int32_t tiles_x, tiles_y, n_tiles, n_ctas;
+  const float* g_f;            // mode 3: dL/dr RGBA
+  const __nv_bfloat16* g_h;    // modes 1, 2: dL/dz (32 channels)
+  const __nv_bfloat16* a_h;    // modes 2, 3: the layer input (32 channels)
+  const float* x;              // mode 1: the network input RGBA
+  float* partial;              // [n_ctas][segment]
+};
+
+cudaError_t launch_refine_conv(int in_mode, int cout, int epi, const RefineConvArgs& a, cudaStream_t s);
+cudaError_t launch_refine_wgrad(int mode, const RefineWgradArgs& a, cudaStream_t s);
+cudaError_t launch_refine_reduce(const float* partial, int n_rows, int seg, float* grad, cudaStream_t s);
+cudaError_t launch_refine_count(const float* x, const float* t, int64_t n_pix, int32_t* count, cudaStream_t s);
+cudaError_t launch_refine_adam(float* p, float* m, float* v, const float* g, int n, float lr, double beta1,
+                               double beta2, float eps, float c1, float c2, cudaStream_t s);
+cudaError_t launch_refine_pack(const float* params, __nv_bfloat16* w, cudaStream_t s);
+// Fused inference (lf_refine_tc.cu): all three layers per tile, tcgen05 MMAs.
+cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, const float* params,
+                                const __nv_bfloat16* packed, int sm_count, int32_t* error, cudaStream_t s);
 
 }  // namespace lfk
