@@ -45,7 +45,8 @@ def parse_args():
                         "work so the clock sampler sees the load")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["rig", "rig256", "tiny", "batch", "learned"], default="rig")
+    p.add_argument("--workload", choices=["rig", "rig256", "tiny", "batch", "learned", "refine"], default="rig")
+    p.add_argument("--refine-kernel", choices=["fused", "layers"], default="fused")
     p.add_argument("--poses", type=int, default=8, help="distinct head poses cycled through")
     p.add_argument("--tex", choices=["f32", "u8", "bf16", "fp8"], default="f32")
     p.add_argument("--mesh", choices=["f32", "f16"], default="f32")
@@ -434,6 +435,73 @@ def _psnr(a, b):
     return float(10.0 * torch.log10(1.0 / (d * d).mean()))
 
 
+def run_refine(args):
+    """The refinement alone: lf_refine of a stereo pair of 1440x1600 RGBA images
+    (smooth synthetic colour fields with 2 % holes) with seeded weights."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_08860_gb300 as lfm
+
+    rng = np.random.default_rng(5 + rank)
+    yy, xx = np.mgrid[0:1600, 0:1440].astype(np.float32)
+    imgs = np.zeros((2, 1600, 1440, 4), np.float32)
+    for k in range(2):
+        for c in range(3):
+            imgs[k, ..., c] = 0.5 + 0.3 * np.sin(rng.uniform(0.01, 0.2) * xx + rng.uniform(0.01, 0.2) * yy)
+        imgs[k, ..., 3] = (rng.uniform(size=(1600, 1440)) > 0.02).astype(np.float32)
+    imgs[..., :3] *= imgs[..., 3:4]
+    x = torch.from_numpy(imgs).cuda()
+    y = torch.empty_like(x)
+    r = lfm.Renderer(local)
+    r.load_refiner(lfm.init_refiner_params(3, out_scale=0.3))
+    r.set_refine_kernel(args.refine_kernel)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        r.refine(x, out=y)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        r.refine(x, out=y)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    r.get_refiner()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    px = 2 * 1440 * 1600
+    mean = statistics.mean(ms)
+    peak, peak_kind = measured_tensor_peak()
+    achieved = REFINE_FLOP_PER_PX * px / (mean / 1000.0) / 1e12
+    result = {
+        "metric": METRIC, "value": world * px / (mean / 1000.0) / 1e6, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "refinement only: lf_refine of 2 x 1440x1600 RGBA images (one launch), seeded "
+                               "weights", "refine_kernel": args.refine_kernel,
+                   "l2": "flushed (256 MiB write) between steps, outside the timed events"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "refine_fused_kernel" if args.refine_kernel == "fused" else "conv_mma_kernel x3",
+                     "peak_source": peak_kind + " bf16 (burst)", "flop_per_pixel": REFINE_FLOP_PER_PX},
+        "gpu_launches": (1 if args.refine_kernel == "fused" else 3) * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    r.close()
+    return 0
+
+
 def run_learned(args):
     """Learned refinement: train y = x + f(x) on pairs the method generates (the
     fast light field's render of a 256x256 crop vs a 2x2-supersampled render
@@ -778,14 +846,16 @@ def run_ours(args):
 def main():
     args = parse_args()
     if args.steps is None:
-        args.steps = 20 if args.impl == "reference" else {"rig": 2000, "batch": 60, "learned": 1000}.get(
-            args.workload, 400)
+        args.steps = 20 if args.impl == "reference" else {"rig": 2000, "batch": 60, "learned": 1000,
+                                                          "refine": 1000}.get(args.workload, 400)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "refine":
+        return run_refine(args)
     return run_ours(args)
 
 

@@ -3,27 +3,37 @@
 // stand-in for the offline projection of Sec. 5, Eq. 4-5) on the
 // fifth-generation tensor cores: tcgen05.mma from shared memory into TMEM.
 //
-// One persistent CTA per SM loops over output tiles of 26 x 30 pixels.  The
-// tile's input is held as a 32 x 36 halo of positions q = 32*hy + hx (3-pixel
-// ring), and every layer is computed over a contiguous range of q as an
-// implicit GEMM whose A rows are the positions themselves: the 3x3 tap
-// (dy, dx) is the same operand shifted by 32*dy + dx rows.  Rows whose taps
-// wrap across a halo row are computed but never read by a needed output.
-//   layer 1: 9 M-tiles of 128 positions, per tap one K = 16 MMA (3 real input
-//            channels), N = 32;
-//   layer 2: 8 M-tiles, per tap two K = 16 MMAs, N = 32;
-//   layer 3: 8 M-tiles, per tap two K = 16 MMAs, N = 16 (3 real outputs).
-// After each layer all 8 warps read the accumulators (tcgen05.ld, warp w sees
-// TMEM lanes 32*(w%4) ..), add the bias, apply ReLU, zero positions outside
-// the image (the next layer's zero padding) and store BF16 back to shared
-// memory for the next layer.  The residual add uses the FP32 input from global
-// memory.  One thread issues the MMAs and commits them to an mbarrier; every
-// wait is bounded and reports through an error flag instead of hanging.
+// One persistent CTA per SM loops over output tiles of 26 x 30 pixels.  A
+// tile's input is a 32 x 36 halo of positions q = 32*hy + hx (3-pixel ring);
+// each halo row is exactly 32 positions, i.e. one warp quadrant of TMEM lanes.
+// Every layer is an implicit GEMM over M-tiles of 128 positions (4 halo rows):
+//   D[q][kx*C + o] = sum_{ky, c} a[q + 32*(ky-1)][c] * W[o][c][ky][kx]
+// so the three kernel rows are three shifted A operands (MMAs accumulating
+// into one D) and the three kernel columns are stacked along N; the epilogue
+// finishes the convolution with two warp shuffles,
+//   out[q][o] = D[q-1][0*C + o] + D[q][1*C + o] + D[q+1][2*C + o].
+// Per M-tile: layer 1 (3 input channels padded to K = 16, N = 96) 3 MMAs,
+// layer 2 (K = 32, N = 96) 6 MMAs, layer 3 (K = 32, N = 16, 3 real outputs
+// per kernel column) 6 MMAs.  The biases ride on the MMAs: the input carries a
+// constant 1 in channel 3 that meets b1 in the centre weights, and layers 2
+// and 3 add one MMA of a constant-1 operand against a bias block.
+//
+// Roles: lane 0 of warps 8 and 9 issues the MMAs (even and odd M-tiles) into a
+// ring of 5 TMEM slots of 96 columns, committing each M-tile to the slot's
+// "full" mbarrier; warps 0-15 (four groups of 4 taking M-tiles in turn; warp
+// w reads TMEM lanes 32*(w%4) ..) wait on "full", read the accumulators, release the slot on its
+// "empty" mbarrier, combine the kernel columns, apply ReLU, zero positions outside the image
+// (the next layer's zero padding) and store BF16 rows for the next layer.  A
+// "layer done" mbarrier lets the issuer start a layer once every row of the
+// previous one is in shared memory.  The next tile's FP32 halo streams into a
+// staging buffer with cp.async while the current tile computes; the residual
+// add uses FP32 inputs loaded into registers while layer 3 runs.  Every wait
+// is bounded and reports through an error flag instead of hanging.
 //
 // Shared-memory operands use the K-major layout without swizzling: a position
-// (row) holds 8 channels in 16 contiguous bytes, rows follow each other every
-// 16 bytes (8-row core matrices 128 bytes apart), and each further group of 8
-// channels starts kGroupB bytes later.
+// (row) holds 8 channels in 16 contiguous bytes, rows follow every 16 bytes
+// (8-row core matrices 128 bytes apart), and each further group of 8 channels
+// starts kGroupB bytes later.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -35,19 +45,29 @@ namespace lfk {
 
 namespace {
 
-constexpr int kHW = 32, kHH = 36;                    // halo tile (positions)
-constexpr int kTW = kHW - 6, kTH = kHH - 6;          // 26 x 30 output pixels
-constexpr int kRows = 1280;                          // positions held per buffer (10 x 128)
-constexpr int kGroupB = kRows * 16;                  // bytes per group of 8 channels
-constexpr int kBufB = 4 * kGroupB;                   // 32 channels
-constexpr int kW1B = 9 * 1024, kW2B = 9 * 2048, kW3B = 9 * 1024;
-constexpr int kWB = kW1B + kW2B + kW3B;              // 36,864 bytes of BF16 weights
-constexpr int kSmemBytes = 2 * kBufB + kWB + 64;
-constexpr int kStart1 = kHW + 1, kTiles1 = 9;        // layer 1 rows [33, 1185)
-constexpr int kStart2 = 2 * (kHW + 1), kTiles2 = 8;  // layer 2 rows [66, 1090)
-constexpr int kStart3 = 3 * (kHW + 1), kTiles3 = 8;  // layer 3 rows [99, 1123)
+constexpr int kHW = 32, kHH = 36;            // halo tile (positions)
+constexpr int kTW = kHW - 6, kTH = kHH - 6;  // 26 x 30 output pixels
+constexpr int kRows = 1280;                  // positions held per buffer (10 x 128)
+constexpr int kGroupB = kRows * 16;          // bytes per group of 8 channels
+constexpr int kBufB = 4 * kGroupB;           // 32 channels
+// B operands: per kernel row (and K half) a block of 2 groups x N rows x 16 B
+constexpr int kW1Blk = 2 * 96 * 16, kW2Blk = 2 * 96 * 16, kW3Blk = 2 * 16 * 16;
+constexpr int kW1B = 3 * kW1Blk, kW2B = 6 * kW2Blk, kW3B = 6 * kW3Blk;
+constexpr int kB2Blk = 2 * 96 * 16, kB3Blk = 2 * 16 * 16;  // b2, b3 against the constant-1 operand
+constexpr int kWB = kW1B + kW2B + kW3B + kB2Blk + kB3Blk;  // 34,304 bytes
+constexpr int kOnesB = 2 * 128 * 16;         // A operand: channel 0 = 1 on 128 rows
+constexpr int kXsB = kHH * kHW * 16;         // FP32 RGBA halo of the next tile
+constexpr int kSlots = 5, kSlotCols = 96;    // TMEM ring
+constexpr int kNumBars = 2 * kSlots + 1;     // full[5], empty[5], layer_done
+constexpr int kSmemBytes = 2 * kBufB + kWB + kOnesB + kXsB + kNumBars * 8 + 8;
+constexpr int kStart1 = 32, kTiles1 = 9;     // layer 1 rows [32, 1184): halo rows 1..36
+constexpr int kStart2 = 64, kTiles2 = 8;     // layer 2 rows [64, 1088): halo rows 2..33
+constexpr int kStart3 = 96, kTiles3 = 8;     // layer 3 rows [96, 1120): halo rows 3..34
 constexpr uint32_t kTmemCols = 512;
-constexpr int kThreads = 256;
+constexpr int kEpiWarps = 16;                // epilogue warps: 4 groups of 4 (one warp per TMEM lane quadrant)
+constexpr int kEpiGroups = kEpiWarps / 4;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = kEpiThreads + 64;   // + two MMA warps
 constexpr int kWaitLimit = 1 << 22;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -76,8 +96,13 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ void arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   for (int it = 0; it < kWaitLimit; ++it) {
+    if ((it & 255) == 0 && *abort_flag) return false;
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -92,99 +117,94 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Barrier among the epilogue warps only (named barrier 1).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
-  uint32_t r[32];
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-__device__ __forceinline__ void tmem_ld4(uint32_t addr, float (&v)[4]) {
-  uint32_t r[4];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-__device__ __forceinline__ int tap_shift(int tap) { return (tap / 3 - 1) * kHW + (tap % 3 - 1); }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 struct FusedArgs {
   int32_t n, H, W, tiles_x, tiles_y, n_tiles;
   const float* in;
   float* out;
-  const float* bias;             // b1 (32), b2 (32), b3 (3) at their parameter offsets
-  const __nv_bfloat16* wtc;      // w1t [9][2][32][8], w2t [9][4][32][8], w3t [9][4][16][8]
-  int32_t* error;                // set to 1 if a wait gave up
+  const __nv_bfloat16* wtc;  // B operands: L1, L2, L3 blocks
+  int32_t* error;            // set to 1 if a wait gave up
 };
 
-// Hidden-layer epilogue: accumulators of M-tile rows -> bias, ReLU, zero
-// outside the image -> BF16 rows of `dst` (4 groups of 8 channels).
-__device__ __forceinline__ void hidden_epilogue(uint32_t tmem, int start, int n_mtiles, const float* bias,
-                                                unsigned char* dst, int x0, int y0, int H, int W) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int quarter = warp & 3;
-  for (int mt = warp >> 2; mt < n_mtiles; mt += 2) {
-    const int q = start + mt * 128 + quarter * 32 + lane;
-    float v[32];
-    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 32), v);
-    if (q >= kRows) continue;
-    const int hy = q >> 5, hx = q & 31;
-    const int gy = y0 - 3 + hy, gx = x0 - 3 + hx;
-    const bool inside = hy < kHH && gy >= 0 && gy < H && gx >= 0 && gx < W;
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      uint32_t w[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = g * 8 + 2 * j;
-        const float a = inside ? fmaxf(v[c] + bias[c], 0.f) : 0.f;
-        const float b = inside ? fmaxf(v[c + 1] + bias[c + 1], 0.f) : 0.f;
-        w[j] = pack2(a, b);
-      }
-      *reinterpret_cast<uint4*>(dst + g * kGroupB + q * 16) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-  }
+__device__ __forceinline__ void tile_origin(const FusedArgs& A, int tile, int& img, int& x0, int& y0) {
+  const int per_img = A.tiles_x * A.tiles_y;
+  img = tile / per_img;
+  const int rem = tile - img * per_img;
+  y0 = (rem / A.tiles_x) * kTH;
+  x0 = (rem % A.tiles_x) * kTW;
 }
+
+// Epilogue threads start copying a tile's FP32 RGBA halo into xs (zeros outside the image).
+__device__ __forceinline__ void prefetch_halo(uint32_t xs, const FusedArgs& A, int tile) {
+  int img, x0, y0;
+  tile_origin(A, tile, img, x0, y0);
+  const float4* in = reinterpret_cast<const float4*>(A.in) + (size_t)img * A.H * A.W;
+  for (int q = threadIdx.x; q < kHH * kHW; q += kEpiThreads) {
+    const int gy = y0 - 3 + (q >> 5), gx = x0 - 3 + (q & 31);
+    const bool ok = gy >= 0 && gy < A.H && gx >= 0 && gx < A.W;
+    cp_async16(xs + q * 16, ok ? static_cast<const void*>(in + (size_t)gy * A.W + gx) : static_cast<const void*>(in),
+               ok ? 16u : 0u);
+  }
+  cp_async_commit();
+}
+
+}  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* buf0 = sm;          // x (group 0), then a2
   unsigned char* buf1 = sm + kBufB;  // a1
   unsigned char* wts = sm + 2 * kBufB;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(wts + kWB);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(wts + kWB + 8);
-  __shared__ int s_abort;
-  __shared__ float s_bias[67];
+  unsigned char* ones = wts + kWB;
+  unsigned char* xs = ones + kOnesB;
+  uint64_t* full = reinterpret_cast<uint64_t*>(xs + kXsB);
+  uint64_t* empty = full + kSlots;
+  uint64_t* layer_done = empty + kSlots;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(layer_done + 1);
+  __shared__ volatile int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool issuer = warp >= kEpiWarps;
 
   // Both activation buffers start at zero (rows never written stay finite),
-  // then the weights and biases.
+  // then the weights and the constant-1 operand; the first tile's halo is already on its way.
+  if (!issuer && blockIdx.x < A.n_tiles) prefetch_halo(su32(xs), A, blockIdx.x);
   for (int i = tid; i < 2 * kBufB / 16; i += kThreads) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < kWB / 16; i += kThreads)
     reinterpret_cast<uint4*>(wts)[i] = reinterpret_cast<const uint4*>(A.wtc)[i];
-  if (tid < 32) s_bias[tid] = A.bias[kRefineOffB1 + tid];
-  else if (tid < 64) s_bias[tid] = A.bias[kRefineOffB2 + tid - 32];
-  else if (tid < 67) s_bias[tid] = A.bias[kRefineOffB3 + tid - 64];
+  for (int i = tid; i < kOnesB / 16; i += kThreads)  // row i (group 0): channel 0 = 1; group 1: zeros
+    reinterpret_cast<uint4*>(ones)[i] = make_uint4(i < 128 ? 0x3F80u : 0u, 0u, 0u, 0u);
   if (tid == 0) {
     s_abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(1));
+    for (int b = 0; b < kSlots; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(full + b)), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(empty + b)), "r"(4));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(layer_done)), "r"(kEpiWarps));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -197,127 +217,233 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
   __syncthreads();
   tc_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t s0 = su32(buf0), s1 = su32(buf1), sw = su32(wts);
   const int H = A.H, W = A.W;
-  uint32_t phase = 0;
 
-  for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
-    const int per_img = A.tiles_x * A.tiles_y;
-    const int img = tile / per_img, rem = tile - img * per_img;
-    const int y0 = (rem / A.tiles_x) * kTH, x0 = (rem % A.tiles_x) * kTW;
-    const float4* in = reinterpret_cast<const float4*>(A.in) + (size_t)img * H * W;
-
-    // ---- stage x (3 channels + zeros) into group 0 of buf0
-    for (int q = tid; q < kRows; q += kThreads) {
-      const int hy = q >> 5, hx = q & 31;
-      const int gy = y0 - 3 + hy, gx = x0 - 3 + hx;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (hy < kHH && gy >= 0 && gy < H && gx >= 0 && gx < W) v = in[(size_t)gy * W + gx];
-      *reinterpret_cast<uint4*>(buf0 + q * 16) = make_uint4(pack2(v.x, v.y), pack2(v.z, 0.f), 0u, 0u);
-    }
-    fence_async_smem();
-    tc_before_sync();
-    __syncthreads();
-
-    // ---- layer 1: A = x rows (group 0; group 1 is multiplied by zero weights)
-    if (tid == 0) {
-      tc_after_sync();
-      for (int mt = 0; mt < kTiles1; ++mt)
-        for (int tap = 0; tap < 9; ++tap) {
-          const int q = kStart1 + mt * 128 + tap_shift(tap);
-          mma(tmem + mt * 32, smem_desc(s0 + q * 16, kGroupB, 128), smem_desc(sw + tap * 1024, 512, 128),
-              instr_desc(128, 32), tap > 0);
-        }
-      commit(bar);
-    }
-    bool ok = __all_sync(0xffffffffu, wait_phase(bar, phase));
-    phase ^= 1u;
-    if (!ok) s_abort = 1;
-    tc_after_sync();
-    if (ok) hidden_epilogue(tmem, kStart1, kTiles1, s_bias, buf1, x0, y0, H, W);
-    fence_async_smem();
-    tc_before_sync();
-    __syncthreads();
-    if (s_abort) break;
-
-    // ---- layer 2: A = a1 (buf1), two K halves of 16 channels
-    if (tid == 0) {
-      tc_after_sync();
-      for (int mt = 0; mt < kTiles2; ++mt)
-        for (int tap = 0; tap < 9; ++tap)
-          for (int kc = 0; kc < 2; ++kc) {
-            const int q = kStart2 + mt * 128 + tap_shift(tap);
-            mma(tmem + mt * 32, smem_desc(s1 + kc * 2 * kGroupB + q * 16, kGroupB, 128),
-                smem_desc(sw + kW1B + tap * 2048 + kc * 1024, 512, 128), instr_desc(128, 32), (tap | kc) != 0);
-          }
-      commit(bar);
-    }
-    ok = __all_sync(0xffffffffu, wait_phase(bar, phase));
-    phase ^= 1u;
-    if (!ok) s_abort = 1;
-    tc_after_sync();
-    if (ok) hidden_epilogue(tmem, kStart2, kTiles2, s_bias + 32, buf0, x0, y0, H, W);
-    fence_async_smem();
-    tc_before_sync();
-    __syncthreads();
-    if (s_abort) break;
-
-    // ---- layer 3: A = a2 (buf0), N = 16 (3 real outputs)
-    if (tid == 0) {
-      tc_after_sync();
-      for (int mt = 0; mt < kTiles3; ++mt)
-        for (int tap = 0; tap < 9; ++tap)
-          for (int kc = 0; kc < 2; ++kc) {
-            const int q = kStart3 + mt * 128 + tap_shift(tap);
-            mma(tmem + mt * 16, smem_desc(s0 + kc * 2 * kGroupB + q * 16, kGroupB, 128),
-                smem_desc(sw + kW1B + kW2B + tap * 1024 + kc * 512, 256, 128), instr_desc(128, 16),
-                (tap | kc) != 0);
-          }
-      commit(bar);
-    }
-    ok = __all_sync(0xffffffffu, wait_phase(bar, phase));
-    phase ^= 1u;
-    if (!ok) s_abort = 1;
-    tc_after_sync();
-    if (ok) {
-      const int quarter = warp & 3;
-      float4* out = reinterpret_cast<float4*>(A.out) + (size_t)img * H * W;
-      for (int mt = warp >> 2; mt < kTiles3; mt += 2) {
-        const int q = kStart3 + mt * 128 + quarter * 32 + lane;
-        float r[4];
-        tmem_ld4(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(mt * 16), r);
-        const int hy = q >> 5, hx = q & 31;
-        if (hy < 3 || hy >= 3 + kTH || hx < 3 || hx >= 3 + kTW) continue;
-        const int gy = y0 - 3 + hy, gx = x0 - 3 + hx;
-        if (gy >= H || gx >= W) continue;
-        const float4 x = in[(size_t)gy * W + gx];
-        float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (x.w > 0.f) {
-          y.x = x.x + (r[0] + s_bias[64]);
-          y.y = x.y + (r[1] + s_bias[65]);
-          y.z = x.z + (r[2] + s_bias[66]);
-          y.w = 1.f;
-        }
-        out[(size_t)gy * W + gx] = y;
+  if (issuer) {
+    // ------------------------------------------------------------ MMA warps (lane 0 of each)
+    // Warp 8 issues the even M-tiles, warp 9 the odd ones, so two threads keep
+    // the tensor core fed; descriptors are precomputed and only their start
+    // address (in 16-byte units, the low field) moves.
+    if (lane == 0) {
+      const int parity = warp - kEpiWarps;
+      const uint64_t a0 = smem_desc(su32(buf0), kGroupB, 128), a1 = smem_desc(su32(buf1), kGroupB, 128);
+      const uint64_t a_ones = smem_desc(su32(ones), 128 * 16, 128);
+      const uint32_t sw = su32(wts);
+      const uint64_t b2bias = smem_desc(sw + kW1B + kW2B + kW3B, 96 * 16, 128);
+      const uint64_t b3bias = smem_desc(sw + kW1B + kW2B + kW3B + kB2Blk, 16 * 16, 128);
+      uint64_t b1d[3], b2d[6], b3d[6];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) b1d[k] = smem_desc(sw + k * kW1Blk, 96 * 16, 128);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        b2d[k] = smem_desc(sw + kW1B + k * kW2Blk, 96 * 16, 128);
+        b3d[k] = smem_desc(sw + kW1B + kW2B + k * kW3Blk, 16 * 16, 128);
       }
+      constexpr uint64_t kHalf = 2 * kGroupB / 16;  // second K half of 16 channels, in 16-byte units
+      uint32_t done_phase = 0;
+      int c = 0;
+      bool ok = true;
+      auto wait_layer = [&]() {
+        ok = ok && wait_phase(layer_done, done_phase, &s_abort);
+        done_phase ^= 1u;
+        tc_after_sync();
+      };
+      // M-tile c: wait for its slot to be released, return the slot's first column.
+      auto slot_col = [&]() -> uint32_t {
+        const int slot = c % kSlots;
+        ok = ok && wait_phase(empty + slot, ((uint32_t)(c / kSlots) & 1u) ^ 1u, &s_abort);
+        tc_after_sync();
+        return tmem + (uint32_t)(slot * kSlotCols);
+      };
+      for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
+        wait_layer();  // x of this tile is in buf0
+        for (int m = 0; m < kTiles1; ++m, ++c) {
+          if ((c & 1) != parity || !ok) continue;
+          const uint32_t d = slot_col();
+          if (!ok) continue;
+          const uint64_t a = a0 + (uint64_t)(kStart1 - 32 + m * 128);
+          mma(d, a, b1d[0], instr_desc(128, 96), 0);
+          mma(d, a + 32, b1d[1], instr_desc(128, 96), 1);
+          mma(d, a + 64, b1d[2], instr_desc(128, 96), 1);
+          commit(full + c % kSlots);
+        }
+        wait_layer();  // every a1 row is written
+        for (int m = 0; m < kTiles2; ++m, ++c) {
+          if ((c & 1) != parity || !ok) continue;
+          const uint32_t d = slot_col();
+          if (!ok) continue;
+          const uint64_t a = a1 + (uint64_t)(kStart2 - 32 + m * 128);
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) {
+            mma(d, a + 32 * dy, b2d[2 * dy], instr_desc(128, 96), dy > 0);
+            mma(d, a + 32 * dy + kHalf, b2d[2 * dy + 1], instr_desc(128, 96), 1);
+          }
+          mma(d, a_ones, b2bias, instr_desc(128, 96), 1);
+          commit(full + c % kSlots);
+        }
+        wait_layer();  // every a2 row is written
+        for (int m = 0; m < kTiles3; ++m, ++c) {
+          if ((c & 1) != parity || !ok) continue;
+          const uint32_t d = slot_col();
+          if (!ok) continue;
+          const uint64_t a = a0 + (uint64_t)(kStart3 - 32 + m * 128);
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) {
+            mma(d, a + 32 * dy, b3d[2 * dy], instr_desc(128, 16), dy > 0);
+            mma(d, a + 32 * dy + kHalf, b3d[2 * dy + 1], instr_desc(128, 16), 1);
+          }
+          mma(d, a_ones, b3bias, instr_desc(128, 16), 1);
+          commit(full + c % kSlots);
+        }
+      }
+      if (!ok) s_abort = 1;
     }
-    tc_before_sync();
-    __syncthreads();  // the next tile overwrites buf0 and the accumulators
-    if (s_abort) break;
+  } else {
+    // ---------------------------------------------------------------- epilogue warps
+    const int quarter = warp & 3, group = warp >> 2;  // group g takes the M-tiles with c % kEpiGroups == g
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    int c = 0;          // the same running M-tile counter as the MMA warp
+    bool ok = true;
+    auto acquire = [&]() -> uint32_t {  // wait for M-tile c's accumulators (lane 0 polls)
+      const int slot = c % kSlots;
+      int got = 1;
+      if (lane == 0) got = wait_phase(full + slot, (uint32_t)(c / kSlots) & 1u, &s_abort) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, got, 0) != 0;
+      if (!ok) s_abort = 1;
+      tc_after_sync();
+      return tmem + lane_base + (uint32_t)(slot * kSlotCols);
+    };
+    auto release = [&]() {  // the slot's accumulators are in registers
+      tmem_wait_ld();
+      tc_before_sync();
+      __syncwarp();
+      if (lane == 0) arrive(empty + c % kSlots);
+    };
+    auto layer_finished = [&]() {  // this warp's shared-memory rows are visible to the MMAs
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) arrive(layer_done);
+    };
+    // A hidden layer: M-tiles of rows start + 128 m into dst (BF16, 4 groups).
+    auto hidden = [&](int start, int n_mtiles, unsigned char* dst, int x0, int y0) {
+      for (int m = 0; m < n_mtiles; ++m, ++c) {
+        if (c % kEpiGroups != group || __any_sync(0xffffffffu, s_abort != 0)) continue;
+        const uint32_t t = acquire();
+        if (!ok) continue;
+        const int q = start + m * 128 + quarter * 32 + lane;  // halo row q / 32, column lane
+        const int gy = y0 - 3 + (q >> 5), gx = x0 - 3 + lane;
+        const bool inside = (q >> 5) < kHH && gy >= 0 && gy < H && gx >= 0 && gx < W;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // output channels 16h .. 16h + 15
+          float d0[16], d1[16], d2[16];
+          tmem_ld16(t + 0 * 32 + 16 * h, d0);
+          tmem_ld16(t + 1 * 32 + 16 * h, d1);
+          tmem_ld16(t + 2 * 32 + 16 * h, d2);
+          if (h == 1) release();  // waits for the loads, then frees the slot for the MMA warps
+          else tmem_wait_ld();
+          uint32_t w[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float v[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int k = 2 * j + e;
+              const float left = __shfl_up_sync(0xffffffffu, d0[k], 1);     // kernel column 0 reads q - 1
+              const float right = __shfl_down_sync(0xffffffffu, d2[k], 1);  // kernel column 2 reads q + 1
+              v[e] = fmaxf(left + d1[k] + right, 0.f);  // the bias came with the MMAs
+            }
+            w[j] = inside ? pack2(v[0], v[1]) : 0u;
+          }
+          if (q < kRows) {
+            *reinterpret_cast<uint4*>(dst + (2 * h) * kGroupB + q * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+            *reinterpret_cast<uint4*>(dst + (2 * h + 1) * kGroupB + q * 16) = make_uint4(w[4], w[5], w[6], w[7]);
+          }
+        }
+      }
+    };
+
+    for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
+      int img, x0, y0;
+      tile_origin(A, tile, img, x0, y0);
+      const float4* in = reinterpret_cast<const float4*>(A.in) + (size_t)img * H * W;
+      // ---- x: FP32 halo (prefetched) -> BF16 group 0 of buf0, then the next halo starts
+      cp_async_wait_all();
+      epi_sync();  // every halo row landed; the previous tile's layer-3 MMAs are complete
+      for (int q = tid; q < kHH * kHW; q += kEpiThreads) {
+        const float4 v = reinterpret_cast<const float4*>(xs)[q];
+        *reinterpret_cast<uint4*>(buf0 + q * 16) = make_uint4(pack2(v.x, v.y), pack2(v.z, 1.f), 0u, 0u);
+      }
+      layer_finished();  // layer 1 may start
+      epi_sync();        // xs is free
+      if (tile + (int)gridDim.x < A.n_tiles) prefetch_halo(su32(xs), A, tile + gridDim.x);
+
+      hidden(kStart1, kTiles1, buf1, x0, y0);
+      layer_finished();
+      hidden(kStart2, kTiles2, buf0, x0, y0);
+      layer_finished();
+
+      // ---- layer 3 and the residual; the FP32 inputs of this warp's outputs load meanwhile.
+      // Layer-3 M-tile m has counter c + m; this group owns m = first + kEpiGroups * j.
+      const int first = (group - c % kEpiGroups + kEpiGroups) % kEpiGroups;
+      constexpr int kOwn = kTiles3 / kEpiGroups;
+      float4 xr[kOwn];
+      int oidx[kOwn];
+#pragma unroll
+      for (int j = 0; j < kOwn; ++j) {
+        const int m = first + kEpiGroups * j;
+        const int hy = (kStart3 >> 5) + 4 * m + quarter;
+        const int gy = y0 - 3 + hy, gx = x0 - 3 + lane;
+        const bool out_ok = hy < 3 + kTH && lane >= 3 && lane < 3 + kTW && gy < H && gx < W;
+        oidx[j] = out_ok ? gy * W + gx : -1;
+        xr[j] = out_ok ? in[(size_t)gy * W + gx] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      float4* out = reinterpret_cast<float4*>(A.out) + (size_t)img * H * W;
+      const int c3 = c;  // counter of layer 3's first M-tile
+#pragma unroll
+      for (int j = 0; j < kOwn; ++j) {
+        c = c3 + first + kEpiGroups * j;
+        if (__any_sync(0xffffffffu, s_abort != 0)) continue;
+        const uint32_t t = acquire();
+        if (!ok) continue;
+        float d[16];
+        tmem_ld16(t, d);
+        release();
+        float r[3];
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          const float left = __shfl_up_sync(0xffffffffu, d[o], 1);
+          const float right = __shfl_down_sync(0xffffffffu, d[8 + o], 1);
+          r[o] = left + d[4 + o] + right;
+        }
+        if (oidx[j] >= 0) {
+          const float4 x = xr[j];
+          float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (x.w > 0.f) {
+            y.x = x.x + r[0];
+            y.y = x.y + r[1];
+            y.z = x.z + r[2];
+            y.w = 1.f;
+          }
+          out[oidx[j]] = y;
+        }
+      }
+      c = c3 + kTiles3;
+    }
+    cp_async_wait_all();
   }
 
-  if (tid == 0 && s_abort) atomicOr(A.error, 1);
+  tc_before_sync();
   __syncthreads();
+  if (tid == 0 && s_abort) atomicOr(A.error, 1);
   if (warp == 0) {
     tc_after_sync();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
   }
 }
 
-}  // namespace
-
 cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, const float* params,
                                 const __nv_bfloat16* packed, int sm_count, int32_t* error, cudaStream_t s) {
+  (void)params;  // the biases are packed with the weights
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(refine_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -333,7 +459,6 @@ cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in
   a.n_tiles = a.tiles_x * a.tiles_y * n;
   a.in = in;
   a.out = out;
-  a.bias = params;
   a.wtc = packed + kPackTc;
   a.error = error;
   if (a.n_tiles == 0) return cudaSuccess;
