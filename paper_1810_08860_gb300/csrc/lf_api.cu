@@ -995,7 +995,11 @@ lf_status lf_get_refiner(lf_ctx* c, float* params, float* grad, float* adam_m, f
   if (step) *step = c->rf.step;
   int32_t err = 0;
   LF_CUDA(c, cudaMemcpy(&err, static_cast<char*>(c->rf.scal.p) + 8, sizeof(err), cudaMemcpyDeviceToHost));
-  if (err) return fail(c, LF_ERR_TIMEOUT, "a wait of the fused refinement kernel gave up");
+  if (err) {
+    char msg[96];
+    std::snprintf(msg, sizeof(msg), "a wait of the fused refinement kernel gave up (error word 0x%x)", (unsigned)err);
+    return fail(c, LF_ERR_TIMEOUT, msg);
+  }
   return LF_OK;
 }
 

@@ -68,7 +68,8 @@ constexpr int kEpiWarps = 16;                // epilogue warps: 4 groups of 4 (o
 constexpr int kEpiGroups = kEpiWarps / 4;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = kEpiThreads + 64;   // + two MMA warps
-constexpr int kWaitLimit = 1 << 22;
+constexpr int kErrIssuerLayer = 2, kErrIssuerSlot = 4, kErrEpilogueFull = 8;  // which wait ran out of time
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait, even under a profiler
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -100,18 +101,32 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
 }
 
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (int it = 0; it < kWaitLimit; ++it) {
-    if ((it & 255) == 0 && *abort_flag) return false;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase of `bar` with the given parity.  Returns 0 once it
+// completed, 2 after kWaitNs of wall time, 1 at once when another warp already
+// gave up.
+__device__ __forceinline__ int wait_phase_status(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 0;; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(su32(bar)), "r"(parity)
         : "memory");
-    if (done) return true;
+    if (done) return 0;
+    if ((it & 255) == 0) {
+      if (*abort_flag) return 1;
+      const uint64_t t = global_ns();
+      if (it == 0) t0 = t;
+      else if (t - t0 > kWaitNs) return 2;
+    }
   }
-  return false;
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -244,14 +259,22 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       int c = 0;
       bool ok = true;
       auto wait_layer = [&]() {
-        ok = ok && wait_phase(layer_done, done_phase, &s_abort);
+        if (ok) {
+          const int w = wait_phase_status(layer_done, done_phase, &s_abort);
+          if (w == 2) atomicOr(A.error, kErrIssuerLayer);
+          ok = w == 0;
+        }
         done_phase ^= 1u;
         tc_after_sync();
       };
       // M-tile c: wait for its slot to be released, return the slot's first column.
       auto slot_col = [&]() -> uint32_t {
         const int slot = c % kSlots;
-        ok = ok && wait_phase(empty + slot, ((uint32_t)(c / kSlots) & 1u) ^ 1u, &s_abort);
+        if (ok) {
+          const int w = wait_phase_status(empty + slot, ((uint32_t)(c / kSlots) & 1u) ^ 1u, &s_abort);
+          if (w == 2) atomicOr(A.error, kErrIssuerSlot);
+          ok = w == 0;
+        }
         tc_after_sync();
         return tmem + (uint32_t)(slot * kSlotCols);
       };
@@ -307,7 +330,11 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
     auto acquire = [&]() -> uint32_t {  // wait for M-tile c's accumulators (lane 0 polls)
       const int slot = c % kSlots;
       int got = 1;
-      if (lane == 0) got = wait_phase(full + slot, (uint32_t)(c / kSlots) & 1u, &s_abort) ? 1 : 0;
+      if (lane == 0) {
+        const int w = wait_phase_status(full + slot, (uint32_t)(c / kSlots) & 1u, &s_abort);
+        if (w == 2) atomicOr(A.error, kErrEpilogueFull);
+        got = w == 0;
+      }
       ok = __shfl_sync(0xffffffffu, got, 0) != 0;
       if (!ok) s_abort = 1;
       tc_after_sync();
