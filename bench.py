@@ -71,6 +71,50 @@ def dist_env():
     return rank, world, local
 
 
+def init_dist(world: int):
+    """One process per GPU under torchrun (NCCL), or gloo ranks on the CPU."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+
+def finish_dist(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+def max_over_ranks(ms: float) -> float:
+    """The slowest rank's duration (the job's time); the value itself at N = 1.
+    Ranks render independent head poses (replicas): no data crosses ranks."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier_all():
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def whole_job_rate(units_per_rank: float, max_ms: float, world: int) -> float:
+    """Units all ranks processed per second (millions), over the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1000.0) / 1e6
+
+
 def make_workload(name: str, n_heads: int, rank: int):
     import scene
 
@@ -302,10 +346,7 @@ def run_batch(args):
     import torch
 
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    init_dist(world)
     torch.cuda.set_device(local)
     import __graft_entry__
 
@@ -335,8 +376,7 @@ def run_batch(args):
     for _ in range(args.warmup):
         r.render_batch(eyes, out=outs)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier_all()
     clocks = ClockSampler(local)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -362,12 +402,8 @@ def run_batch(args):
         if k >= 1:
             raster_ms.append(st["ms_raster"])
     rt.close()
-    total_ms = sum(x.elapsed_time(y) for x, y in ev)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * px * args.steps / (total_ms / 1000.0) / 1e6
+    total_ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev))
+    value = whole_job_rate(px * args.steps, total_ms, world)
     peak, peak_kind = measured_peak()
     tex_bytes = {"f32": 16, "u8": 4, "bf16": 8, "fp8": 4}[args.tex]
     raster_bytes = uniq * tex_bytes + px * 16
@@ -394,8 +430,7 @@ def run_batch(args):
     if rank == 0:
         print(json.dumps(result), flush=True)
     r.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    finish_dist(world)
     return 0
 
 
@@ -442,6 +477,7 @@ def run_refine(args):
     import torch
 
     rank, world, local = dist_env()
+    init_dist(world)
     torch.cuda.set_device(local)
     import __graft_entry__
 
@@ -479,11 +515,11 @@ def run_refine(args):
     r.get_refiner()
     ms = [a.elapsed_time(b) for a, b in ev]
     px = 2 * 1440 * 1600
-    mean = statistics.mean(ms)
+    mean = max_over_ranks(sum(ms)) / len(ms)
     peak, peak_kind = measured_tensor_peak()
     achieved = REFINE_FLOP_PER_PX * px / (mean / 1000.0) / 1e12
     result = {
-        "metric": METRIC, "value": world * px / (mean / 1000.0) / 1e6, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": whole_job_rate(px, mean, world), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "refinement only: lf_refine of 2 x 1440x1600 RGBA images (one launch), seeded "
@@ -499,6 +535,7 @@ def run_refine(args):
     if rank == 0:
         print(json.dumps(result), flush=True)
     r.close()
+    finish_dist(world)
     return 0
 
 
@@ -512,6 +549,7 @@ def run_learned(args):
     import torch
 
     rank, world, local = dist_env()
+    init_dist(world)
     torch.cuda.set_device(local)
     import __graft_entry__
 
@@ -647,12 +685,8 @@ def run_learned(args):
 
     ms_e2e = timed(e2e_step, max(20, args.steps // 4))
     st = rf.get_refiner()  # raises if the fused kernel reported a failed wait
-    total = sum(ms_refined)
-    if world > 1:
-        t = torch.tensor([total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
-    value = world * px * args.steps / (total / 1000.0) / 1e6
+    total = max_over_ranks(sum(ms_refined))
+    value = whole_job_rate(px * args.steps, total, world)
     kern = statistics.mean(ms_kernel)
     peak, peak_kind = measured_tensor_peak()
     achieved = REFINE_FLOP_PER_PX * px / (kern / 1000.0) / 1e12
@@ -703,6 +737,7 @@ def run_learned(args):
     if rank == 0:
         print(json.dumps(result), flush=True)
     rf.close()
+    finish_dist(world)
     return 0
 
 
@@ -710,10 +745,7 @@ def run_ours(args):
     import torch
 
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    init_dist(world)
     torch.cuda.set_device(local)
     import __graft_entry__
 
@@ -757,8 +789,7 @@ def run_ours(args):
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier_all()
     clocks = ClockSampler(local)
     clocks.start()
     torch.cuda.synchronize()
@@ -773,13 +804,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
-    value = world * px_per_step * args.steps / (total_ms / 1000.0) / 1e6
+    total_ms = max_over_ranks(sum(step_ms))
+    barrier_all()
+    value = whole_job_rate(px_per_step * args.steps, total_ms, world)
 
     # End to end through the public call: host poses in, images read back to host.
     host = [torch.empty(o.shape, dtype=torch.float32, pin_memory=True) for o in outs]
@@ -795,12 +822,8 @@ def run_ours(args):
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * px_per_step * len(e2e_ms) / (e2e_total / 1000.0) / 1e6
+    e2e_total = max_over_ranks(sum(e2e_ms))
+    e2e_value = whole_job_rate(px_per_step * len(e2e_ms), e2e_total, world)
 
     peak, peak_kind = measured_peak()
     mean_raster = statistics.mean(raster_ms)
@@ -838,8 +861,7 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(result), flush=True)
     r.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    finish_dist(world)
     return 0
 
 
