@@ -30,6 +30,7 @@ constexpr int kMaxTileThreads = 256;
 constexpr int kSnapLimit = 1 << 29;     // |snapped| must stay below 2^29 subpixels
 constexpr int kBigEdge = 1 << 22;       // edge deltas from 2^22 subpixels use the int64 path
 constexpr int kQClamp = 1 << 28;        // clamp of the per-tile edge offset in the int32 path
+constexpr int kBinSmemTiles = 8192;     // footprint tiles a binning CTA counts in shared memory
 
 // device error bits
 constexpr uint32_t kErrPoolOverflow = 1u << 0;

@@ -700,6 +700,9 @@ __global__ void __launch_bounds__(BLOCK) bin_kernel(FrameArgs A) {
   __shared__ int s_warp[BLOCK / 32];
   __shared__ long long s_off, s_ent;
   __shared__ int s_big;
+  // per-tile counts, then cursors: in shared memory when the footprint fits
+  // (nearly always), else in the offset pool's cursor half
+  __shared__ int s_cnt[kBinSmemTiles];
   const int tw = A.tile_w, th = A.tile_h;
   const int tx0 = R.bb[0] / tw, ty0 = R.bb[1] / th;
   const int ntx = R.bb[2] / tw - tx0 + 1, nty = R.bb[3] / th - ty0 + 1;
@@ -714,7 +717,9 @@ __global__ void __launch_bounds__(BLOCK) bin_kernel(FrameArgs A) {
   if (s_off < 0) return;
   int* offs = A.bin_offsets + s_off;
   int* curs = offs + nt + 1;
-  for (int k = threadIdx.x; k <= nt; k += BLOCK) offs[k] = 0;
+  const bool in_smem = nt <= kBinSmemTiles;
+  int* cnt = in_smem ? s_cnt : curs;  // counts, then cursors
+  for (int k = threadIdx.x; k < nt; k += BLOCK) cnt[k] = 0;
   __syncthreads();
   const TriRec* tris = A.pool + R.tri_base;
   auto span = [&](int t, int& x0, int& y0, int& x1, int& y1) {
@@ -731,7 +736,7 @@ __global__ void __launch_bounds__(BLOCK) bin_kernel(FrameArgs A) {
     if (x0 > x1 || y0 > y1) continue;
     if ((x1 - x0 + 1) * (y1 - y0 + 1) > A.bin_max_tiles) { ++my_big; continue; }
     for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) atomicAdd(&offs[y * ntx + x], 1);
+      for (int x = x0; x <= x1; ++x) atomicAdd(&cnt[y * ntx + x], 1);
   }
   if (my_big) atomicAdd(&s_big, my_big);
   __syncthreads();
@@ -739,7 +744,7 @@ __global__ void __launch_bounds__(BLOCK) bin_kernel(FrameArgs A) {
   const int per = (nt + BLOCK - 1) / BLOCK;
   const int r0 = threadIdx.x * per, r1 = min(r0 + per, nt);
   int run = 0;
-  for (int k = r0; k < r1; ++k) run += offs[k];
+  for (int k = r0; k < r1; ++k) run += cnt[k];
   int total;
   int o = block_exclusive_scan(run, s_warp, total);
   if (threadIdx.x == 0) {
@@ -752,9 +757,9 @@ __global__ void __launch_bounds__(BLOCK) bin_kernel(FrameArgs A) {
   const long long ent = s_ent;
   if (ent < 0) return;
   for (int k = r0; k < r1; ++k) {
-    const int c = offs[k];
+    const int c = cnt[k];
     offs[k] = (int)(ent + o);
-    curs[k] = (int)(ent + o);
+    cnt[k] = (int)(ent + o);  // cursor
     o += c;
   }
   if (threadIdx.x == 0) {
@@ -773,7 +778,7 @@ __global__ void __launch_bounds__(BLOCK) bin_kernel(FrameArgs A) {
       continue;
     }
     for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) A.bin_entries[atomicAdd(&curs[y * ntx + x], 1)] = idx;
+      for (int x = x0; x <= x1; ++x) A.bin_entries[atomicAdd(&cnt[y * ntx + x], 1)] = idx;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
