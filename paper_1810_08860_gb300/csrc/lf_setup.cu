@@ -187,6 +187,7 @@ __device__ void pixel_range(float lo, float hi, float f, float c, int n, int& i0
 
 constexpr int kViewsPerSetupBlock = 16;
 constexpr int kViewSetupThreads = 128;
+constexpr int kViewSetupSlices = 4;  // blocks sharing one group of views' (view, tile) cone tests
 
 // A block takes 16 views of one eye.  Threads 0-15 do the per-view set-up
 // (FP64 composition, FP32 shading map and disk constants, conservative
@@ -206,7 +207,8 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
   const EyeParams& E = A.eyes[e];
   const float tile_half_diag = 0.5f * sqrtf((float)(A.tile_w * A.tile_w + A.tile_h * A.tile_h));
   const float alpha_tile = tile_half_diag / fminf((float)E.fx, (float)E.fy);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  const bool writer = blockIdx.z == 0;  // the other slices only share the cone tests
+  if (writer && blockIdx.x == 0 && threadIdx.x == 0) {
     // the eye's FP32 decision constants, each rounded once from FP64
     EyeFloat& F = A.eyes_f[e];
     for (int k = 0; k < 9; ++k) F.R[k] = __double2float_rn(E.R[k]);
@@ -222,6 +224,7 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
     float dir[4] = {0.f, 0.f, 1.f, 2.f};
     if (v < A.n_views) {
       const ViewStatic& V = A.views[v];
+      if (writer) {
       ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
       // A1: M = R_eye^T R_i, m = R_eye^T (t_i - t_eye) in FP64, fixed order, no fusion.
       double M[9], m[3];
@@ -274,6 +277,7 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
       R.big_base = 0;
       R.big_count = 0;
       R.tri_count = 0;
+      }
 
       // Conservative footprint: a pixel whose sphere crossing can fall inside the
       // disk has a forward ray passing within r of c_i, so it lies in the screen
@@ -292,7 +296,10 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
         x1 = min(x1, E.W - 1); y1 = min(y1, E.H - 1);
         if (x0 <= x1 && y0 <= y1) { bb[0] = x0; bb[1] = y0; bb[2] = x1; bb[3] = y1; }
       }
-      R.bb[0] = bb[0]; R.bb[1] = bb[1]; R.bb[2] = bb[2]; R.bb[3] = bb[3];
+      if (writer) {
+        ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
+        R.bb[0] = bb[0]; R.bb[1] = bb[1]; R.bb[2] = bb[2]; R.bb[3] = bb[3];
+      }
       // cone of the ball seen from the eye, widened by a tile's angular radius
       const float L = sqrtf(ce[0] * ce[0] + ce[1] * ce[1] + ce[2] * ce[2]);
       if (L > rho) {
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
   __syncthreads();
   const int total = s_off[kViewsPerSetupBlock];
   const float fx = (float)E.fx, fy = (float)E.fy, cx = (float)E.cx, cy = (float)E.cy;
-  for (int f = threadIdx.x; f < total; f += kViewSetupThreads) {
+  for (int f = threadIdx.x + blockIdx.z * kViewSetupThreads; f < total; f += kViewSetupThreads * kViewSetupSlices) {
     int k = 0;
     while (k + 1 < kViewsPerSetupBlock && s_off[k + 1] <= f) ++k;
     const int q = f - s_off[k];
@@ -342,7 +349,7 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
 }
 
 cudaError_t launch_view_setup(const FrameArgs& a, cudaStream_t s) {
-  dim3 grid((a.n_views + kViewsPerSetupBlock - 1) / kViewsPerSetupBlock, a.n_eyes);
+  dim3 grid((a.n_views + kViewsPerSetupBlock - 1) / kViewsPerSetupBlock, a.n_eyes, kViewSetupSlices);
   view_setup_kernel<<<grid, kViewSetupThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
