@@ -187,7 +187,7 @@ __device__ void pixel_range(float lo, float hi, float f, float c, int n, int& i0
 
 constexpr int kViewsPerSetupBlock = 16;
 constexpr int kViewSetupThreads = 128;
-constexpr int kViewSetupSlices = 4;  // blocks sharing one group of views' (view, tile) cone tests
+constexpr int kViewSetupSlices = 8;  // blocks sharing one group of views' (view, tile) cone tests
 
 // A block takes 16 views of one eye.  Threads 0-15 do the per-view set-up
 // (FP64 composition, FP32 shading map and disk constants, conservative
