@@ -175,12 +175,25 @@ __device__ __forceinline__ int collect_views(const uint32_t* mask, int mask_word
 // pixels, keeping the nearest fragment per view; (d) when the view changes, a
 // pixel's winner is buffered, and buffered winners are shaded (bilinear
 // fetch, weight, accumulate) with both pixels' texel loads in flight.
-template <int TW, int TH, int FMT, bool INSPECT>
+template <int TW, int TH, int FMT, bool INSPECT, bool MANY_EYES>
 __device__ void raster_strip(const FrameArgs& A, const int item, const int strip, WarpSmem& S) {
   constexpr int ROWS = (32 / TW) * kPx;
   const int lane = threadIdx.x & 31;
+  const uint32_t* mask = A.tile_masks + (int64_t)item * A.mask_words;
+  // the eye holding this tile: the last one whose first tile is <= item (a
+  // binary search in the batch kernel, whose calls hold up to 128 eyes; a scan
+  // in the per-call kernel, which keeps its registers for the pixels)
   int e = 0;
-  while (e + 1 < A.n_eyes && A.eyes[e + 1].tile_base <= item) ++e;
+  if constexpr (MANY_EYES) {
+    for (int lo = 0, hi = A.n_eyes; hi - lo > 1;) {
+      const int mid = (lo + hi) >> 1;
+      if (A.eyes[mid].tile_base <= item) lo = mid;
+      else hi = mid;
+      e = lo;
+    }
+  } else {
+    while (e + 1 < A.n_eyes && A.eyes[e + 1].tile_base <= item) ++e;
+  }
   const EyeParams& E = A.eyes[e];
   const int tile = item - E.tile_base;
   const int tx = tile % E.tiles_x, ty = tile / E.tiles_x;
@@ -195,7 +208,6 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
   const float px = (float)pi + 0.5f;
   const int64_t P0x = 256 * (int64_t)i0 + 128, P0y = 256 * (int64_t)j0 + 128;
   const int64_t tex_per_view = (int64_t)A.src_w * A.src_h;
-  const uint32_t* mask = A.tile_masks + (int64_t)item * A.mask_words;
 
   bool valid[kPx], has_p[kPx];
   float ey[kPx], py[kPx], p[kPx][3];
@@ -537,7 +549,7 @@ __global__ void __launch_bounds__(TW * TH / kPx, 6) raster_kernel(FrameArgs A) {
   __shared__ WarpSmem S[WARPS];
   const int warp = threadIdx.x >> 5;
   if constexpr (!PERSISTENT) {
-    raster_strip<TW, TH, FMT, INSPECT>(A, blockIdx.x, warp, S[warp]);
+    raster_strip<TW, TH, FMT, INSPECT, false>(A, blockIdx.x, warp, S[warp]);
   } else {
     const int n_items = A.total_tiles * WARPS;
     for (;;) {
@@ -545,7 +557,7 @@ __global__ void __launch_bounds__(TW * TH / kPx, 6) raster_kernel(FrameArgs A) {
       if ((threadIdx.x & 31) == 0) item = atomicAdd(A.work_counter, 1);
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= n_items) break;
-      raster_strip<TW, TH, FMT, INSPECT>(A, item / WARPS, item % WARPS, S[warp]);
+      raster_strip<TW, TH, FMT, INSPECT, true>(A, item / WARPS, item % WARPS, S[warp]);
     }
   }
 }
