@@ -68,7 +68,9 @@ FRAG_RECORD_DTYPE = np.dtype([("view", np.int32), ("n_cover", np.int32), ("winne
 EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_build_view_meshes", "lf_render",
            "lf_render_batch", "lf_render_inspect", "lf_render_static", "lf_tune_batch", "lf_get_stats",
            "lf_status_string", "lf_last_error", "lf_load_refiner", "lf_refine_set_kernel", "lf_get_refiner",
-           "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined"]
+           "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined", "lf_render_host",
+           "lf_host_wait"]
+HOST_FRAMES_IN_FLIGHT = 3
 
 REFINE_N_PARAMS = 11011
 REFINE_SHAPES = [("W1", (32, 3, 3, 3)), ("b1", (32,)), ("W2", (32, 32, 3, 3)), ("b2", (32,)),
@@ -138,6 +140,10 @@ def load_library(path: str = LIB_PATH):
     lib.lf_refine_train_step.restype = ctypes.c_int
     lib.lf_render_refined.argtypes = [vp, i32, vp, vp, vp, vp]
     lib.lf_render_refined.restype = ctypes.c_int
+    lib.lf_render_host.argtypes = [vp, i32, vp, vp, vp, i32, ctypes.POINTER(i64), vp]
+    lib.lf_render_host.restype = ctypes.c_int
+    lib.lf_host_wait.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_uint32)]
+    lib.lf_host_wait.restype = ctypes.c_int
     lib.lf_status_string.argtypes = [ctypes.c_int]
     lib.lf_status_string.restype = ctypes.c_char_p
     lib.lf_last_error.argtypes = [vp]
@@ -252,11 +258,40 @@ class Renderer:
         self._check(self.lib.lf_render(self.ctx, len(eyes), poses, intr, ptrs, _stream_handle(stream)), "lf_render")
         return out
 
-    def render_host(self, eyes, stream=None):
-        """End-to-end call from host poses to host images: the render plus the
-        device->host copy of the result (what a client reading pixels back pays)."""
-        out = self.render(eyes, stream=stream)
-        return [o.cpu() for o in out]
+    def render_host(self, eyes, out=None, refined: bool = False, stream=None):
+        """Render eye views and deliver them to host memory (lf_render_host): the
+        device->host copy of this frame overlaps the rendering of the next.
+        `out` holds one contiguous float32 CPU tensor (H, W, 4) per eye, pinned
+        for an asynchronous copy (allocated pinned when None).  Returns
+        (frame, out); the images are complete once host_wait(frame) returns."""
+        import torch
+        if out is None:
+            out = [torch.empty((e.height, e.width, 4), dtype=torch.float32, pin_memory=True) for e in eyes]
+        for e, o in zip(eyes, out):
+            if o.dtype != torch.float32 or o.is_cuda or not o.is_contiguous() or tuple(o.shape) != (e.height, e.width, 4):
+                raise ValueError("each host output must be a contiguous float32 CPU tensor of shape (H, W, 4)")
+        if len(out) != len(eyes):
+            raise ValueError("one host output per eye")
+        poses, intr = self._eye_arrays(eyes)
+        ptrs = (ctypes.c_void_p * len(out))(*[o.data_ptr() for o in out])
+        frame = ctypes.c_int64(-1)
+        self._check(self.lib.lf_render_host(self.ctx, len(eyes), poses, intr, ptrs, 1 if refined else 0,
+                                            ctypes.byref(frame), _stream_handle(stream)), "lf_render_host")
+        # keep the host buffers alive until their frame is delivered
+        self._in_flight = [(f, o) for f, o in getattr(self, "_in_flight", []) if f > frame.value - HOST_FRAMES_IN_FLIGHT]
+        self._in_flight.append((frame.value, out))
+        return frame.value, out
+
+    def host_wait(self, frame: int = -1) -> int:
+        """Wait until `frame` (every frame when negative) of render_host is in host
+        memory; returns the OR of the delivered frames' device error bits."""
+        err = ctypes.c_uint32(0)
+        self._check(self.lib.lf_host_wait(self.ctx, int(frame), ctypes.byref(err)), "lf_host_wait")
+        if frame < 0:
+            self._in_flight = []
+        else:
+            self._in_flight = [(f, o) for f, o in getattr(self, "_in_flight", []) if f > frame]
+        return err.value
 
     def render_batch(self, eyes, out=None, stream=None):
         """Render many eyes in one graph-replayed persistent launch (lf_render_batch)."""

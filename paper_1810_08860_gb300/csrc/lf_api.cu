@@ -20,6 +20,8 @@ using namespace lfk;
 namespace {
 
 constexpr int kRing = 4;
+constexpr int kHostSlots = LF_HOST_FRAMES_IN_FLIGHT;
+constexpr size_t kCounterBlock = 32;  // triangles, error word, work counter, bin offsets, bin entries
 
 struct Buffer {
   void* p = nullptr;
@@ -72,6 +74,16 @@ struct lf_ctx {
     Buffer scal;      // loss (f32), valid count (i32)
     Buffer a1, a2, gz2, gr, partial, frame;
   } rf;
+  // frames delivered to host memory (lf_render_host): frame k uses slot k % kHostSlots
+  struct HostPipe {
+    cudaStream_t copy = nullptr;
+    cudaEvent_t rendered[kHostSlots] = {}, copied[kHostSlots] = {};
+    Buffer image[kHostSlots];  // device images of the slot's frame
+    Buffer counters;           // one counter block per slot
+    uint32_t* err = nullptr;   // pinned: the error word of each slot's frame
+    int64_t issued = 0, delivered = 0;
+    uint32_t err_acc = 0;      // error bits of the frames delivered since the last lf_host_wait
+  } hp;
 };
 
 namespace {
@@ -187,6 +199,16 @@ lf_status stage_eyes(lf_ctx* c, const Layout& L, cudaStream_t s) {
   return LF_OK;
 }
 
+// Point a frame's counters at a 32-byte block: triangles (8 B), error word,
+// work counter, bin offsets (8 B), bin entries (8 B).  enqueue_frame zeroes it.
+void use_counters(FrameArgs& a, unsigned char* block) {
+  a.pool_counter = reinterpret_cast<unsigned long long*>(block);
+  a.error_word = reinterpret_cast<uint32_t*>(block + 8);
+  a.work_counter = reinterpret_cast<int32_t*>(block + 12);
+  a.bin_offsets_counter = reinterpret_cast<unsigned long long*>(block + 16);
+  a.bin_entries_counter = reinterpret_cast<unsigned long long*>(block + 24);
+}
+
 FrameArgs frame_args(lf_ctx* c, const Layout& L) {
   FrameArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -217,13 +239,7 @@ FrameArgs frame_args(lf_ctx* c, const Layout& L) {
   a.bin_entries = static_cast<int32_t*>(c->bin_entries.p);
   a.bin_entries_capacity = bin_entries_capacity(c, L.total_tiles);
   a.bin_max_tiles = 1 << 30;  // bin every triangle into every footprint tile its box covers
-  // counter block: triangles (8 B), error word, work counter, bin offsets (8 B), bin entries (8 B)
-  unsigned char* sm = static_cast<unsigned char*>(c->small.p);
-  a.pool_counter = reinterpret_cast<unsigned long long*>(sm);
-  a.error_word = reinterpret_cast<uint32_t*>(sm + 8);
-  a.work_counter = reinterpret_cast<int32_t*>(sm + 12);
-  a.bin_offsets_counter = reinterpret_cast<unsigned long long*>(sm + 16);
-  a.bin_entries_counter = reinterpret_cast<unsigned long long*>(sm + 24);
+  use_counters(a, static_cast<unsigned char*>(c->small.p));
   a.active = static_cast<uint8_t*>(c->active.p);
   a.total_tiles = L.total_tiles;
   a.tile_w = c->cfg.tile_w;
@@ -236,7 +252,7 @@ lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persis
   const bool t = c->cfg.timing != 0;
   LF_CUDA(c, cudaMemsetAsync(a.tile_masks, 0, sizeof(uint32_t) * (size_t)a.total_tiles * a.mask_words, s));
   // the counter block starts at zero each call
-  LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, 32, s));
+  LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, kCounterBlock, s));
   LF_CUDA(c, cudaMemsetAsync(a.active, 0, (size_t)a.n_eyes * a.n_views, s));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[0], s));
   LF_CUDA(c, launch_view_setup(a, s));
@@ -418,6 +434,14 @@ void lf_destroy(lf_ctx* ctx) {
   for (Buffer* b : {&ctx->rf.state, &ctx->rf.packed, &ctx->rf.scal, &ctx->rf.a1, &ctx->rf.a2, &ctx->rf.gz2,
                     &ctx->rf.gr, &ctx->rf.partial, &ctx->rf.frame})
     release(*b);
+  for (int k = 0; k < kHostSlots; ++k) {
+    release(ctx->hp.image[k]);
+    if (ctx->hp.rendered[k]) cudaEventDestroy(ctx->hp.rendered[k]);
+    if (ctx->hp.copied[k]) cudaEventDestroy(ctx->hp.copied[k]);
+  }
+  release(ctx->hp.counters);
+  if (ctx->hp.err) cudaFreeHost(ctx->hp.err);
+  if (ctx->hp.copy) cudaStreamDestroy(ctx->hp.copy);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->work_stream) cudaStreamDestroy(ctx->work_stream);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
@@ -797,11 +821,7 @@ extern "C" lf_status lf_render_static(lf_ctx* c, const lf_pose* eye, const lf_in
   a.bin_max_tiles = kBinMaxTiles;
   a.pool = reinterpret_cast<TriRec*>(base + kOffPool);
   a.pool_capacity = kStaticTris;
-  a.pool_counter = reinterpret_cast<unsigned long long*>(base + kOffCounters);
-  a.error_word = reinterpret_cast<uint32_t*>(base + kOffCounters + 8);
-  a.work_counter = reinterpret_cast<int32_t*>(base + kOffCounters + 12);
-  a.bin_offsets_counter = reinterpret_cast<unsigned long long*>(base + kOffCounters + 16);
-  a.bin_entries_counter = reinterpret_cast<unsigned long long*>(base + kOffCounters + 24);
+  use_counters(a, base + kOffCounters);
   // enqueue_frame zeroes the masks, counters and flags that must start at zero
   return enqueue_frame(c, a, false, false, s);
 }
@@ -1059,6 +1079,136 @@ lf_status lf_render_refined(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, cons
     if ((st = refine_apply(c, 1, intr[e].width, intr[e].height, tmp[e], out_rgba[e],
                            static_cast<cudaStream_t>(stream))) != LF_OK)
       return st;
+  return LF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Frames delivered to host memory (lf_render_host, lf_host_wait).
+//
+// Frame k renders on the caller's stream into device slot k % kHostSlots,
+// with that slot's own counter block; the context's copy stream waits for the
+// render and copies the images and the error word to host memory.  The copy
+// of frame k therefore overlaps the render of frame k + 1, and a later
+// frame's counter reset cannot erase frame k's error word before it is read.
+// A slot is reused only after the host has seen its previous frame delivered,
+// which also bounds the frames in flight.
+
+namespace {
+
+lf_status host_pipe_init(lf_ctx* c) {
+  auto& H = c->hp;
+  if (!H.copy) LF_CUDA(c, cudaStreamCreateWithFlags(&H.copy, cudaStreamNonBlocking));
+  for (int k = 0; k < kHostSlots; ++k) {
+    if (!H.rendered[k]) LF_CUDA(c, cudaEventCreateWithFlags(&H.rendered[k], cudaEventDisableTiming));
+    if (!H.copied[k]) LF_CUDA(c, cudaEventCreateWithFlags(&H.copied[k], cudaEventDisableTiming));
+  }
+  LF_CUDA(c, ensure(H.counters, kCounterBlock * kHostSlots));
+  if (!H.err) LF_CUDA(c, cudaMallocHost((void**)&H.err, sizeof(uint32_t) * kHostSlots));
+  return LF_OK;
+}
+
+// Wait until the oldest undelivered frame is in host memory; collect its error bits.
+lf_status host_deliver_oldest(lf_ctx* c) {
+  auto& H = c->hp;
+  const int slot = (int)(H.delivered % kHostSlots);
+  LF_CUDA(c, cudaEventSynchronize(H.copied[slot]));
+  H.err_acc |= H.err[slot];
+  ++H.delivered;
+  return LF_OK;
+}
+
+// Enqueue the render of one frame into `slot` and its copy to host memory.
+lf_status host_enqueue(lf_ctx* c, int slot, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                       float* const* host_rgba, const std::vector<size_t>& off, const std::vector<size_t>& bytes,
+                       bool refined, cudaStream_t s) {
+  auto& H = c->hp;
+  unsigned char* img = static_cast<unsigned char*>(H.image[slot].p);
+  std::vector<float*> dev(n_eyes), target(n_eyes);
+  for (int e = 0; e < n_eyes; ++e) dev[e] = target[e] = reinterpret_cast<float*>(img + off[e]);
+  if (refined) {  // render into the context's scratch image, refine into the slot
+    LF_CUDA(c, ensure(c->rf.frame, off[n_eyes - 1] + bytes[n_eyes - 1]));
+    for (int e = 0; e < n_eyes; ++e)
+      target[e] = reinterpret_cast<float*>(static_cast<unsigned char*>(c->rf.frame.p) + off[e]);
+  }
+  lf_status st;
+  Layout L;
+  if ((st = make_layout(c, n_eyes, eyes, intr, target.data(), L)) != LF_OK) return st;
+  if ((st = ensure_scratch(c, n_eyes, L.total_tiles)) != LF_OK) return st;
+  if ((st = stage_eyes(c, L, s)) != LF_OK) return st;
+  FrameArgs a = frame_args(c, L);
+  unsigned char* counters = static_cast<unsigned char*>(H.counters.p) + kCounterBlock * slot;
+  use_counters(a, counters);
+  if ((st = enqueue_frame(c, a, false, false, s)) != LF_OK) return st;
+  if (refined)
+    for (int e = 0; e < n_eyes; ++e)
+      if ((st = refine_apply(c, 1, intr[e].width, intr[e].height, target[e], dev[e], s)) != LF_OK) return st;
+  LF_CUDA(c, cudaEventRecord(H.rendered[slot], s));
+  LF_CUDA(c, cudaStreamWaitEvent(H.copy, H.rendered[slot], 0));
+  for (int e = 0; e < n_eyes; ++e)
+    LF_CUDA(c, cudaMemcpyAsync(host_rgba[e], dev[e], bytes[e], cudaMemcpyDeviceToHost, H.copy));
+  LF_CUDA(c, cudaMemcpyAsync(&H.err[slot], counters + 8, sizeof(uint32_t), cudaMemcpyDeviceToHost, H.copy));
+  LF_CUDA(c, cudaEventRecord(H.copied[slot], H.copy));
+  return LF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lf_status lf_render_host(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
+                         float* const* host_rgba, int32_t refined, int64_t* frame, void* stream) {
+  lf_status st = check_ready(c);
+  if (st != LF_OK) return st;
+  if (refined != 0 && refined != 1) return fail(c, LF_ERR_INVALID_ARG, "refined must be 0 or 1");
+  if (n_eyes < 1 || n_eyes > c->cfg.max_eyes || !eyes || !intr || !host_rgba)
+    return fail(c, LF_ERR_INVALID_ARG, "bad eye arguments");
+  std::vector<size_t> off(n_eyes), bytes(n_eyes);
+  size_t total = 0;
+  for (int e = 0; e < n_eyes; ++e) {
+    if (!host_rgba[e]) return fail(c, LF_ERR_INVALID_ARG, "null host output pointer");
+    if (intr[e].width < 1 || intr[e].height < 1 || intr[e].width > 32767 || intr[e].height > 32767)
+      return fail(c, LF_ERR_INVALID_ARG, "eye size out of range");
+    off[e] = total;
+    bytes[e] = sizeof(float) * 4 * (size_t)intr[e].width * intr[e].height;
+    total += (bytes[e] + 255) & ~(size_t)255;
+  }
+  if ((st = host_pipe_init(c)) != LF_OK) return st;
+  auto& H = c->hp;
+  while (H.issued - H.delivered >= kHostSlots)
+    if ((st = host_deliver_oldest(c)) != LF_OK) return st;
+  const int slot = (int)(H.issued % kHostSlots);
+  LF_CUDA(c, ensure(H.image[slot], total));  // the slot's previous frame has been delivered
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = host_enqueue(c, slot, n_eyes, eyes, intr, host_rgba, off, bytes, refined == 1 && c->rf.loaded, s);
+  if (st != LF_OK) {
+    // leave nothing of the frame running: the caller may free its buffers
+    cudaStreamSynchronize(s);
+    cudaStreamSynchronize(H.copy);
+    cudaGetLastError();
+    return st;
+  }
+  if (frame) *frame = H.issued;
+  ++H.issued;
+  return LF_OK;
+}
+
+lf_status lf_host_wait(lf_ctx* c, int64_t frame, uint32_t* error_word) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (error_word) *error_word = 0;
+  auto& H = c->hp;
+  if (frame >= H.issued) return fail(c, LF_ERR_INVALID_ARG, "lf_host_wait: no such frame has been issued");
+  const int64_t upto = frame < 0 ? H.issued : frame + 1;
+  if (H.delivered < upto) LF_CUDA(c, cudaSetDevice(c->device));
+  while (H.delivered < upto) {
+    lf_status st = host_deliver_oldest(c);
+    if (st != LF_OK) return st;
+  }
+  const uint32_t err = H.err_acc;
+  H.err_acc = 0;
+  if (error_word) *error_word = err;
+  if (err & kErrPoolOverflow) return fail(c, LF_ERR_CAPACITY, "a frame delivered to host memory overflowed its scratch");
   return LF_OK;
 }
 
