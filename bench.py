@@ -150,9 +150,14 @@ def measured_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
+RASTER_SOURCES = ("lf_raster.cu", "lf_internal.h")
+REFINE_SOURCES = ("lf_refine_tc.cu", "lf_internal.h")
+REFINE_PROFILE = "refine_fused_stereo_2x1440x1600"
+
+
+def kernel_source_hash(files=RASTER_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in ("lf_raster.cu", "lf_internal.h"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1810_08860_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -194,10 +199,10 @@ def host_e2e(r, heads, shapes, flush, stream, steps, px_per_step, world, refined
     return whole_job_rate(px_per_step * steps, total_ms, world), statistics.mean(lat)
 
 
-def ncu_traffic(workload: str, tex: str, tile: str):
-    """DRAM bytes per raster launch from the committed ncu summary, if it was
-    taken on the current kernel source for this workload; else None."""
-    path = os.path.join(ROOT, "profiles", "raster_%s_%s_%s.txt" % (workload, tex, tile))
+def ncu_traffic(profile: str, files=RASTER_SOURCES):
+    """DRAM bytes per launch from the committed ncu summary profiles/<profile>.txt,
+    if it was taken on the current source of the kernel (`files`); else None."""
+    path = os.path.join(ROOT, "profiles", profile + ".txt")
     try:
         vals = {}
         with open(path) as fh:
@@ -205,7 +210,7 @@ def ncu_traffic(workload: str, tex: str, tile: str):
                 if ":" in line:
                     k, v = line.split(":", 1)
                     vals[k.strip()] = v.strip()
-        if vals.get("kernel_source_sha") != kernel_source_hash():
+        if vals.get("kernel_source_sha") != kernel_source_hash(files):
             return None
         return float(vals["dram_bytes_per_launch"])
     except Exception:
@@ -457,7 +462,8 @@ def run_batch(args):
                                for t in tune["tried"]]},
         "plain_per_eye_calls": {"ms_per_step": plain_ms, "value": px / (plain_ms / 1000.0) / 1e6, "unit": UNIT},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "raster_kernel (persistent)",
+                     "traffic": ncu_traffic("raster_batch128_%s_persistent" % args.tex),
+                     "kernel": "raster_kernel (persistent)",
                      "peak_source": peak_kind + " (HBM copy)", "algorithmic_bytes_per_launch": raster_bytes,
                      "unique_texels_per_step": uniq, "ms_per_launch": mean_raster},
         "gpu_launches": 4 * args.steps,
@@ -562,7 +568,8 @@ def run_refine(args):
                                "weights", "refine_kernel": args.refine_kernel,
                    "l2": "flushed (256 MiB write) between steps, outside the timed events"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": ncu_traffic(REFINE_PROFILE, REFINE_SOURCES) if args.refine_kernel == "fused" else None,
                      "kernel": "refine_fused_kernel" if args.refine_kernel == "fused" else "conv_mma_kernel x3",
                      "peak_source": peak_kind + " bf16 (burst)", "flop_per_pixel": REFINE_FLOP_PER_PX},
         "gpu_launches": (1 if args.refine_kernel == "fused" else 3) * args.steps,
@@ -735,7 +742,8 @@ def run_learned(args):
                          "value": px / (statistics.mean(ms_plain) / 1000.0) / 1e6, "unit": UNIT},
         "refine_kernel": {"ms_per_launch_2_eyes": kern, "value": px / (kern / 1000.0) / 1e6, "unit": UNIT},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "refine_fused_kernel",
+                     "frac": achieved / peak, "traffic": ncu_traffic(REFINE_PROFILE, REFINE_SOURCES),
+                     "kernel": "refine_fused_kernel",
                      "peak_source": peak_kind + " bf16 (burst)", "flop_per_pixel": REFINE_FLOP_PER_PX,
                      "algorithmic_flop_per_launch": REFINE_FLOP_PER_PX * px},
         "quality": {"vs": "dense reference (method, %d views, %d^2 meshes, 2x2 supersampled)" % (
@@ -848,7 +856,7 @@ def run_ours(args):
     achieved = raster_bytes / (mean_raster / 1000.0) / 1e9
     step_bytes = raster_bytes + mesh_bytes
     step_achieved = step_bytes / (total_ms / args.steps / 1000.0) / 1e9
-    traffic = ncu_traffic(args.workload, args.tex, args.tile)
+    traffic = ncu_traffic("raster_%s_%s_%s" % (args.workload, args.tex, args.tile))
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
