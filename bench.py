@@ -163,28 +163,56 @@ def kernel_source_hash(files=RASTER_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-E2E_WHAT = ("%s: host poses in, both eye images delivered to pinned host memory by the context's copy "
-            "stream while the next frame renders; wall clock over the run, with the 256 MiB L2 flush before "
-            "each frame inside it; frame_latency_ms: one frame at a time, call to delivery")
+E2E_WHAT = ("%s: host poses in, %s delivered to pinned host memory by the context's copy stream while "
+            "the next frame renders; wall clock over the run, with the 256 MiB L2 flush before each frame "
+            "inside it; frame_latency_ms: one frame at a time, call to delivery")
 
 
-def host_e2e(r, heads, shapes, flush, stream, steps, px_per_step, world, refined=False):
+def host_memory_available() -> int:
+    """Bytes of host memory this process may still use: the smaller of the
+    kernel's MemAvailable and the cgroup's remaining limit (0 if unknown)."""
+    avail = 0
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        return 0
+    try:
+        with open("/sys/fs/cgroup/memory.max") as fh:
+            lim = fh.read().strip()
+        if lim != "max":
+            with open("/sys/fs/cgroup/memory.current") as fh:
+                avail = min(avail, int(lim) - int(fh.read().strip()))
+    except (OSError, ValueError):
+        pass
+    return max(avail, 0)
+
+
+def host_e2e(r, heads, shapes, flush, stream, steps, px_per_step, world, form="plain", in_flight=None):
     """Whole-job throughput of lf_render_host over `steps` pipelined frames
-    (wall clock, max over ranks) and the mean single-frame latency."""
+    (wall clock, max over ranks) and the mean single-frame latency.  At most
+    `in_flight` frames are undelivered at a time, each with its own pinned
+    host images (default: as many as the library pipelines)."""
     import torch
     import paper_1810_08860_gb300 as lfm
 
-    sets = [[torch.empty(sh, dtype=torch.float32, pin_memory=True) for sh in shapes]
-            for _ in range(lfm.HOST_FRAMES_IN_FLIGHT + 1)]
+    n_sets = in_flight or lfm.HOST_FRAMES_IN_FLIGHT
+    sets = [[torch.empty(sh, dtype=torch.float32, pin_memory=True) for sh in shapes] for _ in range(n_sets)]
     for k in range(len(sets)):  # warm the slots
-        r.render_host(heads[k % len(heads)], out=sets[k], refined=refined, stream=stream)
+        r.render_host(heads[k % len(heads)], out=sets[k], form=form, stream=stream)
     r.host_wait()
     torch.cuda.synchronize()
     barrier_all()
     t0 = time.perf_counter()
+    issued = []
     for k in range(steps):
+        if k >= n_sets:
+            r.host_wait(issued[k - n_sets])  # its host images are about to be reused
         flush.zero_()
-        r.render_host(heads[k % len(heads)], out=sets[k % len(sets)], refined=refined, stream=stream)
+        f, _ = r.render_host(heads[k % len(heads)], out=sets[k % len(sets)], form=form, stream=stream)
+        issued.append(f)
     if r.host_wait() != 0:
         raise RuntimeError("a frame delivered to host memory reported device errors")
     total_ms = max_over_ranks(1000.0 * (time.perf_counter() - t0))
@@ -193,7 +221,7 @@ def host_e2e(r, heads, shapes, flush, stream, steps, px_per_step, world, refined
         flush.zero_()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        f, _ = r.render_host(heads[k % len(heads)], out=sets[0], refined=refined, stream=stream)
+        f, _ = r.render_host(heads[k % len(heads)], out=sets[0], form=form, stream=stream)
         r.host_wait(f)
         lat.append(1000.0 * (time.perf_counter() - t1))
     return whole_job_rate(px_per_step * steps, total_ms, world), statistics.mean(lat)
@@ -460,6 +488,19 @@ def run_batch(args):
     rt.close()
     total_ms = max_over_ranks(sum(x.elapsed_time(y) for x, y in ev))
     value = whole_job_rate(px * args.steps, total_ms, world)
+    # end to end through lf_render_host (batch form): all eyes delivered to
+    # pinned host memory, two frames in flight, each with its own host images
+    need = 2 * px * 16
+    avail = host_memory_available()
+    e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": 160 * len(eyes), "d2h_bytes_per_step": px * 16}
+    if avail >= 4 * need:
+        e2e["value"], e2e["frame_latency_ms"] = host_e2e(r, [eyes], [o.shape for o in outs], flush, stream,
+                                                         max(3, args.steps // 4), px, world, form="batch",
+                                                         in_flight=2)
+        e2e["what"] = E2E_WHAT % ("lf_render_host (batch)", "all %d eye images" % len(eyes))
+    else:
+        e2e["skipped"] = "host memory: %.1f GB available, %.1f GB of pinned images needed (x4 margin)" % (
+            avail / 1e9, need / 1e9)
     peak, peak_kind = measured_peak()
     tex_bytes = {"f32": 16, "u8": 4, "bf16": 8, "fp8": 4}[args.tex]
     raster_bytes = uniq * tex_bytes + px * 16
@@ -481,6 +522,7 @@ def run_batch(args):
                      "kernel": "raster_kernel (persistent)",
                      "peak_source": peak_kind + " (HBM copy)", "algorithmic_bytes_per_launch": raster_bytes,
                      "unique_texels_per_step": uniq, "ms_per_launch": mean_raster},
+        "e2e": e2e,
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
@@ -569,10 +611,25 @@ def run_refine(args):
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    # end to end: the pair from pinned host memory, lf_refine, the result back
+    # to pinned host memory, one step at a time (events around all three)
+    hx = x.cpu().pin_memory()
+    hy = torch.empty(hx.shape, dtype=torch.float32, pin_memory=True)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(max(3, args.steps // 4))]
+    for a, b in e2e_ev:
+        flush.zero_()
+        a.record(stream)
+        x.copy_(hx, non_blocking=True)
+        r.refine(x, out=y)
+        hy.copy_(y, non_blocking=True)
+        b.record(stream)
+    torch.cuda.synchronize()
     r.get_refiner()
     ms = [a.elapsed_time(b) for a, b in ev]
     px = 2 * 1440 * 1600
     mean = max_over_ranks(sum(ms)) / len(ms)
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev)) / len(e2e_ev)
     peak, peak_kind = measured_tensor_peak()
     achieved = REFINE_FLOP_PER_PX * px / (mean / 1000.0) / 1e12
     result = {
@@ -587,6 +644,10 @@ def run_refine(args):
                      "traffic": ncu_traffic(REFINE_PROFILE, REFINE_SOURCES) if args.refine_kernel == "fused" else None,
                      "kernel": "refine_fused_kernel" if args.refine_kernel == "fused" else "conv_mma_kernel x3",
                      "peak_source": peak_kind + " bf16 (burst)", "flop_per_pixel": REFINE_FLOP_PER_PX},
+        "e2e": {"value": whole_job_rate(px, e2e_ms, world), "unit": UNIT, "h2d_bytes_per_step": px * 16,
+                "d2h_bytes_per_step": px * 16,
+                "what": "the pair copied from pinned host memory, lf_refine, the result copied back to pinned "
+                        "host memory; events around all three, one step at a time"},
         "gpu_launches": (1 if args.refine_kernel == "fused" else 3) * args.steps,
         "clocks": clk,
     }
@@ -735,7 +796,7 @@ def run_learned(args):
     ms_kernel = timed(lambda k: rf.refine(pair, out=refined), max(20, args.steps // 4))
     # end to end: host poses in, both refined images delivered to pinned host memory
     e2e_value, e2e_latency = host_e2e(rf, heads, [o.shape for o in outs], flush, stream,
-                                      max(20, args.steps // 4), px, world, refined=True)
+                                      max(20, args.steps // 4), px, world, form="refined")
     st = rf.get_refiner()  # raises if the fused kernel reported a failed wait
     total = max_over_ranks(sum(ms_refined))
     value = whole_job_rate(px * args.steps, total, world)
@@ -771,7 +832,7 @@ def run_learned(args):
                      "ms_per_step_wall": 1000.0 * train_s / max(1, args.train_steps), "loss_trace": losses,
                      "pairs_s": pairs_s, "scene_generation_s": gen_s, "adam_step": st["step"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 320, "d2h_bytes_per_step": px * 16,
-                "frame_latency_ms": e2e_latency, "what": E2E_WHAT % "lf_render_host (refined)"},
+                "frame_latency_ms": e2e_latency, "what": E2E_WHAT % ("lf_render_host (refined)", "both refined eye images")},
         "gpu_launches": 6 * args.steps,
         "clocks": clk,
     }
@@ -890,7 +951,7 @@ def run_ours(args):
         "active_views_per_step": statistics.mean(active),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 160 * len(heads[0]),
                 "d2h_bytes_per_step": out_bytes, "frame_latency_ms": e2e_latency,
-                "what": E2E_WHAT % "lf_render_host"},
+                "what": E2E_WHAT % ("lf_render_host", "both eye images")},
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }

@@ -239,23 +239,29 @@ LF_API lf_status lf_render_inspect(lf_ctx* ctx, const lf_pose* eye, const lf_int
 LF_API lf_status lf_render_static(lf_ctx* ctx, const lf_pose* eye, const lf_intrinsics* intr, float* out_rgba,
                                   void* stream);
 
+/* What lf_render_host renders. */
+typedef enum {
+  LF_HOST_PLAIN = 0,    /* lf_render */
+  LF_HOST_REFINED = 1,  /* lf_render_refined (the plain method if no refiner is loaded) */
+  LF_HOST_BATCH = 2     /* lf_render_batch's persistent raster over all eyes, launched without a graph */
+} lf_host_form;
+
 /*
- * Frames delivered to host memory: the render of lf_render (or of
- * lf_render_refined when `refined` is 1) followed by the device-to-host copy
- * of its images, pipelined so that the copy of one frame overlaps the
- * rendering of the next - a client that reads its pixels back (an encoder, a
+ * Frames delivered to host memory: a render (see lf_host_form) followed by
+ * the device-to-host copy of its images, pipelined so that the copy of one
+ * frame overlaps the rendering of the next - a client that reads its pixels back (an encoder, a
  * compositor on another device, a file writer) pays max(render, copy) per
  * frame instead of their sum.  The paper has no counterpart: its renderer
  * displays from the GPU (Sec. 4.2).
  * The frame renders on `stream` into one of LF_HOST_FRAMES_IN_FLIGHT device
  * image slots the context owns; a copy stream of the context then copies the
  * images, and the frame's device error word, to host memory.
- *   n_eyes, eyes, intr  as for lf_render
+ *   n_eyes, eyes, intr  as for lf_render (1 .. lf_config.max_eyes eyes, mixed sizes allowed)
  *   host_rgba  n_eyes host pointers, each height*width*4 floats (the output
  *              of lf_render).  Pinned memory (cudaHostAlloc, cudaHostRegister)
  *              lets the copy run asynchronously; with pageable memory the call
  *              returns only after its own copy has finished (no overlap).
- *   refined    0: the plain method; 1: refined (plain if no refiner is loaded)
+ *   form       LF_HOST_PLAIN, LF_HOST_REFINED or LF_HOST_BATCH
  *   frame      out (may be NULL): the frame's number, counting from 0 per context
  *   stream     cudaStream_t the render runs on, in order with the caller's work
  * The images of a frame are complete, and its host buffers may be read or
@@ -263,12 +269,12 @@ LF_API lf_status lf_render_static(lf_ctx* ctx, const lf_pose* eye, const lf_intr
  * LF_HOST_FRAMES_IN_FLIGHT frames are undelivered, the call first waits for
  * the oldest.  lf_get_stats does not report these frames; lf_host_wait
  * returns their error bits.  Errors: as lf_render, plus LF_ERR_INVALID_ARG for
- * a NULL host pointer or a `refined` other than 0 or 1.  On an error nothing of
- * the frame is left running.
+ * a NULL host pointer or an unknown form.  On an error nothing of the frame is
+ * left running.
  */
 #define LF_HOST_FRAMES_IN_FLIGHT 3
 LF_API lf_status lf_render_host(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
-                                float* const* host_rgba, int32_t refined, int64_t* frame, void* stream);
+                                float* const* host_rgba, lf_host_form form, int64_t* frame, void* stream);
 
 /*
  * Wait until frame `frame` of lf_render_host, and every earlier frame, is in

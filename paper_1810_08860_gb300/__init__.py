@@ -71,6 +71,7 @@ EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_
            "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined", "lf_render_host",
            "lf_host_wait"]
 HOST_FRAMES_IN_FLIGHT = 3
+HOST_FORMS = {"plain": 0, "refined": 1, "batch": 2}
 
 REFINE_N_PARAMS = 11011
 REFINE_SHAPES = [("W1", (32, 3, 3, 3)), ("b1", (32,)), ("W2", (32, 32, 3, 3)), ("b2", (32,)),
@@ -258,12 +259,14 @@ class Renderer:
         self._check(self.lib.lf_render(self.ctx, len(eyes), poses, intr, ptrs, _stream_handle(stream)), "lf_render")
         return out
 
-    def render_host(self, eyes, out=None, refined: bool = False, stream=None):
+    def render_host(self, eyes, out=None, form: str = "plain", stream=None):
         """Render eye views and deliver them to host memory (lf_render_host): the
         device->host copy of this frame overlaps the rendering of the next.
-        `out` holds one contiguous float32 CPU tensor (H, W, 4) per eye, pinned
-        for an asynchronous copy (allocated pinned when None).  Returns
-        (frame, out); the images are complete once host_wait(frame) returns."""
+        form: "plain" (lf_render), "refined" (lf_render_refined) or "batch" (the
+        persistent raster of lf_render_batch).  `out` holds one contiguous
+        float32 CPU tensor (H, W, 4) per eye, pinned for an asynchronous copy
+        (allocated pinned when None).  Returns (frame, out); the images are
+        complete once host_wait(frame) returns."""
         import torch
         if out is None:
             out = [torch.empty((e.height, e.width, 4), dtype=torch.float32, pin_memory=True) for e in eyes]
@@ -275,7 +278,7 @@ class Renderer:
         poses, intr = self._eye_arrays(eyes)
         ptrs = (ctypes.c_void_p * len(out))(*[o.data_ptr() for o in out])
         frame = ctypes.c_int64(-1)
-        self._check(self.lib.lf_render_host(self.ctx, len(eyes), poses, intr, ptrs, 1 if refined else 0,
+        self._check(self.lib.lf_render_host(self.ctx, len(eyes), poses, intr, ptrs, HOST_FORMS[form],
                                             ctypes.byref(frame), _stream_handle(stream)), "lf_render_host")
         # keep the host buffers alive until their frame is delivered
         self._in_flight = [(f, o) for f, o in getattr(self, "_in_flight", []) if f > frame.value - HOST_FRAMES_IN_FLIGHT]

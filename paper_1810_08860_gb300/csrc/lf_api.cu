@@ -260,9 +260,21 @@ lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persis
   LF_CUDA(c, launch_tri_setup(a, s));
   LF_CUDA(c, launch_bin(a, s));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[2], s));
-  LF_CUDA(c, launch_raster(a, inspect, persistent, c->persistent_blocks, s));
+  // the persistent grid never exceeds the call's work items (tiles x strips >= tiles)
+  const int blocks = std::min(c->persistent_blocks, std::max(1, a.total_tiles));
+  LF_CUDA(c, launch_raster(a, inspect, persistent, blocks, s));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[3], s));
   c->timed_call = t;
+  return LF_OK;
+}
+
+// The persistent raster grid of lf_render_batch before any tuning: the
+// occupancy limit of CTAs per SM times the SM count.
+lf_status ensure_persistent_blocks(lf_ctx* c) {
+  if (c->persistent_blocks > 0) return LF_OK;
+  int per_sm = 0;
+  LF_CUDA(c, raster_occupancy(c->cfg.tile_w, c->cfg.tile_h, c->tex_fmt, &per_sm));
+  c->persistent_blocks = std::max(1, per_sm) * c->sm_count;
   return LF_OK;
 }
 
@@ -614,12 +626,7 @@ lf_status lf_render_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const 
   Layout L;
   if ((st = make_layout(c, n_eyes, eyes, intr, out_rgba, L)) != LF_OK) return st;
   if ((st = ensure_scratch(c, n_eyes, L.total_tiles)) != LF_OK) return st;
-  if (c->persistent_blocks <= 0) {
-    int per_sm = 0;
-    LF_CUDA(c, raster_occupancy(c->cfg.tile_w, c->cfg.tile_h, c->tex_fmt, &per_sm));
-    c->persistent_blocks = std::max(1, per_sm) * c->sm_count;
-  }
-  c->persistent_blocks = std::min(c->persistent_blocks, std::max(1, L.total_tiles));
+  if ((st = ensure_persistent_blocks(c)) != LF_OK) return st;
   // The graph depends on the layout and on every scratch address it names.
   std::vector<int64_t> sig = {n_eyes, L.total_tiles, c->n_views, c->G, c->tex_fmt, c->mesh_fmt,
                               (int64_t)(intptr_t)c->eyes.p, (int64_t)(intptr_t)c->eyes_f.p,
@@ -1122,7 +1129,8 @@ lf_status host_deliver_oldest(lf_ctx* c) {
 // Enqueue the render of one frame into `slot` and its copy to host memory.
 lf_status host_enqueue(lf_ctx* c, int slot, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
                        float* const* host_rgba, const std::vector<size_t>& off, const std::vector<size_t>& bytes,
-                       bool refined, cudaStream_t s) {
+                       lf_host_form form, cudaStream_t s) {
+  const bool refined = form == LF_HOST_REFINED && c->rf.loaded;
   auto& H = c->hp;
   unsigned char* img = static_cast<unsigned char*>(H.image[slot].p);
   std::vector<float*> dev(n_eyes), target(n_eyes);
@@ -1140,7 +1148,8 @@ lf_status host_enqueue(lf_ctx* c, int slot, int32_t n_eyes, const lf_pose* eyes,
   FrameArgs a = frame_args(c, L);
   unsigned char* counters = static_cast<unsigned char*>(H.counters.p) + kCounterBlock * slot;
   use_counters(a, counters);
-  if ((st = enqueue_frame(c, a, false, false, s)) != LF_OK) return st;
+  if (form == LF_HOST_BATCH && (st = ensure_persistent_blocks(c)) != LF_OK) return st;
+  if ((st = enqueue_frame(c, a, false, form == LF_HOST_BATCH, s)) != LF_OK) return st;
   if (refined)
     for (int e = 0; e < n_eyes; ++e)
       if ((st = refine_apply(c, 1, intr[e].width, intr[e].height, target[e], dev[e], s)) != LF_OK) return st;
@@ -1158,10 +1167,11 @@ lf_status host_enqueue(lf_ctx* c, int slot, int32_t n_eyes, const lf_pose* eyes,
 extern "C" {
 
 lf_status lf_render_host(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
-                         float* const* host_rgba, int32_t refined, int64_t* frame, void* stream) {
+                         float* const* host_rgba, lf_host_form form, int64_t* frame, void* stream) {
   lf_status st = check_ready(c);
   if (st != LF_OK) return st;
-  if (refined != 0 && refined != 1) return fail(c, LF_ERR_INVALID_ARG, "refined must be 0 or 1");
+  if (form != LF_HOST_PLAIN && form != LF_HOST_REFINED && form != LF_HOST_BATCH)
+    return fail(c, LF_ERR_INVALID_ARG, "unknown lf_host_form");
   if (n_eyes < 1 || n_eyes > c->cfg.max_eyes || !eyes || !intr || !host_rgba)
     return fail(c, LF_ERR_INVALID_ARG, "bad eye arguments");
   std::vector<size_t> off(n_eyes), bytes(n_eyes);
@@ -1181,7 +1191,7 @@ lf_status lf_render_host(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const l
   const int slot = (int)(H.issued % kHostSlots);
   LF_CUDA(c, ensure(H.image[slot], total));  // the slot's previous frame has been delivered
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = host_enqueue(c, slot, n_eyes, eyes, intr, host_rgba, off, bytes, refined == 1 && c->rf.loaded, s);
+  st = host_enqueue(c, slot, n_eyes, eyes, intr, host_rgba, off, bytes, form, s);
   if (st != LF_OK) {
     // leave nothing of the frame running: the caller may free its buffers
     cudaStreamSynchronize(s);

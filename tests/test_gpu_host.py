@@ -105,7 +105,7 @@ def test_refined_host_frames_equal_render_refined(lfmod, tiny):
         r.load_refiner(lfmod.init_refiner_params(3, out_scale=0.5))
         r.set_refine_kernel(kernel)
         pairs = _eyes(4, 93, w=80, h=72)
-        got = [r.render_host(pair, refined=True) for pair in pairs]
+        got = [r.render_host(pair, form="refined") for pair in pairs]
         r.host_wait()
         for (frame, out), pair in zip(got, pairs):
             ref = [o.cpu() for o in r.render_refined(pair)]
@@ -115,6 +115,33 @@ def test_refined_host_frames_equal_render_refined(lfmod, tiny):
                 assert not torch.equal(a, p)  # the refinement changed something
         r.get_refiner()  # raises if a wait of the fused kernel gave up
         r.close()
+
+
+def test_batch_form_equals_render_batch(lfmod, tiny):
+    # the persistent raster launched without a graph, into host memory, against
+    # the graph-replayed lf_render_batch of the same eyes (mixed sizes)
+    import torch
+
+    rng = scene.SplitMix64(94)
+    sizes = [(96, 64), (40, 33), (128, 128), (17, 131), (64, 64)]
+    eyes = [scene.head_pose_eyes(rng, w, h, 90.0, yaw_range=(-0.2, 0.2), pitch_deg=8.0, stereo=False)[0]
+            for w, h in sizes]
+    r = lfmod.Renderer(0, max_eyes=8)
+    r.load_views(tiny)
+    r.build_meshes(tiny)
+    frames = [r.render_host(eyes, form="batch") for _ in range(2)]
+    r.host_wait()
+    ref = [o.cpu() for o in r.render_batch(eyes)]
+    for frame, out in frames:
+        for k, (a, b) in enumerate(zip(out, ref)):
+            assert torch.equal(a, b), (frame, k)
+    # a smaller batch afterwards does not shrink the persistent grid of later ones
+    small = [r.render_host(eyes[:1], form="batch")]
+    again = r.render_host(eyes, form="batch")
+    r.host_wait()
+    assert torch.equal(small[0][1][0], ref[0])
+    assert all(torch.equal(a, b) for a, b in zip(again[1], ref))
+    r.close()
 
 
 def test_overflowing_frame_reports_capacity(lfmod, tiny):
@@ -151,7 +178,7 @@ def test_host_argument_errors(lfmod, tiny):
     null = (ctypes.c_void_p * 1)(None)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     frame = ctypes.c_int64(-7)
-    assert r.lib.lf_render_host(r.ctx, 1, poses, intr, ptrs, 2, ctypes.byref(frame), stream) == 1
+    assert r.lib.lf_render_host(r.ctx, 1, poses, intr, ptrs, 3, ctypes.byref(frame), stream) == 1
     assert r.lib.lf_render_host(r.ctx, 1, poses, intr, null, 0, ctypes.byref(frame), stream) == 1
     assert r.lib.lf_render_host(r.ctx, 3, poses, intr, ptrs, 0, ctypes.byref(frame), stream) == 1
     assert frame.value == -7  # no frame was issued
