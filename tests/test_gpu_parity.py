@@ -133,6 +133,26 @@ def test_one_pixel_and_empty_eyes(tiny_renderer, tiny):
     assert float(got["rgba"].abs().max()) == 0.0
 
 
+def test_eye_outside_the_capture_sphere(tiny_renderer, tiny):
+    """Degenerate eye positions for the sphere crossing p of Eq. 2: behind the
+    capture sphere looking through it (the outer rays miss the sphere, the
+    others take the far crossing, the larger root), on the sphere, and outside
+    looking away (both roots negative: no crossing, an empty image)."""
+    R = scene.look_rotation([0.0, 0.0, 1.0])
+    K = np.array([64.0, 64.0, 64.0, 48.0])  # 128 x 96 at 90 degrees
+    behind = scene.Eye(scene.pose_array(R, (0.0, 0.0, -0.6)), K, 128, 96)
+    got, ref = _check_full_frame(tiny_renderer, tiny, behind)
+    valid = ref["rgba"][..., 3] > 0
+    assert 0 < valid.sum() < valid.size
+    on = scene.Eye(scene.pose_array(R, (0.0, 0.0, -0.35)), K, 128, 96)
+    got, ref = _check_full_frame(tiny_renderer, tiny, on)
+    assert (ref["rgba"][..., 3] > 0).sum() > 0
+    away = scene.Eye(scene.pose_array(R, (0.0, 0.0, 0.6)), K, 128, 96)
+    got, _ = _check_full_frame(tiny_renderer, tiny, away)
+    assert got["active"].sum() == 0
+    assert float(got["rgba"].abs().max()) == 0.0
+
+
 def test_tile_shapes_identical(lfmod, tiny, tiny_renderer):
     eye = tiny.eyes[0]
     base = tiny_renderer.render([eye])[0].cpu()
