@@ -133,6 +133,38 @@ def test_one_pixel_and_empty_eyes(tiny_renderer, tiny):
     assert float(got["rgba"].abs().max()) == 0.0
 
 
+def test_widest_and_tallest_eyes(tiny_renderer, tiny):
+    """Eye views at the 32,767-pixel limit of lf_render in one dimension
+    (2,048 screen tiles across, ragged in the other dimension)."""
+    pose = tiny.eyes[0].pose
+    for w, h, K in [(32767, 3, [8000.0, 8000.0, 16383.5, 1.5]), (5, 32767, [8000.0, 8000.0, 2.5, 16383.5])]:
+        got, ref = _check_full_frame(tiny_renderer, tiny, scene.Eye(pose, np.array(K), w, h))
+        assert (ref["rgba"][..., 3] > 0).sum() > 1000
+
+
+def test_65536_views_the_maximum(lfmod):
+    """The largest view count lf_load_views accepts: 65,536 Fibonacci views of
+    8x8 pixels with 2x2 depth grids, about 8,000 of them selected by one eye
+    (2,048 view-mask words per screen tile, hundreds of views per tile)."""
+    n = 65536
+    prims = scene.sphere_scene(4, 8, forward_cone_deg=35.0)
+    poses, intr = scene.rig_from_directions(scene.fibonacci_directions(n), scene.CAPTURE_RADIUS, 8, 8, 120.0)
+    rgba, grid, _ = scene.ray_cast(prims, poses, intr, 8, 8, grid_n=2)
+    r_disk = 1.2 * math.sqrt(4.0 * math.pi * scene.CAPTURE_RADIUS ** 2 / n)  # 1.2 x the mean spacing
+    lf = scene.LightField(poses=poses, intr=intr, width=8, height=8, images=rgba, grid_n=2, depth=grid,
+                          disk_c=poses[:, 9:12].astype(np.float32), disk_r=np.full(n, r_disk, np.float32),
+                          sphere_c=np.zeros(3), sphere_r=scene.CAPTURE_RADIUS, prims=prims, name="many")
+    r = lfmod.Renderer(0)
+    r.load_views(lf)
+    r.build_meshes(lf)
+    R = scene.look_rotation([0.0, 0.0, 1.0])
+    eye = scene.Eye(scene.pose_array(R, (0.02, -0.01, 0.03)), np.array([40.0, 40.0, 40.0, 30.0]), 80, 60)
+    got, ref = _check_full_frame(r, lf, eye)
+    assert got["active"].sum() > 4000
+    assert (ref["rgba"][..., 3] > 0).all()
+    r.close()
+
+
 def test_eye_outside_the_capture_sphere(tiny_renderer, tiny):
     """Degenerate eye positions for the sphere crossing p of Eq. 2: behind the
     capture sphere looking through it (the outer rays miss the sphere, the
