@@ -14,8 +14,28 @@
 #include <vector>
 
 #include "lf_internal.h"
+#include "lf_launch.h"
 
 using namespace lfk;
+
+cudaError_t lfk::ensure_dynamic_smem(const void* kernel, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<int, const void*>, int>> done;  // (device, kernel) -> bytes set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& d : done)
+    if (d.first.first == dev && d.first.second == kernel) {
+      if (d.second >= bytes) return cudaSuccess;
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e == cudaSuccess) d.second = bytes;
+      return e;
+    }
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.push_back({{dev, kernel}, bytes});
+  return e;
+}
 
 namespace {
 

@@ -23,6 +23,7 @@
 #include <cstdint>
 
 #include "lf_internal.h"
+#include "lf_launch.h"
 
 namespace lfk {
 
@@ -477,13 +478,8 @@ cudaError_t launch_conv_t(const RefineConvArgs& a, cudaStream_t s) {
   const int taps = IN == kConvInRGBA ? 1 : 9;
   const int in_bytes = IN == kConvInRGBA ? 256 * kRowB : kHaloW * kHaloH * kRowB;
   const int smem = taps * COUT * kRowB + in_bytes;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(conv_mma_kernel<IN, COUT, EPI>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(conv_mma_kernel<IN, COUT, EPI>), smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((a.W + kRTW - 1) / kRTW, (a.H + kRTH - 1) / kRTH, a.n);
   conv_mma_kernel<IN, COUT, EPI><<<grid, 256, smem, s>>>(a);
   return cudaGetLastError();
@@ -495,12 +491,8 @@ cudaError_t launch_wgrad_t(const RefineWgradArgs& a, cudaStream_t s) {
   const int a_bytes = MODE == 1 ? 256 * kRowB : kHaloW * kHaloH * kRowB;
   int smem = g_bytes + a_bytes;
   if (MODE == 1 && smem < 8 * 32 * 32 * 4) smem = 8 * 32 * 32 * 4;  // the cross-warp reduction reuses it
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(wgrad_kernel<MODE>), smem);
+  if (e != cudaSuccess) return e;
   wgrad_kernel<MODE><<<a.n_ctas, MODE == 1 ? 256 : 288, smem, s>>>(a);
   return cudaGetLastError();
 }

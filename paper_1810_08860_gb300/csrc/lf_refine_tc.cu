@@ -40,6 +40,7 @@
 #include <cstdint>
 
 #include "lf_internal.h"
+#include "lf_launch.h"
 
 namespace lfk {
 
@@ -471,12 +472,8 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
 cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, const float* params,
                                 const __nv_bfloat16* packed, int sm_count, int32_t* error, cudaStream_t s) {
   (void)params;  // the biases are packed with the weights
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(refine_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(refine_fused_kernel), kSmemBytes);
+  if (e != cudaSuccess) return e;
   FusedArgs a;
   a.n = n;
   a.H = h;

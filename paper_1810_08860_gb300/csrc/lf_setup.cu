@@ -20,6 +20,7 @@
 #include <cuda_fp16.h>
 
 #include "lf_internal.h"
+#include "lf_launch.h"
 
 namespace lfk {
 
@@ -805,13 +806,8 @@ cudaError_t launch_bin(const FrameArgs& a, cudaStream_t s) {
 
 cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s) {
   const size_t limit = 96 * 1024;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t err = cudaFuncSetAttribute(tri_setup_kernel<kSetupBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)limit + 64);
-    if (err != cudaSuccess) return err;
-    attr_done = true;
-  }
+  cudaError_t err = ensure_dynamic_smem(reinterpret_cast<const void*>(tri_setup_kernel<kSetupBlock>), (int)limit + 64);
+  if (err != cudaSuccess) return err;
   const int rows = setup_band_rows(a.G, limit);
   const size_t bytes = (size_t)(rows + 1) * vertex_row_stride(a.G) * kVtxBytes + 2 * 2 * (size_t)(a.G - 1) * rows + 64;
   dim3 grid(a.n_views, a.n_eyes);
