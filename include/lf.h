@@ -151,8 +151,9 @@ LF_API void lf_destroy(lf_ctx* ctx);
  *   sphere_r    its radius in metres (> 0); p is the larger-root crossing of
  *               each eye ray with this sphere
  *   fmt         device storage of the textures
- * Replaces any views loaded before (meshes must then be rebuilt).  Blocks
- * until the upload is complete.  Errors: LF_ERR_INVALID_ARG, LF_ERR_OOM,
+ * Replaces any views loaded before (meshes must then be rebuilt); first waits
+ * for all work on the device, since renders in flight may read the old views.
+ * Blocks until the upload is complete.  Errors: LF_ERR_INVALID_ARG, LF_ERR_OOM,
  * LF_ERR_UNSUPPORTED, LF_ERR_CUDA.
  */
 LF_API lf_status lf_load_views(lf_ctx* ctx, int32_t n_views, const lf_pose* poses, const lf_intrinsics* intr,
@@ -169,7 +170,8 @@ LF_API lf_status lf_load_views(lf_ctx* ctx, int32_t n_views, const lf_pose* pose
  *   depth    host, n_views*grid_n*grid_n floats, row k then column j, z-depth
  *            in the view's camera frame (> 0)
  *   fmt      device storage of the depth grids
- * Requires lf_load_views first (else LF_ERR_STATE).  Blocks until done.
+ * Requires lf_load_views first (else LF_ERR_STATE).  Waits for all work on the
+ * device first (renders in flight may read the old meshes); blocks until done.
  */
 LF_API lf_status lf_build_view_meshes(lf_ctx* ctx, int32_t grid_n, const float* depth, lf_mesh_format fmt);
 
@@ -342,8 +344,9 @@ typedef enum {
 } lf_refine_kernel;
 
 /* Load refinement weights (copied; the caller keeps `params`).  Resets the
- * Adam moments and step to 0.  LF_ERR_INVALID_ARG on a NULL or non-finite
- * parameter. */
+ * Adam moments and step to 0.  Waits for all work on the device first (a
+ * refinement in flight may read the old weights).  LF_ERR_INVALID_ARG on a
+ * NULL or non-finite parameter. */
 LF_API lf_status lf_load_refiner(lf_ctx* ctx, const float* params);
 
 /* Choose the inference kernel of lf_refine and lf_render_refined (default

@@ -298,6 +298,16 @@ lf_status ensure_persistent_blocks(lf_ctx* c) {
   return LF_OK;
 }
 
+// Before a load replaces views, meshes or refiner weights: wait until no
+// earlier work of any call can still read them.  Renders, refinements and
+// host-delivered frames run on caller streams the context does not keep, so
+// the whole device is synchronised (loads are rare and block anyway).
+lf_status quiesce(lf_ctx* c) {
+  LF_CUDA(c, cudaSetDevice(c->device));
+  LF_CUDA(c, cudaDeviceSynchronize());
+  return LF_OK;
+}
+
 lf_status check_ready(lf_ctx* c) {
   if (!c) return LF_ERR_INVALID_ARG;
   if (c->n_views <= 0) return fail(c, LF_ERR_STATE, "views not loaded");
@@ -507,8 +517,8 @@ lf_status lf_load_views(lf_ctx* c, int32_t n_views, const lf_pose* poses, const 
     V.disk_r = disk_r[v];
     V.tex_scale = 1.0f;
   }
-  LF_CUDA(c, cudaSetDevice(c->device));
-  if (c->has_call && c->last_stream) LF_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  lf_status st = quiesce(c);
+  if (st != LF_OK) return st;
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_sig.clear(); }
   c->n_views = 0;
   c->G = 0;
@@ -565,8 +575,8 @@ lf_status lf_build_view_meshes(lf_ctx* c, int32_t grid_n, const float* depth, lf
   if (c->n_views <= 0) return fail(c, LF_ERR_STATE, "views not loaded");
   if (grid_n < 2 || grid_n > kMaxGridForSetup || !depth) return fail(c, LF_ERR_INVALID_ARG, "bad mesh arguments");
   if (fmt != LF_MESH_F32_DEPTH && fmt != LF_MESH_F16_OFFSET) return fail(c, LF_ERR_INVALID_ARG, "bad mesh format");
-  LF_CUDA(c, cudaSetDevice(c->device));
-  if (c->has_call && c->last_stream) LF_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  lf_status st = quiesce(c);
+  if (st != LF_OK) return st;
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_sig.clear(); }
   c->G = 0;
   cudaStream_t s = c->work_stream;
@@ -1005,7 +1015,8 @@ lf_status lf_load_refiner(lf_ctx* c, const float* params) {
   for (int i = 0; i < kRefineParams; ++i)
     if (!(params[i] == params[i]) || params[i] > 1e30f || params[i] < -1e30f)
       return fail(c, LF_ERR_INVALID_ARG, "non-finite refiner parameter");
-  LF_CUDA(c, cudaSetDevice(c->device));
+  lf_status st = quiesce(c);  // a refinement in flight may still read the weights
+  if (st != LF_OK) return st;
   LF_CUDA(c, ensure(c->rf.state, sizeof(float) * 4 * kRefineParams));
   LF_CUDA(c, ensure(c->rf.packed, sizeof(__nv_bfloat16) * kRefinePackedElems));
   LF_CUDA(c, ensure(c->rf.scal, 64));
