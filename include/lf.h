@@ -386,6 +386,47 @@ LF_API lf_status lf_refine_train_step(lf_ctx* ctx, int32_t n_images, int32_t wid
 LF_API lf_status lf_render_refined(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
                                    float* const* out_rgba, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Prefiltering the light field images (Sec. 5).  Each image i of the
+ * real-time model is replaced by a Monte Carlo estimate (Eq. 5) of the 4D
+ * integral of Eq. 4 over the disk D_i (ray origins) and the pixel basis
+ * (ray targets on view i's own mesh) of a higher-quality model's ray query:
+ *     I'_i(s', t') = sum_j rho_j sigma_j Lbar_j / sum_j rho_j sigma_j.
+ * sigma is the separable Lanczos-2 kernel (Sec. 5.1) and rho the linear disk
+ * kernel.  The J samples are shared by every pixel of every view.  Sample j
+ * puts the ray origin on the capture sphere at chord distance r_i sqrt(a) from
+ * the disk centre, at angle 2 pi b from view i's image x axis (uniform in area),
+ * 1e-5 R inside the sphere, with weight rho = 1 - sqrt(a); the ray passes
+ * through the mesh point of image point (s' + ds, t' + dt), clamped to the
+ * image.  Lbar for the rays of one (view, sample), which share their origin,
+ * is a render of the dense model (lf_render_batch on `dense`) at that origin
+ * with view i's rotation and intrinsics times `supersample`, read by a
+ * bilinear filter at each mesh point's projection, on colour premultiplied by
+ * the render's alpha.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  float a, b;    /* aperture: a in [0, 1] (chord r sqrt(a)), b in [0, 1] (angle 2 pi b) */
+  float ds, dt;  /* pixel-basis offset in pixels, each in [-2, 2] */
+} lf_prefilter_sample;
+
+/*
+ * Prefilter views first_view .. first_view + n_views - 1 of the model loaded
+ * on `ctx` (views and meshes), with Lbar from the model loaded on `dense` (a
+ * second context on the same device, created with max_eyes >= n_samples).
+ *   samples     n_samples (1 .. dense max_eyes) samples (host)
+ *   supersample render scale, 1 .. 4 (render width and height <= 32767)
+ *   out_rgba    device, n_views x H x W x 4 floats, caller-owned: per pixel
+ *               (rgb, 1) where the ratio's denominator is > 0, else (0,0,0,0);
+ *               not clamped (the Lanczos lobes can overshoot [0, 1])
+ *   stream      cudaStream_t to run on
+ * Uses per-call scratch of n_samples x supersample^2 x W x H x 16 bytes on
+ * `ctx`.  Blocks until done.  Errors: LF_ERR_INVALID_ARG, LF_ERR_STATE (either
+ * model not loaded), LF_ERR_CAPACITY (a dense render overflowed its scratch:
+ * raise the dense context's tri_capacity), LF_ERR_CUDA.
+ */
+LF_API lf_status lf_prefilter(lf_ctx* ctx, lf_ctx* dense, int32_t first_view, int32_t n_views, int32_t n_samples,
+                              const lf_prefilter_sample* samples, int32_t supersample, float* out_rgba, void* stream);
+
 /* Counters of the last render call; synchronises with its stream. */
 LF_API lf_status lf_get_stats(lf_ctx* ctx, lf_stats* out);
 

@@ -131,13 +131,13 @@ def _bilinear_premultiplied(img, u, v):
 
 
 def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=None, threads=None,
-              renders=None) -> np.ndarray:
+              renders=None, details: bool = False):
     """Eq. 5 for view `view` of the real-time model `target`, with Lbar from
     the light field `dense`.  samples: J x 4 (a, b, ds, dt).  pixels: K x 2
     integer (i, j), or None for the whole image.  Returns H x W x 4 (or K x 4)
-    FP64.  `renders` may pass the J renders (from virtual_renders) in."""
-    import oracle
-
+    FP64.  `renders` may pass the J renders (from virtual_renders) in.  With
+    details, returns a dict that also holds the denominator and the sum of
+    |rho sigma| alpha (the error magnification of the ratio)."""
     samples = np.asarray(samples, dtype=np.float64).reshape(-1, 4)
     W, H = target.width, target.height
     if pixels is None:
@@ -151,6 +151,7 @@ def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=No
     Ks, _, _ = virtual_intrinsics(target, view, supersample)
     num = np.zeros((pix.shape[0], 3))
     den = np.zeros(pix.shape[0])
+    den_abs = np.zeros(pix.shape[0])
     for jdx, smp in enumerate(samples):
         a, b, ds, dt = smp
         w = sample_weight(smp)
@@ -162,11 +163,14 @@ def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=No
         val = _bilinear_premultiplied(renders[jdx], qx - 0.5, qy - 0.5)
         num += w * val[:, :3]
         den += w * val[:, 3]
+        den_abs += abs(w) * val[:, 3]
     out = np.zeros((pix.shape[0], 4))
     ok = den > 0.0
     out[ok, :3] = num[ok] / den[ok, None]
     out[ok, 3] = 1.0
-    return out.reshape(H, W, 4) if pixels is None else out
+    if pixels is None:
+        out, den, den_abs = out.reshape(H, W, 4), den.reshape(H, W), den_abs.reshape(H, W)
+    return {"rgba": out, "den": den, "den_abs": den_abs} if details else out
 
 
 def virtual_renders(target, dense, view: int, samples, supersample: int = 1, threads=None):

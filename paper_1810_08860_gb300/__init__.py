@@ -69,7 +69,7 @@ EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_
            "lf_render_batch", "lf_render_inspect", "lf_render_static", "lf_tune_batch", "lf_get_stats",
            "lf_status_string", "lf_last_error", "lf_load_refiner", "lf_refine_set_kernel", "lf_get_refiner",
            "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined", "lf_render_host",
-           "lf_host_wait"]
+           "lf_host_wait", "lf_prefilter"]
 HOST_FRAMES_IN_FLIGHT = 3
 HOST_FORMS = {"plain": 0, "refined": 1, "batch": 2}
 
@@ -92,6 +92,23 @@ def init_refiner_params(seed: int, out_scale: float = 0.1) -> np.ndarray:
             std = np.sqrt(2.0 / fan_in) * (out_scale if name == "W3" else 1.0)
             parts.append(rng.normal(0.0, std, shape))
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+def prefilter_samples(n: int, seed: int) -> np.ndarray:
+    """n stratified prefilter samples (a, b, ds, dt), float32 (lf_prefilter).
+    a is stratified over [0, 1) (n strata), b uniform; (ds, dt) lie on a
+    jittered k x k grid over [-2, 2)^2 (k = floor(sqrt(n)); the rest uniform),
+    so the Lanczos-2 weights of the set sum well above zero."""
+    rng = np.random.default_rng(seed)
+    s = np.empty((n, 4))
+    s[:, 0] = rng.permutation((np.arange(n) + rng.uniform(0.0, 1.0, n)) / n)
+    s[:, 1] = rng.uniform(0.0, 1.0, n)
+    k = int(np.sqrt(n))
+    cells = np.stack(np.meshgrid(np.arange(k), np.arange(k), indexing="ij"), -1).reshape(-1, 2)
+    s[:k * k, 2:] = -2.0 + 4.0 * (cells + rng.uniform(0.0, 1.0, (k * k, 2))) / k
+    s[k * k:, 2:] = rng.uniform(-2.0, 2.0, (n - k * k, 2))
+    s[:, 2:] = np.clip(s[:, 2:], -2.0, 2.0)
+    return s.astype(np.float32)
+
 
 _lib = None
 
@@ -145,6 +162,8 @@ def load_library(path: str = LIB_PATH):
     lib.lf_render_host.restype = ctypes.c_int
     lib.lf_host_wait.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_uint32)]
     lib.lf_host_wait.restype = ctypes.c_int
+    lib.lf_prefilter.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp]
+    lib.lf_prefilter.restype = ctypes.c_int
     lib.lf_status_string.argtypes = [ctypes.c_int]
     lib.lf_status_string.restype = ctypes.c_char_p
     lib.lf_last_error.argtypes = [vp]
@@ -226,6 +245,7 @@ class Renderer:
         self._check(self.lib.lf_load_views(self.ctx, n, poses, intr, ptrs, dc.ctypes.data, dr.ctypes.data, sc,
                                            float(lf.sphere_r), TEX_FORMATS[tex_format]), "lf_load_views")
         self.n_views = n
+        self._src_hw = (lf.height, lf.width)
 
     def build_meshes(self, lf, mesh_format: str = "f32"):
         """Upload the per-view depth grids (lf_build_view_meshes)."""
@@ -440,6 +460,26 @@ class Renderer:
         self._check(self.lib.lf_refine_train_step(self.ctx, n, w, h, ctypes.c_void_p(x.data_ptr()),
                                                   ctypes.c_void_p(t.data_ptr()), float(lr), _stream_handle(stream)),
                     "lf_refine_train_step")
+
+    def prefilter(self, dense, samples, first_view: int = 0, n_views=None, supersample: int = 1, out=None,
+                  stream=None):
+        """Prefiltered images of views first_view .. (lf_prefilter, Sec. 5 Eq. 5)
+        with Lbar from `dense` (a Renderer holding the higher-quality model,
+        created with max_eyes >= len(samples)).  samples: J x 4 (a, b, ds, dt).
+        Returns a CUDA tensor (n_views, H, W, 4) float32."""
+        import torch
+        S = np.ascontiguousarray(np.asarray(samples, dtype=np.float32).reshape(-1, 4))
+        if n_views is None:
+            n_views = self.n_views - first_view
+        H, W = self._src_hw
+        if out is None:
+            out = torch.empty((n_views, H, W, 4), dtype=torch.float32, device="cuda:%d" % self.device)
+        if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() or tuple(out.shape) != (n_views, H, W, 4):
+            raise ValueError("out must be a contiguous float32 CUDA tensor of shape (n_views, H, W, 4)")
+        self._check(self.lib.lf_prefilter(self.ctx, dense.ctx, int(first_view), int(n_views), S.shape[0],
+                                          S.ctypes.data_as(ctypes.c_void_p), int(supersample),
+                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "lf_prefilter")
+        return out
 
     def render_refined(self, eyes, out=None, stream=None):
         """lf_render followed by the refinement (plain render if no refiner is loaded)."""

@@ -15,6 +15,7 @@
 
 #include "lf_internal.h"
 #include "lf_launch.h"
+#include "lf_prefilter.h"
 
 using namespace lfk;
 
@@ -61,6 +62,7 @@ struct lf_ctx {
   double sphere_c[3] = {0, 0, 0};
   double sphere_r = 0;
   Buffer views, tex;
+  std::vector<ViewStatic> views_host;  // poses, intrinsics and disks as loaded
   // meshes
   int32_t G = 0;
   lf_mesh_format mesh_fmt = LF_MESH_F32_DEPTH;
@@ -104,6 +106,10 @@ struct lf_ctx {
     int64_t issued = 0, delivered = 0;
     uint32_t err_acc = 0;      // error bits of the frames delivered since the last lf_host_wait
   } hp;
+  // prefilter scratch (lf_prefilter)
+  struct Prefilter {
+    Buffer renders, params, err;
+  } pf;
 };
 
 namespace {
@@ -482,6 +488,7 @@ void lf_destroy(lf_ctx* ctx) {
     if (ctx->hp.copied[k]) cudaEventDestroy(ctx->hp.copied[k]);
   }
   release(ctx->hp.counters);
+  for (Buffer* b : {&ctx->pf.renders, &ctx->pf.params, &ctx->pf.err}) release(*b);
   if (ctx->hp.err) cudaFreeHost(ctx->hp.err);
   if (ctx->hp.copy) cudaStreamDestroy(ctx->hp.copy);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -562,6 +569,7 @@ lf_status lf_load_views(lf_ctx* c, int32_t n_views, const lf_pose* poses, const 
   release(stage);
   release(scale);
   c->n_views = n_views;
+  c->views_host = std::move(vs);
   c->src_w = W;
   c->src_h = H;
   c->tex_fmt = fmt;
@@ -1254,3 +1262,150 @@ lf_status lf_host_wait(lf_ctx* c, int64_t frame, uint32_t* error_word) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Prefiltering (lf_prefilter): Sec. 5.1, Eq. 5.  The host places each
+// sample's aperture point (FP64), renders the dense model from it for all
+// samples of a view in one lf_render_batch call on the dense context, and the
+// accumulation kernel (lf_prefilter.cu) forms the ratio per pixel.
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kApertureInset = 1e-5;  // fraction of R by which aperture points sit inside the sphere
+
+// Lanczos-2: sinc(x) sinc(x / 2) for |x| < 2, sinc(x) = sin(pi x) / (pi x).
+double lanczos2(double x) {
+  if (std::fabs(x) >= 2.0) return 0.0;
+  if (x == 0.0) return 1.0;
+  const double p = kPi * x;
+  return (std::sin(p) / p) * (std::sin(0.5 * p) / (0.5 * p));
+}
+
+void cross3(const double* a, const double* b, double* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void normalize3(double* v) {
+  const double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  for (int k = 0; k < 3; ++k) v[k] /= n;
+}
+
+// World position of aperture sample (a, b) on view V's disk: on the capture
+// sphere (centre C, radius R) at chord distance r sqrt(a) from the disk
+// centre's radial projection, at angle 2 pi b from the image x axis in the
+// tangent plane, pulled kApertureInset R toward C.
+void aperture_point(const ViewStatic& V, const double* C, double R, double a, double b, double* o) {
+  double n[3] = {V.disk_c[0] - C[0], V.disk_c[1] - C[1], V.disk_c[2] - C[2]};
+  normalize3(n);
+  const double xc[3] = {V.R[0], V.R[3], V.R[6]};  // image x axis (first column of R)
+  const double xn = xc[0] * n[0] + xc[1] * n[1] + xc[2] * n[2];
+  double x[3] = {xc[0] - xn * n[0], xc[1] - xn * n[1], xc[2] - xn * n[2]};
+  normalize3(x);
+  double y[3];
+  cross3(n, x, y);
+  const double chord = (double)V.disk_r * std::sqrt(a);
+  const double theta = 2.0 * std::asin(std::min(1.0, chord / (2.0 * R)));
+  const double phi = 2.0 * kPi * b;
+  const double ct = std::cos(theta), st = std::sin(theta), cp = std::cos(phi), sp = std::sin(phi);
+  for (int k = 0; k < 3; ++k)
+    o[k] = C[k] + (1.0 - kApertureInset) * R * (ct * n[k] + st * (cp * x[k] + sp * y[k]));
+}
+
+}  // namespace
+
+extern "C" lf_status lf_prefilter(lf_ctx* c, lf_ctx* dense, int32_t first_view, int32_t n_views, int32_t n_samples,
+                                  const lf_prefilter_sample* samples, int32_t supersample, float* out_rgba,
+                                  void* stream) {
+  lf_status st = check_ready(c);
+  if (st != LF_OK) return st;
+  if (!dense || dense == c) return fail(c, LF_ERR_INVALID_ARG, "the dense model needs a context of its own");
+  if (dense->n_views <= 0 || dense->G <= 0) return fail(c, LF_ERR_STATE, "the dense context has no views or meshes");
+  if (dense->device != c->device) return fail(c, LF_ERR_INVALID_ARG, "the two contexts are on different devices");
+  if (n_samples < 1 || n_samples > dense->cfg.max_eyes)
+    return fail(c, LF_ERR_INVALID_ARG, "n_samples must be 1 .. the dense context's max_eyes");
+  if (first_view < 0 || n_views < 0 || (int64_t)first_view + n_views > c->n_views)
+    return fail(c, LF_ERR_INVALID_ARG, "view range out of bounds");
+  if (!samples || (n_views > 0 && !out_rgba)) return fail(c, LF_ERR_INVALID_ARG, "null argument");
+  if (supersample < 1 || supersample > 4 || (int64_t)supersample * std::max(c->src_w, c->src_h) > 32767)
+    return fail(c, LF_ERR_INVALID_ARG, "supersample must be 1 .. 4 with renders up to 32767 pixels");
+  for (int j = 0; j < n_samples; ++j) {
+    const lf_prefilter_sample& q = samples[j];
+    if (!(q.a >= 0.0f && q.a <= 1.0f && q.b >= 0.0f && q.b <= 1.0f && q.ds >= -2.0f && q.ds <= 2.0f &&
+          q.dt >= -2.0f && q.dt <= 2.0f))
+      return fail(c, LF_ERR_INVALID_ARG, "sample out of range (a, b in [0, 1]; ds, dt in [-2, 2])");
+  }
+  if (n_views == 0) return LF_OK;
+  const int J = n_samples, S = supersample, W = c->src_w, H = c->src_h, Ws = S * W, Hs = S * H;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // per (view, sample): the render's pose and the kernel's (o', rho sigma); per sample: (ds, dt)
+  std::vector<lf_pose> poses((size_t)n_views * J);
+  std::vector<float> params((size_t)n_views * J * 4 + (size_t)J * 2);
+  float* offs = params.data() + (size_t)n_views * J * 4;
+  std::vector<double> wj(J);
+  for (int j = 0; j < J; ++j) {
+    wj[j] = (1.0 - std::sqrt((double)samples[j].a)) * lanczos2(samples[j].ds) * lanczos2(samples[j].dt);
+    offs[2 * j] = samples[j].ds;
+    offs[2 * j + 1] = samples[j].dt;
+  }
+  for (int k = 0; k < n_views; ++k) {
+    const ViewStatic& V = c->views_host[first_view + k];
+    for (int j = 0; j < J; ++j) {
+      double o[3];
+      aperture_point(V, c->sphere_c, c->sphere_r, samples[j].a, samples[j].b, o);
+      lf_pose& P = poses[(size_t)k * J + j];
+      std::memcpy(P.R, V.R, sizeof(P.R));
+      for (int r = 0; r < 3; ++r) P.t[r] = o[r];
+      float* q = params.data() + ((size_t)k * J + j) * 4;
+      for (int r = 0; r < 3; ++r)  // o' = R^T (o - t): the origin in the view's camera frame
+        q[r] = (float)(V.R[0 * 3 + r] * (o[0] - V.t[0]) + V.R[1 * 3 + r] * (o[1] - V.t[1]) +
+                       V.R[2 * 3 + r] * (o[2] - V.t[2]));
+      q[3] = (float)wj[j];
+    }
+  }
+  LF_CUDA(c, ensure(c->pf.renders, sizeof(float) * 4 * (size_t)J * Ws * Hs));
+  LF_CUDA(c, ensure(c->pf.params, sizeof(float) * params.size()));
+  LF_CUDA(c, ensure(c->pf.err, 256));
+  LF_CUDA(c, cudaMemcpyAsync(c->pf.params.p, params.data(), sizeof(float) * params.size(), cudaMemcpyHostToDevice, s));
+  LF_CUDA(c, cudaMemsetAsync(c->pf.err.p, 0, sizeof(uint32_t), s));
+  std::vector<float*> outs(J);
+  for (int j = 0; j < J; ++j) outs[j] = static_cast<float*>(c->pf.renders.p) + (size_t)j * Ws * Hs * 4;
+  for (int k = 0; k < n_views; ++k) {
+    const ViewStatic& V = c->views_host[first_view + k];
+    std::vector<lf_intrinsics> intr(J, lf_intrinsics{S * V.fx, S * V.fy, S * V.cx, S * V.cy, Ws, Hs});
+    st = lf_render_batch(dense, J, poses.data() + (size_t)k * J, intr.data(), outs.data(), stream);
+    if (st != LF_OK) {
+      cudaStreamSynchronize(s);
+      return fail(c, st, (std::string("dense render: ") + dense->last_error).c_str());
+    }
+    PrefilterArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.view = first_view + k;
+    a.W = W; a.H = H; a.G = c->G;
+    a.mesh_format = c->mesh_fmt;
+    a.depth = c->depth.p;
+    a.tab_a = static_cast<const float*>(c->tab_a.p);
+    a.tab_b = static_cast<const float*>(c->tab_b.p);
+    a.views = static_cast<const ViewStatic*>(c->views.p);
+    a.fx = (float)V.fx; a.fy = (float)V.fy; a.cx = (float)V.cx; a.cy = (float)V.cy;
+    a.Ws = Ws; a.Hs = Hs;
+    a.fxs = (float)(S * V.fx); a.fys = (float)(S * V.fy); a.cxs = (float)(S * V.cx); a.cys = (float)(S * V.cy);
+    a.n_samples = J;
+    a.sample = static_cast<const float4*>(c->pf.params.p) + (size_t)k * J;
+    a.offset = reinterpret_cast<const float2*>(static_cast<const float*>(c->pf.params.p) + (size_t)n_views * J * 4);
+    a.renders = static_cast<const float4*>(c->pf.renders.p);
+    a.out = reinterpret_cast<float4*>(out_rgba) + (size_t)k * W * H;
+    a.dense_error = reinterpret_cast<const uint32_t*>(static_cast<const unsigned char*>(dense->small.p) + 8);
+    a.error = static_cast<uint32_t*>(c->pf.err.p);
+    LF_CUDA(c, launch_prefilter_accumulate(a, s));
+  }
+  LF_CUDA(c, cudaStreamSynchronize(s));
+  uint32_t err = 0;
+  LF_CUDA(c, cudaMemcpy(&err, c->pf.err.p, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err & kErrPoolOverflow)
+    return fail(c, LF_ERR_CAPACITY, "a dense render overflowed its scratch: raise the dense context's tri_capacity");
+  return LF_OK;
+}
