@@ -45,7 +45,9 @@ def parse_args():
                         "work so the clock sampler sees the load")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["rig", "rig256", "tiny", "batch", "learned", "refine"], default="rig")
+    p.add_argument("--workload", choices=["rig", "rig256", "tiny", "batch", "learned", "refine", "prefilter"],
+                   default="rig")
+    p.add_argument("--samples", type=int, default=32, help="prefilter: Monte Carlo samples per pixel (Eq. 5)")
     p.add_argument("--refine-kernel", choices=["fused", "layers"], default="fused")
     p.add_argument("--poses", type=int, default=8, help="distinct head poses cycled through")
     p.add_argument("--tex", choices=["f32", "u8", "bf16", "fp8"], default="f32")
@@ -658,6 +660,187 @@ def run_refine(args):
     return 0
 
 
+PREFILTER_VIEWS_PER_STEP = 8
+
+
+def pick_prefilter_samples(lfm, J: int):
+    """The first seed whose stratified sample set's weights rho sigma sum to more
+    than 0.6 of their absolute sum (a set whose Lanczos lobes do not nearly cancel)."""
+    import numpy as np
+
+    for seed in range(1000):
+        S = lfm.prefilter_samples(J, seed).astype(np.float64)
+        w = (1.0 - np.sqrt(S[:, 0])) * np.sinc(S[:, 2]) * np.sinc(S[:, 2] / 2) * np.sinc(S[:, 3]) * np.sinc(S[:, 3] / 2)
+        if w.sum() > 0.6 * np.abs(w).sum():
+            return S.astype(np.float32), seed, float(w.sum() / np.abs(w).sum())
+    raise RuntimeError("no balanced prefilter sample set")
+
+
+def run_prefilter(args):
+    """The light field prefilter (Sec. 5, Eq. 5) at rig scale: images of the
+    1,024-view real-time model replaced by Monte Carlo estimates over each
+    view's disk and a Lanczos-2 pixel basis, with Lbar rendered by the method
+    from a 4,096-view dense model with 256^2 meshes.  Timed: blocks of 8 views
+    per step.  Quality: stereo eyes rendered from the prefiltered and from the
+    original images, each against the analytic ray-cast truth."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    init_dist(world)
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_08860_gb300 as lfm
+    import scene
+
+    t0 = time.perf_counter()
+    lf = scene.rig_light_field(1, n_heads=2)
+    dense = scene.build_light_field(lf.prims, scene.fibonacci_directions(args.dense_views), lf.width, lf.height,
+                                    120.0, args.dense_grid)
+    gen_s = time.perf_counter() - t0
+    J = args.samples
+    samples, seed, balance = pick_prefilter_samples(lfm, J)
+    rt = lfm.Renderer(local)
+    rt.load_views(lf)
+    rt.build_meshes(lf)
+    rd = lfm.Renderer(local, max_eyes=J, tri_capacity=J << 20, timing=True)
+    rd.load_views(dense, tex_format="u8")
+    rd.build_meshes(dense)
+    V, W, H = PREFILTER_VIEWS_PER_STEP, lf.width, lf.height
+    n_blocks = lf.n_views // V
+    out = torch.empty((V, H, W, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    first = lambda k: ((k + rank) % n_blocks) * V  # noqa: E731  ranks take different blocks
+    for k in range(args.warmup):
+        rt.prefilter(rd, samples, first_view=first(k), n_views=V, out=out)
+    torch.cuda.synchronize()
+    barrier_all()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    raster_ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        rt.prefilter(rd, samples, first_view=first(args.warmup + k), n_views=V, out=out)
+        ev[k][1].record(stream)
+        raster_ms.append(rd.stats()["ms_raster"])  # the last view's batched dense render
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev))
+    texels = V * W * H
+    value = whole_job_rate(texels * args.steps, total_ms, world)
+    # end to end: the prefiltered block copied to pinned host memory each step
+    host = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(max(3, args.steps // 2))]
+    for k, (a, b) in enumerate(e2e_ev):
+        flush.zero_()
+        a.record(stream)
+        rt.prefilter(rd, samples, first_view=first(k), n_views=V, out=out)
+        host.copy_(out, non_blocking=True)
+        b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev)) / len(e2e_ev)
+
+    # roofline of the dense raster: the J renders of one view read these texels and write J images
+    P, K, (Ws, Hs) = rt.prefilter_cameras(0, samples)
+    cams = [scene.Eye(P[j], K[j], Ws, Hs) for j in range(J)]
+    uniq = rd.unique_texels(cams, dense.width, dense.height)
+    raster_bytes = uniq * 4 + J * Ws * Hs * 16
+    mean_raster = statistics.mean(raster_ms)
+    peak, peak_kind = measured_peak()
+    achieved = raster_bytes / (mean_raster / 1000.0) / 1e9
+    result = {
+        "metric": "prefiltered source texels/s (Sec. 5, Eq. 5)", "value": value, "unit": "Mtexel/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "prefilter: rig model (1,024 Fibonacci views 1024^2 at 120 deg, 64^2 meshes), "
+                               "Lbar from a %d-view dense model with %d^2 meshes (u8 textures); %d samples per "
+                               "pixel (stratified, seed %d, weight balance %.2f); %d views per step" % (
+                                   args.dense_views, args.dense_grid, J, seed, balance, V),
+                   "l2": "flushed (256 MiB write) between steps, outside the timed events",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "per_step": {"renders": V * J, "render_pixels": V * J * Ws * Hs, "ms_per_render": total_ms / args.steps / (V * J)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "raster_kernel (persistent): the %d dense renders of one view" % J,
+                     "peak_source": peak_kind + " (HBM copy)", "algorithmic_bytes_per_launch": raster_bytes,
+                     "unique_texels_per_launch": uniq, "ms_per_launch": mean_raster},
+        "e2e": {"value": whole_job_rate(texels, e2e_ms, world), "unit": "Mtexel/s", "h2d_bytes_per_step": 16 * J,
+                "d2h_bytes_per_step": texels * 16,
+                "what": "lf_prefilter from host samples plus the prefiltered block copied to pinned host memory"},
+        "gpu_launches": 5 * V * args.steps,
+        "clocks": clk,
+        "scene_generation_s": gen_s,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["quality"] = prefilter_quality(lfm, scene, rt, rd, lf, samples, local)
+        from oracle import prefilter as opf
+
+        rng = np.random.default_rng(13)
+        pix = np.stack([rng.integers(0, W, 200), rng.integers(0, H, 200)], axis=1)
+        t1 = time.perf_counter()
+        opf.prefilter(lf, dense, 0, samples.astype(np.float64), pixels=pix, sparse=True, threads=os.cpu_count())
+        dt = time.perf_counter() - t1
+        result["cpu_baseline"] = {"value": 200 / dt / 1e6, "unit": "Mtexel/s", "cores": os.cpu_count() or 1,
+                                  "kind": "oracle", "sample": "200 random texels of view 0, %d samples, renders "
+                                                              "evaluated only where read, %.1f s" % (J, dt)}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    rt.close()
+    rd.close()
+    finish_dist(world)
+    return 0
+
+
+def prefilter_quality(lfm, scene, rt, rd, lf, samples, local):
+    """PSNR against the analytic truth of the rig's stereo eyes rendered from the
+    original images and from images prefiltered (every view the eyes select)."""
+    import dataclasses
+
+    import numpy as np
+
+    active = np.zeros(lf.n_views, dtype=bool)
+    for e in lf.eyes:
+        active |= np.asarray(rt.render_inspect(e, max_records=1)["active"]).astype(bool)
+    ids = np.nonzero(active)[0]
+    images = lf.images.copy()
+    t0 = time.perf_counter()
+    runs = np.split(ids, np.nonzero(np.diff(ids) != 1)[0] + 1)
+    for run in runs:
+        for c0 in range(0, len(run), 32):
+            part = run[c0:c0 + 32]
+            o = rt.prefilter(rd, samples, first_view=int(part[0]), n_views=len(part)).cpu().numpy()
+            rgb8 = np.clip(np.rint(o[..., :3] * 255.0), 0, 255).astype(np.uint8)
+            for m, v in enumerate(part):
+                ok = o[m, ..., 3] > 0
+                images[v][ok, :3] = rgb8[m][ok]
+    pre_s = time.perf_counter() - t0
+    rp = lfm.Renderer(local)
+    lfp = dataclasses.replace(lf, images=images)
+    rp.load_views(lfp)
+    rp.build_meshes(lfp)
+    res = {}
+    for name, r in (("original", rt), ("prefiltered", rp)):
+        sq, n = 0.0, 0
+        for e in lf.eyes:
+            img = r.render([e])[0].cpu().numpy().astype(np.float64)
+            t = scene.truth_image(lf, e)[..., :3].astype(np.float64) / 255.0
+            ok = img[..., 3] > 0
+            d = img[ok][:, :3] - t[ok]
+            sq += float(np.sum(d * d))
+            n += d.size
+        res["psnr_%s_db" % name] = 10.0 * math.log10(1.0 / (sq / n))
+    rp.close()
+    res.update({"vs": "analytic ray-cast truth, every valid pixel of %d eyes (1440x1600)" % len(lf.eyes),
+                "views_prefiltered": int(len(ids)), "prefilter_s": pre_s,
+                "gain_db": res["psnr_prefiltered_db"] - res["psnr_original_db"]})
+    return res
+
+
 def run_learned(args):
     """Learned refinement: train y = x + f(x) on pairs the method generates (the
     fast light field's render of a 256x256 crop vs a 2x2-supersampled render
@@ -970,13 +1153,15 @@ def main():
     args = parse_args()
     if args.steps is None:
         args.steps = 20 if args.impl == "reference" else {"rig": 2000, "batch": 60, "learned": 1000,
-                                                          "refine": 1000}.get(args.workload, 400)
+                                                          "refine": 1000, "prefilter": 10}.get(args.workload, 400)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "prefilter":
+        return run_prefilter(args)
     if args.workload == "refine":
         return run_refine(args)
     return run_ours(args)

@@ -427,6 +427,13 @@ typedef struct {
 LF_API lf_status lf_prefilter(lf_ctx* ctx, lf_ctx* dense, int32_t first_view, int32_t n_views, int32_t n_samples,
                               const lf_prefilter_sample* samples, int32_t supersample, float* out_rgba, void* stream);
 
+/* The J render cameras lf_prefilter uses for view `view` (host outputs, n_samples
+ * each): the pose at each sample's aperture point with the view's rotation, and
+ * the view's intrinsics times `supersample`.  Errors: LF_ERR_INVALID_ARG,
+ * LF_ERR_STATE. */
+LF_API lf_status lf_prefilter_cameras(lf_ctx* ctx, int32_t view, int32_t n_samples, const lf_prefilter_sample* samples,
+                                      int32_t supersample, lf_pose* poses, lf_intrinsics* intr);
+
 /* Counters of the last render call; synchronises with its stream. */
 LF_API lf_status lf_get_stats(lf_ctx* ctx, lf_stats* out);
 

@@ -131,13 +131,15 @@ def _bilinear_premultiplied(img, u, v):
 
 
 def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=None, threads=None,
-              renders=None, details: bool = False):
+              renders=None, details: bool = False, sparse: bool = False):
     """Eq. 5 for view `view` of the real-time model `target`, with Lbar from
     the light field `dense`.  samples: J x 4 (a, b, ds, dt).  pixels: K x 2
     integer (i, j), or None for the whole image.  Returns H x W x 4 (or K x 4)
     FP64.  `renders` may pass the J renders (from virtual_renders) in.  With
     details, returns a dict that also holds the denominator and the sum of
-    |rho sigma| alpha (the error magnification of the ratio)."""
+    |rho sigma| alpha (the error magnification of the ratio).  With sparse,
+    each render is evaluated only at the texels the pixels' bilinear reads
+    touch (the same values, for a few pixels of a large view)."""
     samples = np.asarray(samples, dtype=np.float64).reshape(-1, 4)
     W, H = target.width, target.height
     if pixels is None:
@@ -146,9 +148,9 @@ def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=No
     else:
         pix = np.asarray(pixels, dtype=np.int64).reshape(-1, 2)
     Rv, tv = _view_R_t(target, view)
-    if renders is None:
+    if renders is None and not sparse:
         renders = virtual_renders(target, dense, view, samples, supersample, threads)
-    Ks, _, _ = virtual_intrinsics(target, view, supersample)
+    Ks, Ws, Hs = virtual_intrinsics(target, view, supersample)
     num = np.zeros((pix.shape[0], 3))
     den = np.zeros(pix.shape[0])
     den_abs = np.zeros(pix.shape[0])
@@ -160,7 +162,11 @@ def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=No
         x = X - o
         qx = Ks[0] * x[:, 0] / x[:, 2] + Ks[2]
         qy = Ks[1] * x[:, 1] / x[:, 2] + Ks[3]
-        val = _bilinear_premultiplied(renders[jdx], qx - 0.5, qy - 0.5)
+        if renders is None:  # sparse: render only the texels the bilinear reads touch
+            img = _sparse_render(target, dense, view, smp, supersample, qx - 0.5, qy - 0.5, threads)
+        else:
+            img = renders[jdx]
+        val = _bilinear_premultiplied(img, qx - 0.5, qy - 0.5)
         num += w * val[:, :3]
         den += w * val[:, 3]
         den_abs += abs(w) * val[:, 3]
@@ -171,6 +177,24 @@ def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=No
     if pixels is None:
         out, den, den_abs = out.reshape(H, W, 4), den.reshape(H, W), den_abs.reshape(H, W)
     return {"rgba": out, "den": den, "den_abs": den_abs} if details else out
+
+
+def _sparse_render(target, dense, view: int, smp, supersample, u, v, threads):
+    """A render image holding only the texels around (u, v) (zero elsewhere)."""
+    import oracle
+    import scene
+
+    Rv, _ = _view_R_t(target, view)
+    Ks, Ws, Hs = virtual_intrinsics(target, view, supersample)
+    i0 = np.floor(u).astype(np.int64)
+    j0 = np.floor(v).astype(np.int64)
+    ii = np.clip(np.concatenate([i0, i0 + 1, i0, i0 + 1]), 0, Ws - 1)
+    jj = np.clip(np.concatenate([j0, j0, j0 + 1, j0 + 1]), 0, Hs - 1)
+    need = np.unique(np.stack([ii, jj], axis=1), axis=0)
+    eye = scene.Eye(scene.pose_array(Rv, aperture_point(target, view, smp[0], smp[1])), Ks, Ws, Hs)
+    img = np.zeros((Hs, Ws, 4))
+    img[need[:, 1], need[:, 0]] = oracle.render(dense, eye, pixels=need, threads=threads)["rgba"]
+    return img
 
 
 def virtual_renders(target, dense, view: int, samples, supersample: int = 1, threads=None):

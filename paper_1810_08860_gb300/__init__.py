@@ -69,7 +69,7 @@ EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_
            "lf_render_batch", "lf_render_inspect", "lf_render_static", "lf_tune_batch", "lf_get_stats",
            "lf_status_string", "lf_last_error", "lf_load_refiner", "lf_refine_set_kernel", "lf_get_refiner",
            "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined", "lf_render_host",
-           "lf_host_wait", "lf_prefilter"]
+           "lf_host_wait", "lf_prefilter", "lf_prefilter_cameras"]
 HOST_FRAMES_IN_FLIGHT = 3
 HOST_FORMS = {"plain": 0, "refined": 1, "batch": 2}
 
@@ -164,6 +164,8 @@ def load_library(path: str = LIB_PATH):
     lib.lf_host_wait.restype = ctypes.c_int
     lib.lf_prefilter.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp]
     lib.lf_prefilter.restype = ctypes.c_int
+    lib.lf_prefilter_cameras.argtypes = [vp, i32, i32, vp, i32, vp, vp]
+    lib.lf_prefilter_cameras.restype = ctypes.c_int
     lib.lf_status_string.argtypes = [ctypes.c_int]
     lib.lf_status_string.restype = ctypes.c_char_p
     lib.lf_last_error.argtypes = [vp]
@@ -480,6 +482,19 @@ class Renderer:
                                           S.ctypes.data_as(ctypes.c_void_p), int(supersample),
                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "lf_prefilter")
         return out
+
+    def prefilter_cameras(self, view: int, samples, supersample: int = 1):
+        """The render cameras of lf_prefilter for one view: poses (J x 12, R
+        row-major then t), intrinsics (J x 4) and the render size (W, H)."""
+        S = np.ascontiguousarray(np.asarray(samples, dtype=np.float32).reshape(-1, 4))
+        J = S.shape[0]
+        poses = (Pose * J)()
+        intr = (Intrinsics * J)()
+        self._check(self.lib.lf_prefilter_cameras(self.ctx, int(view), J, S.ctypes.data_as(ctypes.c_void_p),
+                                                  int(supersample), poses, intr), "lf_prefilter_cameras")
+        P = np.array([list(p.R) + list(p.t) for p in poses])
+        K = np.array([[k.fx, k.fy, k.cx, k.cy] for k in intr])
+        return P, K, (intr[0].width, intr[0].height) if J else (0, 0)
 
     def render_refined(self, eyes, out=None, stream=None):
         """lf_render followed by the refinement (plain render if no refiner is loaded)."""

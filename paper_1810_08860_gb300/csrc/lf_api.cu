@@ -1314,7 +1314,46 @@ void aperture_point(const ViewStatic& V, const double* C, double R, double a, do
     o[k] = C[k] + (1.0 - kApertureInset) * R * (ct * n[k] + st * (cp * x[k] + sp * y[k]));
 }
 
+// The render camera of sample q for view V (pose at the aperture point, the
+// view's rotation, intrinsics times S) and the kernel's record (o' = R^T (o - t)
+// in the view's camera frame, rho sigma).
+void prefilter_camera(const lf_ctx* c, const ViewStatic& V, const lf_prefilter_sample& q, int S, lf_pose* P,
+                      lf_intrinsics* K, float* rec) {
+  double o[3];
+  aperture_point(V, c->sphere_c, c->sphere_r, q.a, q.b, o);
+  std::memcpy(P->R, V.R, sizeof(P->R));
+  for (int r = 0; r < 3; ++r) P->t[r] = o[r];
+  *K = lf_intrinsics{S * V.fx, S * V.fy, S * V.cx, S * V.cy, S * c->src_w, S * c->src_h};
+  if (rec) {
+    for (int r = 0; r < 3; ++r)
+      rec[r] = (float)(V.R[0 * 3 + r] * (o[0] - V.t[0]) + V.R[1 * 3 + r] * (o[1] - V.t[1]) +
+                       V.R[2 * 3 + r] * (o[2] - V.t[2]));
+    rec[3] = (float)((1.0 - std::sqrt((double)q.a)) * lanczos2(q.ds) * lanczos2(q.dt));
+  }
+}
+
+bool prefilter_sample_ok(const lf_prefilter_sample& q) {
+  return q.a >= 0.0f && q.a <= 1.0f && q.b >= 0.0f && q.b <= 1.0f && q.ds >= -2.0f && q.ds <= 2.0f &&
+         q.dt >= -2.0f && q.dt <= 2.0f;
+}
+
 }  // namespace
+
+extern "C" lf_status lf_prefilter_cameras(lf_ctx* c, int32_t view, int32_t n_samples,
+                                          const lf_prefilter_sample* samples, int32_t supersample, lf_pose* poses,
+                                          lf_intrinsics* intr) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (c->n_views <= 0) return fail(c, LF_ERR_STATE, "views not loaded");
+  if (view < 0 || view >= c->n_views || n_samples < 0 || (n_samples > 0 && (!samples || !poses || !intr)))
+    return fail(c, LF_ERR_INVALID_ARG, "bad prefilter camera arguments");
+  if (supersample < 1 || supersample > 4 || (int64_t)supersample * std::max(c->src_w, c->src_h) > 32767)
+    return fail(c, LF_ERR_INVALID_ARG, "supersample must be 1 .. 4 with renders up to 32767 pixels");
+  for (int j = 0; j < n_samples; ++j) {
+    if (!prefilter_sample_ok(samples[j])) return fail(c, LF_ERR_INVALID_ARG, "sample out of range");
+    prefilter_camera(c, c->views_host[view], samples[j], supersample, poses + j, intr + j, nullptr);
+  }
+  return LF_OK;
+}
 
 extern "C" lf_status lf_prefilter(lf_ctx* c, lf_ctx* dense, int32_t first_view, int32_t n_views, int32_t n_samples,
                                   const lf_prefilter_sample* samples, int32_t supersample, float* out_rgba,
@@ -1331,41 +1370,27 @@ extern "C" lf_status lf_prefilter(lf_ctx* c, lf_ctx* dense, int32_t first_view, 
   if (!samples || (n_views > 0 && !out_rgba)) return fail(c, LF_ERR_INVALID_ARG, "null argument");
   if (supersample < 1 || supersample > 4 || (int64_t)supersample * std::max(c->src_w, c->src_h) > 32767)
     return fail(c, LF_ERR_INVALID_ARG, "supersample must be 1 .. 4 with renders up to 32767 pixels");
-  for (int j = 0; j < n_samples; ++j) {
-    const lf_prefilter_sample& q = samples[j];
-    if (!(q.a >= 0.0f && q.a <= 1.0f && q.b >= 0.0f && q.b <= 1.0f && q.ds >= -2.0f && q.ds <= 2.0f &&
-          q.dt >= -2.0f && q.dt <= 2.0f))
+  for (int j = 0; j < n_samples; ++j)
+    if (!prefilter_sample_ok(samples[j]))
       return fail(c, LF_ERR_INVALID_ARG, "sample out of range (a, b in [0, 1]; ds, dt in [-2, 2])");
-  }
   if (n_views == 0) return LF_OK;
   const int J = n_samples, S = supersample, W = c->src_w, H = c->src_h, Ws = S * W, Hs = S * H;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // per (view, sample): the render's pose and the kernel's (o', rho sigma); per sample: (ds, dt)
   std::vector<lf_pose> poses((size_t)n_views * J);
+  std::vector<lf_intrinsics> intr((size_t)n_views * J);
   std::vector<float> params((size_t)n_views * J * 4 + (size_t)J * 2);
   float* offs = params.data() + (size_t)n_views * J * 4;
-  std::vector<double> wj(J);
   for (int j = 0; j < J; ++j) {
-    wj[j] = (1.0 - std::sqrt((double)samples[j].a)) * lanczos2(samples[j].ds) * lanczos2(samples[j].dt);
     offs[2 * j] = samples[j].ds;
     offs[2 * j + 1] = samples[j].dt;
   }
-  for (int k = 0; k < n_views; ++k) {
-    const ViewStatic& V = c->views_host[first_view + k];
+  for (int k = 0; k < n_views; ++k)
     for (int j = 0; j < J; ++j) {
-      double o[3];
-      aperture_point(V, c->sphere_c, c->sphere_r, samples[j].a, samples[j].b, o);
-      lf_pose& P = poses[(size_t)k * J + j];
-      std::memcpy(P.R, V.R, sizeof(P.R));
-      for (int r = 0; r < 3; ++r) P.t[r] = o[r];
-      float* q = params.data() + ((size_t)k * J + j) * 4;
-      for (int r = 0; r < 3; ++r)  // o' = R^T (o - t): the origin in the view's camera frame
-        q[r] = (float)(V.R[0 * 3 + r] * (o[0] - V.t[0]) + V.R[1 * 3 + r] * (o[1] - V.t[1]) +
-                       V.R[2 * 3 + r] * (o[2] - V.t[2]));
-      q[3] = (float)wj[j];
+      const size_t i = (size_t)k * J + j;
+      prefilter_camera(c, c->views_host[first_view + k], samples[j], S, &poses[i], &intr[i], &params[i * 4]);
     }
-  }
   LF_CUDA(c, ensure(c->pf.renders, sizeof(float) * 4 * (size_t)J * Ws * Hs));
   LF_CUDA(c, ensure(c->pf.params, sizeof(float) * params.size()));
   LF_CUDA(c, ensure(c->pf.err, 256));
@@ -1375,8 +1400,7 @@ extern "C" lf_status lf_prefilter(lf_ctx* c, lf_ctx* dense, int32_t first_view, 
   for (int j = 0; j < J; ++j) outs[j] = static_cast<float*>(c->pf.renders.p) + (size_t)j * Ws * Hs * 4;
   for (int k = 0; k < n_views; ++k) {
     const ViewStatic& V = c->views_host[first_view + k];
-    std::vector<lf_intrinsics> intr(J, lf_intrinsics{S * V.fx, S * V.fy, S * V.cx, S * V.cy, Ws, Hs});
-    st = lf_render_batch(dense, J, poses.data() + (size_t)k * J, intr.data(), outs.data(), stream);
+    st = lf_render_batch(dense, J, poses.data() + (size_t)k * J, intr.data() + (size_t)k * J, outs.data(), stream);
     if (st != LF_OK) {
       cudaStreamSynchronize(s);
       return fail(c, st, (std::string("dense render: ") + dense->last_error).c_str());

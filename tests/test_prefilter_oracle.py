@@ -239,3 +239,13 @@ def test_constant_colour_field_and_invariances():
     assert np.allclose(a, c, atol=1e-12)
     # positive weights only: a convex combination of render values in [0, 1]
     assert np.all(a[a[:, 3] > 0, :3] >= -1e-12) and np.all(a[a[:, 3] > 0, :3] <= 1 + 1e-12)
+
+
+def test_sparse_renders_give_the_same_values():
+    lf = scene.tiny_light_field(3)
+    rng = np.random.default_rng(12)
+    samples = _samples(rng, 4)
+    pix = np.stack([rng.integers(0, lf.width, 60), rng.integers(0, lf.height, 60)], 1)
+    full = pf.prefilter(lf, lf, 7, samples, pixels=pix)
+    sparse = pf.prefilter(lf, lf, 7, samples, pixels=pix, sparse=True)
+    assert np.array_equal(full, sparse)
