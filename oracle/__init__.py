@@ -44,7 +44,8 @@ class LightFieldC(ctypes.Structure):
                 ("G", ctypes.c_int32), ("poses", ctypes.c_void_p), ("intr", ctypes.c_void_p),
                 ("rgba", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("disk_c", ctypes.c_void_p),
                 ("disk_r", ctypes.c_void_p), ("sphere_c", ctypes.c_double * 3),
-                ("sphere_r", ctypes.c_double), ("z_near", ctypes.c_float), ("pad", ctypes.c_int32)]
+                ("sphere_r", ctypes.c_double), ("z_near", ctypes.c_float), ("pad", ctypes.c_int32),
+                ("disk_ext", ctypes.c_void_p)]
 
 
 class EyeC(ctypes.Structure):
@@ -107,6 +108,9 @@ class _Bound:
             c.sphere_c[k] = float(lf.sphere_c[k])
         c.sphere_r = float(lf.sphere_r)
         c.z_near = z_near
+        ext = getattr(lf, "disk_ext", None)
+        self.disk_ext = None if ext is None else np.ascontiguousarray(ext, dtype=np.float32).reshape(-1, 4)
+        c.disk_ext = None if self.disk_ext is None else self.disk_ext.ctypes.data
         self.c = c
 
 

@@ -23,6 +23,15 @@
  *     bilinearly (the continuous sample I_i(s_i, t_i) of Eq. 2);
  *   - Eq. 2: sum_i w_i I_i / sum_i w_i, alpha 1; (0,0,0,0) where sum w = 0.
  *
+ * Asymmetric oval disks (Sec. 4.4), when disk extents are given: disk i lies
+ * in the plane through its centre c_i normal to view i's optical axis, its u
+ * and v axes along the view's image x and y axes; (u, v) is where the eye ray
+ * meets that plane (t >= 0), and the oval is the union of four quarter
+ * ellipses with semi-axes e_u+, e_u- (for u >= 0, u < 0) and e_v+, e_v-:
+ * rho^2 = (u / e_u)^2 + (v / e_v)^2, inside where rho^2 < 1, weight 1 - rho
+ * (the linear falloff of Sec. 4.1 along each ray from the centre).  No sphere
+ * crossing is involved in this mode.
+ *
  * Precision.  Colour, weights, depths and texture coordinates are FP64.  The
  * discrete decisions - the snapped vertex positions, which triangle wins the
  * depth test, and whether p lies inside a disk - are taken in FP32 with the
@@ -53,6 +62,7 @@ typedef struct {
   double sphere_r;
   float z_near;
   int32_t pad;
+  const float* disk_ext; /* n x 4 oval extents (+u, -u, +v, -v) in metres, or NULL: round disks */
 } orc_lightfield;
 
 typedef struct {
@@ -110,6 +120,12 @@ typedef struct {
   /* disk in sphere-centred FP32 coordinates for the inside decision */
   float cc[3], r2;
   double c64[3], r64;
+  /* oval disk (Sec. 4.4) in the eye frame: plane normal n, axes x, y (columns of
+     M), k = n.c', (u0, v0) = (x.c', y.c') with c' the disk centre; reciprocal
+     extents (+u, -u) and (+v, -v).  FP32 for the decision, FP64 for the weight. */
+  int oval;
+  float on[3], ox[3], oy[3], ok, ou0, ov0, oru[2], orv[2];
+  double on64[3], ox64[3], oy64[3], ok64, ou064, ov064, oru64[2], orv64[2];
 } orc_viewpose;
 
 /* A1: pose composition in FP64, fixed order, no fusion; then one rounding to FP32. */
@@ -391,8 +407,40 @@ static void orc_pixel_ray(const orc_lightfield* lf, const orc_eye* eye, int32_t 
   }
 }
 
+/* Oval disk (Sec. 4.4), FP32 decision: rho^2 < 1 where the eye ray meets the
+   disk plane at t >= 0.  Fixed order: each dot product with e = (ex, ey, 1) is
+   fma(a0, ex, fma(a1, ey, a2)). */
+static int orc_inside_oval(const orc_ray* r, const orc_viewpose* vp) {
+  const float den = fmaf(vp->on[0], r->ex, fmaf(vp->on[1], r->ey, vp->on[2]));
+  if (den == 0.0f) return 0;
+  const float t = vp->ok / den;
+  if (!(t >= 0.0f)) return 0;
+  const float ue = fmaf(vp->ox[0], r->ex, fmaf(vp->ox[1], r->ey, vp->ox[2]));
+  const float ve = fmaf(vp->oy[0], r->ex, fmaf(vp->oy[1], r->ey, vp->oy[2]));
+  const float u = fmaf(t, ue, -vp->ou0), v = fmaf(t, ve, -vp->ov0);
+  const float a = u * (u >= 0.0f ? vp->oru[0] : vp->oru[1]);
+  const float b = v * (v >= 0.0f ? vp->orv[0] : vp->orv[1]);
+  return fmaf(a, a, b * b) < 1.0f;
+}
+
+/* FP64 oval weight 1 - rho at the FP64 ray's plane hit. */
+static double orc_weight_oval(const orc_ray* r, const orc_viewpose* vp) {
+  const double* e = r->e64;
+  const double den = vp->on64[0] * e[0] + vp->on64[1] * e[1] + vp->on64[2] * e[2];
+  if (den == 0.0) return 0.0;
+  const double t = vp->ok64 / den;
+  if (t < 0.0) return 0.0;
+  const double u = t * (vp->ox64[0] * e[0] + vp->ox64[1] * e[1] + vp->ox64[2] * e[2]) - vp->ou064;
+  const double v = t * (vp->oy64[0] * e[0] + vp->oy64[1] * e[1] + vp->oy64[2] * e[2]) - vp->ov064;
+  const double a = u * (u >= 0.0 ? vp->oru64[0] : vp->oru64[1]);
+  const double b = v * (v >= 0.0 ? vp->orv64[0] : vp->orv64[1]);
+  const double w = 1.0 - sqrt(a * a + b * b);
+  return w > 0.0 ? w : 0.0;
+}
+
 /* FP32 disk membership: |p - c_i|^2 < r_i^2 with sphere-centred coordinates. */
 static int orc_inside(const orc_ray* r, const orc_viewpose* vp) {
+  if (vp->oval) return orc_inside_oval(r, vp);
   if (!r->has_p32) return 0;
   float df[3] = {r->p32[0] - vp->cc[0], r->p32[1] - vp->cc[1], r->p32[2] - vp->cc[2]};
   return dot3f(df, df) < vp->r2;
@@ -400,6 +448,7 @@ static int orc_inside(const orc_ray* r, const orc_viewpose* vp) {
 
 /* FP64 linear disk kernel (Sec. 4.1): 1 at the centre, 0 at the rim. */
 static double orc_weight(const orc_ray* r, const orc_viewpose* vp) {
+  if (vp->oval) return orc_weight_oval(r, vp);
   if (!r->has_p64) return 0.0;
   double dx = r->p64[0] - vp->c64[0], dy = r->p64[1] - vp->c64[1], dz = r->p64[2] - vp->c64[2];
   double w = 1.0 - sqrt(dx * dx + dy * dy + dz * dz) / vp->r64;
@@ -576,6 +625,42 @@ static void orc_init_viewposes(const orc_lightfield* lf, const orc_eye* eye, orc
     }
     vp->r2 = lf->disk_r[v] * lf->disk_r[v];
     vp->r64 = (double)lf->disk_r[v];
+    vp->oval = lf->disk_ext != NULL;
+    if (vp->oval) {
+      /* axes: the columns of M = R_eye^T R_i; the disk centre in the eye frame in FP64 */
+      const double* Re = eye->pose;
+      double dc[3], cp[3];
+      for (int k = 0; k < 3; ++k) dc[k] = (double)lf->disk_c[v * 3 + k] - Re[9 + k];
+      for (int r = 0; r < 3; ++r) {
+        double s = Re[0 * 3 + r] * dc[0];
+        s = s + Re[1 * 3 + r] * dc[1];
+        s = s + Re[2 * 3 + r] * dc[2];
+        cp[r] = s;
+      }
+      for (int k = 0; k < 3; ++k) {
+        vp->ox64[k] = vp->M[k * 3 + 0];
+        vp->oy64[k] = vp->M[k * 3 + 1];
+        vp->on64[k] = vp->M[k * 3 + 2];
+        vp->ox[k] = vp->Mf[k * 3 + 0];
+        vp->oy[k] = vp->Mf[k * 3 + 1];
+        vp->on[k] = vp->Mf[k * 3 + 2];
+      }
+      vp->ok64 = vp->on64[0] * cp[0] + vp->on64[1] * cp[1] + vp->on64[2] * cp[2];
+      vp->ou064 = vp->ox64[0] * cp[0] + vp->ox64[1] * cp[1] + vp->ox64[2] * cp[2];
+      vp->ov064 = vp->oy64[0] * cp[0] + vp->oy64[1] * cp[1] + vp->oy64[2] * cp[2];
+      vp->ok = (float)vp->ok64;
+      vp->ou0 = (float)vp->ou064;
+      vp->ov0 = (float)vp->ov064;
+      const float* ext = lf->disk_ext + (size_t)v * 4;
+      vp->oru64[0] = 1.0 / (double)ext[0];
+      vp->oru64[1] = 1.0 / (double)ext[1];
+      vp->orv64[0] = 1.0 / (double)ext[2];
+      vp->orv64[1] = 1.0 / (double)ext[3];
+      for (int k = 0; k < 2; ++k) {
+        vp->oru[k] = (float)vp->oru64[k];
+        vp->orv[k] = (float)vp->orv64[k];
+      }
+    }
   }
 }
 

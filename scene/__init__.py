@@ -255,6 +255,7 @@ class LightField:
     prims: np.ndarray | None = None
     eyes: list = field(default_factory=list)
     name: str = ""
+    disk_ext: np.ndarray | None = None  # n x 4 float32 oval extents (+u, -u, +v, -v), or None: round disks
 
     @property
     def n_views(self) -> int:
