@@ -161,6 +161,23 @@ LF_API lf_status lf_load_views(lf_ctx* ctx, int32_t n_views, const lf_pose* pose
                         const double sphere_c[3], double sphere_r, lf_tex_format fmt);
 
 /*
+ * Switch the loaded views to asymmetric oval disks (Sec. 4.4), or back to
+ * round ones (extents NULL).  Disk i then lies in the plane through its
+ * centre normal to view i's optical axis, with u and v along the view's image
+ * x and y axes; (u, v) is where the eye ray meets that plane (t >= 0), and the
+ * oval is the union of four quarter ellipses with semi-axes e_u+ (u >= 0),
+ * e_u- (u < 0), e_v+, e_v-:  rho^2 = (u / e_u)^2 + (v / e_v)^2, inside where
+ * rho^2 < 1 (decided in FP32), weight w = 1 - rho.  The capture sphere plays no
+ * part in this mode.  Sec. 4.4 sizes the extents to reach the farthest
+ * Delaunay 1-ring neighbour along each axis (the Python helper oval_extents).
+ *   extents  host, n_views x 4 floats (+u, -u, +v, -v) in metres, all > 0
+ * Waits for all work on the device first; later renders of every form use
+ * the ovals.  lf_load_views resets to round disks.  Errors: LF_ERR_STATE (no
+ * views), LF_ERR_INVALID_ARG, LF_ERR_CUDA.
+ */
+LF_API lf_status lf_set_disk_ovals(lf_ctx* ctx, const float* extents);
+
+/*
  * Build each view's mesh (Sec. 4.5): a grid_n x grid_n grid of vertices (j, k)
  * at source pixel-edge coordinates (j W/(grid_n-1), k H/(grid_n-1)), displaced
  * along the view's pixel rays to the given z-depths, split into two triangles

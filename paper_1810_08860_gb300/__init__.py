@@ -69,7 +69,7 @@ EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_
            "lf_render_batch", "lf_render_inspect", "lf_render_static", "lf_tune_batch", "lf_get_stats",
            "lf_status_string", "lf_last_error", "lf_load_refiner", "lf_refine_set_kernel", "lf_get_refiner",
            "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined", "lf_render_host",
-           "lf_host_wait", "lf_prefilter", "lf_prefilter_cameras"]
+           "lf_host_wait", "lf_prefilter", "lf_prefilter_cameras", "lf_set_disk_ovals"]
 HOST_FRAMES_IN_FLIGHT = 3
 HOST_FORMS = {"plain": 0, "refined": 1, "batch": 2}
 
@@ -164,6 +164,8 @@ def load_library(path: str = LIB_PATH):
     lib.lf_host_wait.restype = ctypes.c_int
     lib.lf_prefilter.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp]
     lib.lf_prefilter.restype = ctypes.c_int
+    lib.lf_set_disk_ovals.argtypes = [vp, vp]
+    lib.lf_set_disk_ovals.restype = ctypes.c_int
     lib.lf_prefilter_cameras.argtypes = [vp, i32, i32, vp, i32, vp, vp]
     lib.lf_prefilter_cameras.restype = ctypes.c_int
     lib.lf_status_string.argtypes = [ctypes.c_int]
@@ -248,6 +250,19 @@ class Renderer:
                                            float(lf.sphere_r), TEX_FORMATS[tex_format]), "lf_load_views")
         self.n_views = n
         self._src_hw = (lf.height, lf.width)
+        if getattr(lf, "disk_ext", None) is not None:
+            self.set_disk_ovals(lf.disk_ext)
+
+    def set_disk_ovals(self, extents):
+        """Asymmetric oval disks (lf_set_disk_ovals, Sec. 4.4): extents n x 4
+        (+u, -u, +v, -v) in metres, e.g. from disks.oval_extents; None: round."""
+        if extents is None:
+            self._check(self.lib.lf_set_disk_ovals(self.ctx, None), "lf_set_disk_ovals")
+            return
+        E = np.ascontiguousarray(np.asarray(extents, dtype=np.float32).reshape(-1, 4))
+        if E.shape[0] != self.n_views:
+            raise ValueError("one row of 4 extents per view")
+        self._check(self.lib.lf_set_disk_ovals(self.ctx, E.ctypes.data_as(ctypes.c_void_p)), "lf_set_disk_ovals")
 
     def build_meshes(self, lf, mesh_format: str = "f32"):
         """Upload the per-view depth grids (lf_build_view_meshes)."""

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -59,6 +60,7 @@ struct lf_ctx {
   // views
   int32_t n_views = 0, src_w = 0, src_h = 0;
   lf_tex_format tex_fmt = LF_TEX_F32;
+  int32_t disk_mode = 0;  // 0: round disks on the capture sphere; 1: ovals (lf_set_disk_ovals)
   double sphere_c[3] = {0, 0, 0};
   double sphere_r = 0;
   Buffer views, tex;
@@ -247,6 +249,7 @@ FrameArgs frame_args(lf_ctx* c, const Layout& L) {
   a.mask_words = mask_words(c);
   a.tex_format = c->tex_fmt;
   a.mesh_format = c->mesh_fmt;
+  a.disk_mode = c->disk_mode;
   a.z_near = c->cfg.z_near;
   for (int k = 0; k < 3; ++k) a.sphere_c[k] = c->sphere_c[k];
   a.sphere_r = c->sphere_r;
@@ -299,7 +302,7 @@ lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persis
 lf_status ensure_persistent_blocks(lf_ctx* c) {
   if (c->persistent_blocks > 0) return LF_OK;
   int per_sm = 0;
-  LF_CUDA(c, raster_occupancy(c->cfg.tile_w, c->cfg.tile_h, c->tex_fmt, &per_sm));
+  LF_CUDA(c, raster_occupancy(c->cfg.tile_w, c->cfg.tile_h, c->tex_fmt, c->disk_mode, &per_sm));
   c->persistent_blocks = std::max(1, per_sm) * c->sm_count;
   return LF_OK;
 }
@@ -345,7 +348,7 @@ lf_status lf_tune_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf
   int best_k = -1;
   for (int ti = 0; ti < 3 && st == LF_OK; ++ti) {
     int per_sm = 0;
-    cudaError_t e = raster_occupancy(tiles[ti][0], tiles[ti][1], c->tex_fmt, &per_sm);
+    cudaError_t e = raster_occupancy(tiles[ti][0], tiles[ti][1], c->tex_fmt, c->disk_mode, &per_sm);
     if (e != cudaSuccess) { st = cuda_fail(c, e, "raster_occupancy"); break; }
     per_sm = std::max(1, per_sm);
     const int cand[4] = {1, 2, 4, per_sm};
@@ -570,11 +573,34 @@ lf_status lf_load_views(lf_ctx* c, int32_t n_views, const lf_pose* poses, const 
   release(scale);
   c->n_views = n_views;
   c->views_host = std::move(vs);
+  c->disk_mode = 0;
   c->src_w = W;
   c->src_h = H;
   c->tex_fmt = fmt;
   for (int k = 0; k < 3; ++k) c->sphere_c[k] = sphere_c[k];
   c->sphere_r = sphere_r;
+  return LF_OK;
+}
+
+lf_status lf_set_disk_ovals(lf_ctx* c, const float* extents) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (c->n_views <= 0) return fail(c, LF_ERR_STATE, "views not loaded");
+  if (extents)
+    for (int64_t i = 0; i < (int64_t)c->n_views * 4; ++i)
+      if (!(extents[i] > 0.0f) || extents[i] > 1e30f) return fail(c, LF_ERR_INVALID_ARG, "oval extents must be > 0");
+  lf_status st = quiesce(c);  // renders in flight read the disks
+  if (st != LF_OK) return st;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_sig.clear(); }
+  if (extents) {
+    for (int v = 0; v < c->n_views; ++v)
+      for (int k = 0; k < 4; ++k) c->views_host[v].disk_ext[k] = extents[v * 4 + k];
+    // only the extent fields: the device records also hold values computed there
+    LF_CUDA(c, cudaMemcpy2D(static_cast<char*>(c->views.p) + offsetof(ViewStatic, disk_ext), sizeof(ViewStatic),
+                            extents, 4 * sizeof(float), 4 * sizeof(float), (size_t)c->n_views,
+                            cudaMemcpyHostToDevice));
+  }
+  c->disk_mode = extents ? 1 : 0;
+  c->persistent_blocks = 0;  // the oval raster holds more shared memory per block
   return LF_OK;
 }
 
@@ -673,7 +699,7 @@ lf_status lf_render_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const 
                               (int64_t)(intptr_t)c->masks.p, (int64_t)(intptr_t)c->pool.p,
                               (int64_t)(intptr_t)c->active.p, (int64_t)(intptr_t)c->small.p,
                               (int64_t)(intptr_t)c->tex.p, (int64_t)(intptr_t)c->depth.p, c->persistent_blocks,
-                              c->cfg.tile_w, c->cfg.tile_h, c->cfg.timing};
+                              c->cfg.tile_w, c->cfg.tile_h, c->cfg.timing, c->disk_mode};
   for (int e = 0; e < n_eyes; ++e) { sig.push_back(intr[e].width); sig.push_back(intr[e].height); }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (c->cfg.timing) {

@@ -45,6 +45,7 @@ struct ViewStatic {
   float depth_origin;   // z0 for the FP16-offset mesh format
   float tex_scale;      // decode scale for FP8 textures
   int32_t pad[2];
+  float disk_ext[4];    // oval extents (+u, -u, +v, -v) in metres when ovals are set
 };
 
 struct EyeParams {
@@ -80,6 +81,11 @@ struct __align__(16) ViewRec {
   int32_t big_base;     // entries of the triangles spanning more than kBinMaxTiles tiles
   int32_t big_count;
   float Mf[12];         // camera -> eye rotation (3x3) then translation, FP32
+  // oval disk (Sec. 4.4) in the eye frame, each the FP32 rounding of an FP64
+  // value: plane normal n, u and v axes x, y (columns of M = R_eye^T R_i),
+  // k = n.c', u0 = x.c', v0 = y.c' (c' the disk centre), reciprocal extents
+  float ov_n[3], ov_x[3], ov_y[3], ov_k, ov_u0, ov_v0;
+  float ov_ru[2], ov_rv[2];   // 1 / e_u+, 1 / e_u-, 1 / e_v+, 1 / e_v-
 };
 
 struct __align__(16) TriRec {
@@ -108,6 +114,7 @@ struct FrameArgs {
   int32_t mask_words;
   int32_t tex_format;
   int32_t mesh_format;
+  int32_t disk_mode;       // 0: round disks on the capture sphere; 1: ovals (Sec. 4.4)
   float z_near;
   double sphere_c[3];
   double sphere_r;
@@ -152,7 +159,7 @@ cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_bin(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_raster(const FrameArgs& a, bool inspect, bool persistent, int persistent_blocks,
                           cudaStream_t s);
-cudaError_t raster_occupancy(int tile_w, int tile_h, int tex_format, int* blocks_per_sm);
+cudaError_t raster_occupancy(int tile_w, int tile_h, int tex_format, int disk_mode, int* blocks_per_sm);
 // FP8 textures: per-view scale = max(RGB) / 255 / 448, also stored in views[v].tex_scale.
 cudaError_t launch_view_scale(const uint8_t* rgba8, int n_views, int64_t texels_per_view, float* scale,
                               ViewStatic* views, cudaStream_t s);

@@ -22,6 +22,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <type_traits>
+
 #include "lf_internal.h"
 
 namespace lfk {
@@ -120,6 +122,30 @@ struct WarpSmem {
   int off[kViewsPerRound + 1];
 };
 
+// With oval disks (Sec. 4.4) a warp also holds each view's oval constants:
+// n (3), x (3), y (3), k, u0, v0, 1/e_u+, 1/e_u-, 1/e_v+, 1/e_v-.
+struct WarpSmemOval : WarpSmem {
+  float ov[kViewsPerRound][16];
+};
+
+// Oval membership, the FP32 decision (fixed order, as the oracle takes it):
+// the ray (ex, ey, 1) meets the disk plane at t = k / (n.e) >= 0; inside where
+// (u / e_u)^2 + (v / e_v)^2 < 1, the extents chosen by the signs of u and v.
+// Returns rho^2 (the weight is 1 - sqrt(rho^2)), or 2 when outside.
+__device__ __forceinline__ float oval_rho2(const float* o, float ex, float ey) {
+  const float den = __fmaf_rn(o[0], ex, __fmaf_rn(o[1], ey, o[2]));
+  if (den == 0.0f) return 2.0f;
+  const float t = __fdiv_rn(o[9], den);
+  if (!(t >= 0.0f)) return 2.0f;
+  const float ue = __fmaf_rn(o[3], ex, __fmaf_rn(o[4], ey, o[5]));
+  const float ve = __fmaf_rn(o[6], ex, __fmaf_rn(o[7], ey, o[8]));
+  const float u = __fmaf_rn(t, ue, -o[10]), v = __fmaf_rn(t, ve, -o[11]);
+  const float a = __fmul_rn(u, u >= 0.0f ? o[12] : o[13]);
+  const float b = __fmul_rn(v, v >= 0.0f ? o[14] : o[15]);
+  const float r2 = __fmaf_rn(a, a, __fmul_rn(b, b));
+  return r2 < 1.0f ? r2 : 2.0f;
+}
+
 // The next (up to 32) views of the tile's mask in increasing order, resuming
 // at (cur_word, cur_bits) when the previous round stopped inside a word.
 __device__ __forceinline__ int collect_views(const uint32_t* mask, int mask_words, int* views, int& cur_word,
@@ -175,7 +201,7 @@ __device__ __forceinline__ int collect_views(const uint32_t* mask, int mask_word
 // pixels, keeping the nearest fragment per view; (d) when the view changes, a
 // pixel's winner is buffered, and buffered winners are shaded (bilinear
 // fetch, weight, accumulate) with both pixels' texel loads in flight.
-template <int TW, int TH, int FMT, bool INSPECT, bool MANY_EYES>
+template <int TW, int TH, int FMT, bool INSPECT, bool MANY_EYES, bool OVAL>
 __device__ void raster_strip(const FrameArgs& A, const int item, const int strip, WarpSmem& S) {
   constexpr int ROWS = (32 / TW) * kPx;
   const int lane = threadIdx.x & 31;
@@ -227,9 +253,9 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
     const float qb = dot3_rn(EF.o[0], EF.o[1], EF.o[2], d[0], d[1], d[2]);
     const float qc = __fsub_rn(dot3_rn(EF.o[0], EF.o[1], EF.o[2], EF.o[0], EF.o[1], EF.o[2]), EF.R2);
     const float disc = __fsub_rn(__fmul_rn(qb, qb), __fmul_rn(qa, qc));
-    has_p[q] = false;
+    has_p[q] = OVAL && valid[q];  // ovals are met in their own planes, not at the sphere
     p[q][0] = p[q][1] = p[q][2] = 0.0f;
-    if (valid[q] && disc >= 0.0f) {
+    if (!OVAL && valid[q] && disc >= 0.0f) {
       const float t = __fdiv_rn(__fsub_rn(__fsqrt_rn(disc), qb), qa);
       if (t >= 0.0f) {
         has_p[q] = true;
@@ -250,8 +276,16 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
     if (nv == 0) break;
     if (lane < nv) {
       const ViewRec& VR = A.vrecs[(int64_t)e * A.n_views + S.views[lane]];
-      S.cc[lane] = *reinterpret_cast<const float4*>(VR.cc);
-      S.inv_r[lane] = VR.inv_r;
+      if constexpr (OVAL) {
+        float* o = static_cast<WarpSmemOval&>(S).ov[lane];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { o[k] = VR.ov_n[k]; o[3 + k] = VR.ov_x[k]; o[6 + k] = VR.ov_y[k]; }
+        o[9] = VR.ov_k; o[10] = VR.ov_u0; o[11] = VR.ov_v0;
+        o[12] = VR.ov_ru[0]; o[13] = VR.ov_ru[1]; o[14] = VR.ov_rv[0]; o[15] = VR.ov_rv[1];
+      } else {
+        S.cc[lane] = *reinterpret_cast<const float4*>(VR.cc);
+        S.inv_r[lane] = VR.inv_r;
+      }
       const char* base = static_cast<const char*>(A.textures);
       S.tex[lane] = base + (int64_t)S.views[lane] * tex_per_view * (FMT == LF_TEX_F32 ? 16 : FMT == LF_TEX_BF16 ? 8 : 4);
       int b0 = 0, bn = 0, g0 = 0, gn = 0;
@@ -280,9 +314,13 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
       inmask[q] = 0u;
       if (has_p[q]) {
         for (int sl = 0; sl < nv; ++sl) {
-          const float4 cc = S.cc[sl];
-          const float dx = __fsub_rn(p[q][0], cc.x), dy = __fsub_rn(p[q][1], cc.y), dz = __fsub_rn(p[q][2], cc.z);
-          if (dot3_rn(dx, dy, dz, dx, dy, dz) < cc.w) inmask[q] |= 1u << sl;
+          if constexpr (OVAL) {
+            if (oval_rho2(static_cast<WarpSmemOval&>(S).ov[sl], ex, ey[q]) < 1.0f) inmask[q] |= 1u << sl;
+          } else {
+            const float4 cc = S.cc[sl];
+            const float dx = __fsub_rn(p[q][0], cc.x), dy = __fsub_rn(p[q][1], cc.y), dz = __fsub_rn(p[q][2], cc.z);
+            if (dot3_rn(dx, dy, dz, dx, dy, dz) < cc.w) inmask[q] |= 1u << sl;
+          }
         }
       }
     }
@@ -324,12 +362,19 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
           if (k >= wcount[q]) continue;
           const int sl = S.wslot[k][q][lane];
           const float iz = S.wiz[k][q][lane];
-          const float4 cc = S.cc[sl];
-          const float dx = __fsub_rn(p[q][0], cc.x), dy = __fsub_rn(p[q][1], cc.y), dz = __fsub_rn(p[q][2], cc.z);
-          const float d2 = dot3_rn(dx, dy, dz, dx, dy, dz);
-          // the weight is a value, not a decision: fast square root
-          const float dist = d2 > 0.0f ? __fmul_rn(d2, rsqrtf(d2)) : 0.0f;
-          const float w = fmaxf(0.0f, __fmaf_rn(-dist, S.inv_r[sl], 1.0f));
+          float w;
+          if constexpr (OVAL) {
+            // rho^2 < 1 here (the view was kept for this pixel); the weight 1 - rho is a value
+            const float r2 = oval_rho2(static_cast<WarpSmemOval&>(S).ov[sl], ex, ey[q]);
+            w = fmaxf(0.0f, 1.0f - (r2 > 0.0f ? __fmul_rn(r2, rsqrtf(r2)) : 0.0f));
+          } else {
+            const float4 cc = S.cc[sl];
+            const float dx = __fsub_rn(p[q][0], cc.x), dy = __fsub_rn(p[q][1], cc.y), dz = __fsub_rn(p[q][2], cc.z);
+            const float d2 = dot3_rn(dx, dy, dz, dx, dy, dz);
+            // the weight is a value, not a decision: fast square root
+            const float dist = d2 > 0.0f ? __fmul_rn(d2, rsqrtf(d2)) : 0.0f;
+            w = fmaxf(0.0f, __fmaf_rn(-dist, S.inv_r[sl], 1.0f));
+          }
           const float* Hm = S.Hm[sl];
           const float hx = fmaf(Hm[0], px, fmaf(Hm[1], py[q], fmaf(Hm[9], iz, Hm[2])));
           const float hy = fmaf(Hm[3], px, fmaf(Hm[4], py[q], fmaf(Hm[10], iz, Hm[5])));
@@ -543,13 +588,14 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
 
 // Non-persistent: one CTA per tile, warp w takes strip w.  Persistent: every
 // warp takes (tile, strip) work items from the device counter by itself.
-template <int TW, int TH, int FMT, bool INSPECT, bool PERSISTENT>
+template <int TW, int TH, int FMT, bool INSPECT, bool PERSISTENT, bool OVAL>
 __global__ void __launch_bounds__(TW * TH / kPx, 6) raster_kernel(FrameArgs A) {
   constexpr int WARPS = TW * TH / kPx / 32;
-  __shared__ WarpSmem S[WARPS];
+  using Smem = typename std::conditional<OVAL, WarpSmemOval, WarpSmem>::type;
+  __shared__ Smem S[WARPS];
   const int warp = threadIdx.x >> 5;
   if constexpr (!PERSISTENT) {
-    raster_strip<TW, TH, FMT, INSPECT, false>(A, blockIdx.x, warp, S[warp]);
+    raster_strip<TW, TH, FMT, INSPECT, false, OVAL>(A, blockIdx.x, warp, S[warp]);
   } else {
     const int n_items = A.total_tiles * WARPS;
     for (;;) {
@@ -557,21 +603,27 @@ __global__ void __launch_bounds__(TW * TH / kPx, 6) raster_kernel(FrameArgs A) {
       if ((threadIdx.x & 31) == 0) item = atomicAdd(A.work_counter, 1);
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= n_items) break;
-      raster_strip<TW, TH, FMT, INSPECT, true>(A, item / WARPS, item % WARPS, S[warp]);
+      raster_strip<TW, TH, FMT, INSPECT, true, OVAL>(A, item / WARPS, item % WARPS, S[warp]);
     }
   }
 }
 
-template <int TW, int TH, int FMT>
-static cudaError_t launch_fmt(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s) {
+template <int TW, int TH, int FMT, bool OVAL>
+static cudaError_t launch_disk(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s) {
   if (inspect) {
-    raster_kernel<TW, TH, FMT, true, false><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
+    raster_kernel<TW, TH, FMT, true, false, OVAL><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
   } else if (persistent) {
-    raster_kernel<TW, TH, FMT, false, true><<<pblocks, TW * TH / kPx, 0, s>>>(a);
+    raster_kernel<TW, TH, FMT, false, true, OVAL><<<pblocks, TW * TH / kPx, 0, s>>>(a);
   } else {
-    raster_kernel<TW, TH, FMT, false, false><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
+    raster_kernel<TW, TH, FMT, false, false, OVAL><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
   }
   return cudaGetLastError();
+}
+
+template <int TW, int TH, int FMT>
+static cudaError_t launch_fmt(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s) {
+  if (a.disk_mode == 1) return launch_disk<TW, TH, FMT, true>(a, inspect, persistent, pblocks, s);
+  return launch_disk<TW, TH, FMT, false>(a, inspect, persistent, pblocks, s);
 }
 
 template <int TW, int TH>
@@ -593,24 +645,33 @@ cudaError_t launch_raster(const FrameArgs& a, bool inspect, bool persistent, int
   return cudaErrorInvalidValue;
 }
 
-template <int TW, int TH>
-static cudaError_t occupancy_tile(int fmt, int* n) {
+template <int TW, int TH, bool OVAL>
+static cudaError_t occupancy_disk(int fmt, int* n) {
   switch (fmt) {
     case LF_TEX_F32:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_F32, false, true>, TW * TH / kPx, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_F32, false, true, OVAL>,
+                                                           TW * TH / kPx, 0);
     case LF_TEX_U8:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_U8, false, true>, TW * TH / kPx, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_U8, false, true, OVAL>,
+                                                           TW * TH / kPx, 0);
     case LF_TEX_BF16:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_BF16, false, true>, TW * TH / kPx, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_BF16, false, true, OVAL>,
+                                                           TW * TH / kPx, 0);
     default:
-      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, raster_kernel<TW, TH, LF_TEX_FP8E4M3, false, true>, TW * TH / kPx, 0);
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          n, raster_kernel<TW, TH, LF_TEX_FP8E4M3, false, true, OVAL>, TW * TH / kPx, 0);
   }
 }
 
-cudaError_t raster_occupancy(int tile_w, int tile_h, int fmt, int* n) {
-  if (tile_w == 16 && tile_h == 16) return occupancy_tile<16, 16>(fmt, n);
-  if (tile_w == 32 && tile_h == 8) return occupancy_tile<32, 8>(fmt, n);
-  return occupancy_tile<8, 8>(fmt, n);
+template <int TW, int TH>
+static cudaError_t occupancy_tile(int fmt, int disk_mode, int* n) {
+  return disk_mode == 1 ? occupancy_disk<TW, TH, true>(fmt, n) : occupancy_disk<TW, TH, false>(fmt, n);
+}
+
+cudaError_t raster_occupancy(int tile_w, int tile_h, int fmt, int disk_mode, int* n) {
+  if (tile_w == 16 && tile_h == 16) return occupancy_tile<16, 16>(fmt, disk_mode, n);
+  if (tile_w == 32 && tile_h == 8) return occupancy_tile<32, 8>(fmt, disk_mode, n);
+  return occupancy_tile<8, 8>(fmt, disk_mode, n);
 }
 
 }  // namespace lfk

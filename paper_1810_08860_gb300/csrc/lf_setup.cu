@@ -273,6 +273,38 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
       for (int k = 0; k < 3; ++k) R.cc[k] = __double2float_rn(__dsub_rn((double)V.disk_c[k], A.sphere_c[k]));
       R.cc[3] = __fmul_rn(V.disk_r, V.disk_r);
       R.inv_r = __frcp_rn(V.disk_r);
+      if (A.disk_mode == 1) {
+        // Oval disk (Sec. 4.4): its plane's normal and axes are the columns of M; the
+        // centre in the eye frame and the dot products in FP64, fixed order, each
+        // rounded once.
+        const double dcw[3] = {__dsub_rn((double)V.disk_c[0], E.t[0]), __dsub_rn((double)V.disk_c[1], E.t[1]),
+                               __dsub_rn((double)V.disk_c[2], E.t[2])};
+        double cp[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          double s = __dmul_rn(E.R[0 * 3 + r], dcw[0]);
+          s = __dadd_rn(s, __dmul_rn(E.R[1 * 3 + r], dcw[1]));
+          s = __dadd_rn(s, __dmul_rn(E.R[2 * 3 + r], dcw[2]));
+          cp[r] = s;
+        }
+        auto dotc = [&](int col) {
+          return __dadd_rn(__dadd_rn(__dmul_rn(M[0 * 3 + col], cp[0]), __dmul_rn(M[1 * 3 + col], cp[1])),
+                           __dmul_rn(M[2 * 3 + col], cp[2]));
+        };
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          R.ov_x[k] = Mc[k * 3 + 0];
+          R.ov_y[k] = Mc[k * 3 + 1];
+          R.ov_n[k] = Mc[k * 3 + 2];
+        }
+        R.ov_k = __double2float_rn(dotc(2));
+        R.ov_u0 = __double2float_rn(dotc(0));
+        R.ov_v0 = __double2float_rn(dotc(1));
+        R.ov_ru[0] = __double2float_rn(__ddiv_rn(1.0, (double)V.disk_ext[0]));
+        R.ov_ru[1] = __double2float_rn(__ddiv_rn(1.0, (double)V.disk_ext[1]));
+        R.ov_rv[0] = __double2float_rn(__ddiv_rn(1.0, (double)V.disk_ext[2]));
+        R.ov_rv[1] = __double2float_rn(__ddiv_rn(1.0, (double)V.disk_ext[3]));
+      }
       R.tri_base = 0;
       R.bin_off = -1;
       R.big_base = 0;
@@ -287,7 +319,11 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
       for (int k = 0; k < 3; ++k) cw[k] = (float)((double)V.disk_c[k] - E.t[k]);
       for (int r = 0; r < 3; ++r)
         ce[r] = (float)E.R[0 * 3 + r] * cw[0] + (float)E.R[1 * 3 + r] * cw[1] + (float)E.R[2 * 3 + r] * cw[2];
-      const float rho = V.disk_r * 1.001f + 1e-4f;
+      // an oval lies in the disk of its largest extent about c_i, in its plane
+      const float r_out = A.disk_mode == 1 ? fmaxf(fmaxf(V.disk_ext[0], V.disk_ext[1]),
+                                                    fmaxf(V.disk_ext[2], V.disk_ext[3]))
+                                           : V.disk_r;
+      const float rho = r_out * 1.001f + 1e-4f;
       float xlo, xhi, ylo, yhi;
       if (axis_extent(ce[0], ce[2], rho, xlo, xhi) && axis_extent(ce[1], ce[2], rho, ylo, yhi)) {
         int x0, x1, y0, y1;

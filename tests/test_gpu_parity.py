@@ -292,9 +292,16 @@ def rig():
     return scene.rig_light_field(1)
 
 
-def test_rig_scale_sampled(lfmod, rig):
+@pytest.mark.parametrize("disks", ["round", "oval"])
+def test_rig_scale_sampled(lfmod, rig, disks):
+    import dataclasses
+
     import torch
 
+    if disks == "oval":  # asymmetric ovals from the Delaunay 1-ring (Sec. 4.4)
+        from paper_1810_08860_gb300 import disks as dk
+
+        rig = dataclasses.replace(rig, disk_ext=dk.oval_extents(rig))
     r = lfmod.Renderer(0)
     r.load_views(rig)
     r.build_meshes(rig)
@@ -326,6 +333,59 @@ def test_rig_scale_sampled(lfmod, rig):
         assert st["active_views"][e] == int(sel.sum())
         assert (got["rgba"].cpu() == out[e].cpu()).all()
     r.close()
+
+
+# ---------------------------------------------------------------- asymmetric oval disks (Sec. 4.4)
+
+
+@pytest.fixture(scope="module")
+def tiny_oval(tiny):
+    import dataclasses
+
+    from paper_1810_08860_gb300 import disks
+
+    return dataclasses.replace(tiny, disk_ext=disks.oval_extents(tiny))
+
+
+def test_oval_disks_full_frames(lfmod, tiny_oval, tiny):
+    r = lfmod.Renderer(0)
+    r.load_views(tiny_oval)
+    r.build_meshes(tiny_oval)
+    got, ref = _check_full_frame(r, tiny_oval, tiny_oval.eyes[0])
+    assert got["active"].sum() >= 4 and ref["stats"]["frag_win"] > 10000
+    eye = scene.Eye(tiny.eyes[0].pose, np.array([50.0, 47.0, 31.3, 29.9]), 75, 53)
+    _check_full_frame(r, tiny_oval, eye)
+    # back to round disks: the plain method again, bit for bit
+    oval_img = r.render([tiny.eyes[0]])[0].cpu()
+    r.set_disk_ovals(None)
+    rr = lfmod.Renderer(0)
+    rr.load_views(tiny)
+    rr.build_meshes(tiny)
+    import torch
+
+    assert torch.equal(r.render([tiny.eyes[0]])[0].cpu(), rr.render([tiny.eyes[0]])[0].cpu())
+    assert not torch.equal(oval_img, rr.render([tiny.eyes[0]])[0].cpu())
+    r.close()
+    rr.close()
+
+
+def test_oval_disks_tiles_and_batch(lfmod, tiny_oval):
+    import torch
+
+    eye = tiny_oval.eyes[0]
+    base = lfmod.Renderer(0)
+    base.load_views(tiny_oval)
+    base.build_meshes(tiny_oval)
+    want = base.render([eye])[0].cpu()
+    for tile in [(32, 8), (8, 8)]:
+        r = lfmod.Renderer(0, tile=tile, max_eyes=3)
+        r.load_views(tiny_oval)
+        r.build_meshes(tiny_oval)
+        assert torch.equal(r.render([eye])[0].cpu(), want)
+        b = r.render_batch([eye, eye, eye])
+        assert all(torch.equal(x.cpu(), want) for x in b)
+        r.close()
+    base.close()
 
 
 # ---------------------------------------------------------------- batched render and its autotuner
