@@ -204,9 +204,9 @@ def host_e2e(r, heads, shapes, flush, stream, steps, px_per_step, world, form="p
 
     n_sets = in_flight or lfm.HOST_FRAMES_IN_FLIGHT
     sets = [[torch.empty(sh, dtype=torch.float32, pin_memory=True) for sh in shapes] for _ in range(n_sets)]
-    for k in range(len(sets)):  # warm the slots
-        r.render_host(heads[k % len(heads)], out=sets[k], form=form, stream=stream)
-    r.host_wait()
+    for k in range(lfm.HOST_FRAMES_IN_FLIGHT):  # allocate every device slot of the library before timing
+        r.render_host(heads[k % len(heads)], out=sets[k % n_sets], form=form, stream=stream)
+        r.host_wait()
     torch.cuda.synchronize()
     barrier_all()
     t0 = time.perf_counter()
