@@ -436,6 +436,9 @@ typedef struct {
  *               (rgb, 1) where the ratio's denominator is > 0, else (0,0,0,0);
  *               not clamped (the Lanczos lobes can overshoot [0, 1])
  *   stream      cudaStream_t to run on
+ * The aperture is view i's round disk (radius disk_r) on the capture sphere,
+ * also when oval extents are set on `ctx` (uniform samples of a four-quarter
+ * oval would need per-quarter area weights in Eq. 5).
  * Uses per-call scratch of n_samples x supersample^2 x W x H x 16 bytes on
  * `ctx`.  Blocks until done.  Errors: LF_ERR_INVALID_ARG, LF_ERR_STATE (either
  * model not loaded), LF_ERR_CAPACITY (a dense render overflowed its scratch:

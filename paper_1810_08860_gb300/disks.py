@@ -21,6 +21,8 @@ def delaunay_neighbours(disk_c, sphere_c) -> list[set]:
     from scipy.spatial import ConvexHull
 
     d = np.asarray(disk_c, dtype=np.float64) - np.asarray(sphere_c, dtype=np.float64)
+    if d.shape[0] < 4:
+        raise ValueError("a Delaunay triangulation on the sphere needs at least 4 disk centres")
     u = d / np.linalg.norm(d, axis=1, keepdims=True)
     hull = ConvexHull(u)
     # median nearest-neighbour angle, from the hull's own edges
