@@ -369,6 +369,35 @@ def test_oval_disks_full_frames(lfmod, tiny_oval, tiny):
     rr.close()
 
 
+def test_oval_disk_errors(lfmod, tiny):
+    r = lfmod.Renderer(0)
+    r.n_views = tiny.n_views  # the binding's own row check passes; the library must refuse
+    with pytest.raises(lfmod.LFError) as info:
+        r.set_disk_ovals(np.full((tiny.n_views, 4), 0.05, np.float32))
+    assert info.value.status == 4  # no views loaded
+    r.load_views(tiny)
+    r.build_meshes(tiny)
+    bad = np.full((tiny.n_views, 4), 0.05, np.float32)
+    bad[3, 2] = 0.0
+    with pytest.raises(lfmod.LFError) as info:
+        r.set_disk_ovals(bad)
+    assert info.value.status == 1
+    bad[3, 2] = np.nan
+    with pytest.raises(lfmod.LFError):
+        r.set_disk_ovals(bad)
+    with pytest.raises(ValueError):
+        r.set_disk_ovals(np.full((tiny.n_views - 1, 4), 0.05, np.float32))
+    # a refused call leaves round disks in place
+    base = lfmod.Renderer(0)
+    base.load_views(tiny)
+    base.build_meshes(tiny)
+    import torch
+
+    assert torch.equal(r.render([tiny.eyes[0]])[0].cpu(), base.render([tiny.eyes[0]])[0].cpu())
+    r.close()
+    base.close()
+
+
 def test_oval_disks_tiles_and_batch(lfmod, tiny_oval):
     import torch
 

@@ -249,3 +249,18 @@ def test_sparse_renders_give_the_same_values():
     full = pf.prefilter(lf, lf, 7, samples, pixels=pix)
     sparse = pf.prefilter(lf, lf, 7, samples, pixels=pix, sparse=True)
     assert np.array_equal(full, sparse)
+
+
+def test_prefilter_sample_sets():
+    import paper_1810_08860_gb300 as lfm
+
+    for n in (1, 7, 16, 40):
+        S = lfm.prefilter_samples(n, 3)
+        assert S.dtype == np.float32 and S.shape == (n, 4)
+        assert np.all((S[:, :2] >= 0) & (S[:, :2] < 1)) and np.all(np.abs(S[:, 2:]) <= 2)
+        # one a per stratum of [0, 1)
+        assert sorted(np.floor(S[:, 0].astype(np.float64) * n).astype(int).tolist()) == list(range(n))
+    S = lfm.prefilter_samples(16, 5)
+    cells = {(int((x + 2) // 1), int((y + 2) // 1)) for x, y in S[:, 2:].astype(np.float64)}
+    assert len(cells) == 16  # a jittered 4 x 4 grid over [-2, 2)^2: one offset per cell
+    assert np.array_equal(S, lfm.prefilter_samples(16, 5))  # seeded
