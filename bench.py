@@ -48,6 +48,7 @@ def parse_args():
     p.add_argument("--workload", choices=["rig", "rig256", "tiny", "batch", "learned", "refine", "prefilter"],
                    default="rig")
     p.add_argument("--samples", type=int, default=32, help="prefilter: Monte Carlo samples per pixel (Eq. 5)")
+    p.add_argument("--supersample", type=int, default=1, help="prefilter: scale of the Lbar renders")
     p.add_argument("--refine-kernel", choices=["fused", "layers"], default="fused")
     p.add_argument("--poses", type=int, default=8, help="distinct head poses cycled through")
     p.add_argument("--tex", choices=["f32", "u8", "bf16", "fp8"], default="f32")
@@ -716,8 +717,9 @@ def run_prefilter(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     first = lambda k: ((k + rank) % n_blocks) * V  # noqa: E731  ranks take different blocks
+    S = args.supersample
     for k in range(args.warmup):
-        rt.prefilter(rd, samples, first_view=first(k), n_views=V, out=out)
+        rt.prefilter(rd, samples, first_view=first(k), n_views=V, supersample=S, out=out)
     torch.cuda.synchronize()
     barrier_all()
     clocks = ClockSampler(local)
@@ -727,7 +729,7 @@ def run_prefilter(args):
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        rt.prefilter(rd, samples, first_view=first(args.warmup + k), n_views=V, out=out)
+        rt.prefilter(rd, samples, first_view=first(args.warmup + k), n_views=V, supersample=S, out=out)
         ev[k][1].record(stream)
         raster_ms.append(rd.stats()["ms_raster"])  # the last view's batched dense render
     torch.cuda.synchronize()
@@ -742,14 +744,14 @@ def run_prefilter(args):
     for k, (a, b) in enumerate(e2e_ev):
         flush.zero_()
         a.record(stream)
-        rt.prefilter(rd, samples, first_view=first(k), n_views=V, out=out)
+        rt.prefilter(rd, samples, first_view=first(k), n_views=V, supersample=S, out=out)
         host.copy_(out, non_blocking=True)
         b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev)) / len(e2e_ev)
 
     # roofline of the dense raster: the J renders of one view read these texels and write J images
-    P, K, (Ws, Hs) = rt.prefilter_cameras(0, samples)
+    P, K, (Ws, Hs) = rt.prefilter_cameras(0, samples, supersample=S)
     cams = [scene.Eye(P[j], K[j], Ws, Hs) for j in range(J)]
     uniq = rd.unique_texels(cams, dense.width, dense.height)
     raster_bytes = uniq * 4 + J * Ws * Hs * 16
@@ -762,8 +764,8 @@ def run_prefilter(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "prefilter: rig model (1,024 Fibonacci views 1024^2 at 120 deg, 64^2 meshes), "
                                "Lbar from a %d-view dense model with %d^2 meshes (u8 textures); %d samples per "
-                               "pixel (stratified, seed %d, weight balance %.2f); %d views per step" % (
-                                   args.dense_views, args.dense_grid, J, seed, balance, V),
+                               "pixel (stratified, seed %d, weight balance %.2f); %d views per step; renders "
+                               "at %dx" % (args.dense_views, args.dense_grid, J, seed, balance, V, S),
                    "l2": "flushed (256 MiB write) between steps, outside the timed events",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "per_step": {"renders": V * J, "render_pixels": V * J * Ws * Hs, "ms_per_render": total_ms / args.steps / (V * J)},
@@ -779,7 +781,7 @@ def run_prefilter(args):
         "scene_generation_s": gen_s,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["quality"] = prefilter_quality(lfm, scene, rt, rd, lf, samples, local)
+        result["quality"] = prefilter_quality(lfm, scene, rt, rd, lf, samples, local, S)
         from oracle import prefilter as opf
 
         rng = np.random.default_rng(13)
@@ -798,7 +800,7 @@ def run_prefilter(args):
     return 0
 
 
-def prefilter_quality(lfm, scene, rt, rd, lf, samples, local):
+def prefilter_quality(lfm, scene, rt, rd, lf, samples, local, supersample=1):
     """PSNR against the analytic truth of the rig's stereo eyes rendered from the
     original images and from images prefiltered (every view the eyes select)."""
     import dataclasses
@@ -815,7 +817,8 @@ def prefilter_quality(lfm, scene, rt, rd, lf, samples, local):
     for run in runs:
         for c0 in range(0, len(run), 32):
             part = run[c0:c0 + 32]
-            o = rt.prefilter(rd, samples, first_view=int(part[0]), n_views=len(part)).cpu().numpy()
+            o = rt.prefilter(rd, samples, first_view=int(part[0]), n_views=len(part),
+                             supersample=supersample).cpu().numpy()
             rgb8 = np.clip(np.rint(o[..., :3] * 255.0), 0, 255).astype(np.uint8)
             for m, v in enumerate(part):
                 ok = o[m, ..., 3] > 0
