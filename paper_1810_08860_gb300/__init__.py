@@ -217,6 +217,8 @@ class Renderer:
         self.ctx = ctypes.c_void_p()
         self._check(self.lib.lf_create(device, ctypes.byref(cfg), ctypes.byref(self.ctx)), "lf_create")
         self.n_views = 0
+        self._src_hw = (0, 0)   # source image size once views are loaded
+        self._in_flight = []    # (frame, host tensors) of render_host not yet known to be delivered
 
     def close(self):
         if self.ctx:
@@ -318,7 +320,7 @@ class Renderer:
         self._check(self.lib.lf_render_host(self.ctx, len(eyes), poses, intr, ptrs, HOST_FORMS[form],
                                             ctypes.byref(frame), _stream_handle(stream)), "lf_render_host")
         # keep the host buffers alive until their frame is delivered
-        self._in_flight = [(f, o) for f, o in getattr(self, "_in_flight", []) if f > frame.value - HOST_FRAMES_IN_FLIGHT]
+        self._in_flight = [(f, o) for f, o in self._in_flight if f > frame.value - HOST_FRAMES_IN_FLIGHT]
         self._in_flight.append((frame.value, out))
         return frame.value, out
 
@@ -330,7 +332,7 @@ class Renderer:
         if frame < 0:
             self._in_flight = []
         else:
-            self._in_flight = [(f, o) for f, o in getattr(self, "_in_flight", []) if f > frame]
+            self._in_flight = [(f, o) for f, o in self._in_flight if f > frame]
         return err.value
 
     def render_batch(self, eyes, out=None, stream=None):
@@ -487,7 +489,7 @@ class Renderer:
         import torch
         S = np.ascontiguousarray(np.asarray(samples, dtype=np.float32).reshape(-1, 4))
         if n_views is None:
-            n_views = self.n_views - first_view
+            n_views = max(0, self.n_views - first_view)
         H, W = self._src_hw
         if out is None:
             out = torch.empty((n_views, H, W, 4), dtype=torch.float32, device="cuda:%d" % self.device)
