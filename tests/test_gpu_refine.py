@@ -287,7 +287,7 @@ def _psnr(a, b):
 def test_training_on_method_generated_pairs_gains_over_the_plain_render(lfmod):
     # fast: 4x4 views on the cap with 12x12 meshes; target: the same scene from
     # 8x8 views with 64x64 meshes, 2x2 supersampled (the method with a denser
-    # light field, as the offline model of Sec. 5).  Train on 256 poses, judge
+    # light field, as the offline model of Sec. 5).  Train on 256 poses, evaluate
     # on 32 held-out poses against the plain fast render.
     import math
 
