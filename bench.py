@@ -322,9 +322,17 @@ def cpu_baseline(lf, eye, seconds: float):
         if total_t >= seconds or total_pix >= 4_000_000:
             break
         n = int(min(max(n * 2, 2000), 400_000))
+    # the same oracle on one thread, over a smaller bounded sample
+    n1, t1 = 2000, 0.0
+    pix = np.stack([rng.integers(0, eye.width, n1), rng.integers(0, eye.height, n1)], axis=1)
+    t0 = time.perf_counter()
+    oracle.render(lf, eye, pixels=pix, threads=1)
+    t1 = time.perf_counter() - t0
     return {"value": total_pix / total_t / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d random pixels of one %dx%d eye of the same workload (each call also builds the "
-                      "per-view meshes it needs), %.1f s" % (total_pix, eye.width, eye.height, total_t)}
+                      "per-view meshes it needs), %.1f s" % (total_pix, eye.width, eye.height, total_t),
+            "single_thread": {"value": n1 / t1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": "%d random pixels, %.1f s" % (n1, t1)}}
 
 
 def quality_vs_oracle(r, lf, head, n_pixels):
