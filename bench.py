@@ -1159,7 +1159,9 @@ def run_ours(args):
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
-    if rank == 0 and args.quality_pixels > 0:
+    # the CPU-baseline leg (the only part of this arm that runs the oracle) also compares
+    # sampled pixels of the GPU frame against it
+    if rank == 0 and not args.no_cpu_baseline and args.quality_pixels > 0:
         result["quality"] = quality_vs_oracle(r, lf, heads[0], args.quality_pixels)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(lf, heads[0][0], args.cpu_seconds)
