@@ -454,6 +454,38 @@ LF_API lf_status lf_prefilter(lf_ctx* ctx, lf_ctx* dense, int32_t first_view, in
 LF_API lf_status lf_prefilter_cameras(lf_ctx* ctx, int32_t view, int32_t n_samples, const lf_prefilter_sample* samples,
                                       int32_t supersample, lf_pose* poses, lf_intrinsics* intr);
 
+/* ------------------------------------------------------------------------
+ * Page cache for streamed light field images (the tile cache of Sec. 4.2.1
+ * with the per-frame decode budget of Sec. 7.2's two-level progressive
+ * renderer).  Host-only bookkeeping, no CUDA calls: it decides which of
+ * n_items images occupy which of `capacity` device pages; the caller copies
+ * each admitted image into its page and renders the coarse level for wanted
+ * images left without one.
+ * ------------------------------------------------------------------------ */
+typedef struct lf_cache lf_cache;
+
+/* n_items >= 1 images, capacity >= 1 pages, all free.  LF_ERR_INVALID_ARG, LF_ERR_OOM. */
+LF_API lf_status lf_cache_create(int32_t n_items, int32_t capacity, lf_cache** out);
+
+/* NULL-safe. */
+LF_API void lf_cache_destroy(lf_cache* cache);
+
+/*
+ * One frame.  `wanted` lists the images the frame needs, most important first
+ * (ids in [0, n_items), host).  Resident wanted images stay.  Missing ones are
+ * admitted in list order, at most `budget` of them.  Each goes into a free page
+ * or else into the page of the earliest admitted image the frame does not want
+ * (first in, first out).  Wanted images that find no page stay missing.
+ * Outputs (host, caller-owned, room for `budget` entries): the admitted images
+ * and their pages, and their count in *n_uploads.  LF_ERR_INVALID_ARG on a bad
+ * id or pointer.
+ */
+LF_API lf_status lf_cache_frame(lf_cache* cache, int32_t n_wanted, const int32_t* wanted, int32_t budget,
+                                int32_t* n_uploads, int32_t* upload_items, int32_t* upload_pages);
+
+/* The page of every image after the last frame (-1: not resident), n_items entries (host). */
+LF_API lf_status lf_cache_pages(const lf_cache* cache, int32_t* page_of_item);
+
 /* Counters of the last render call; synchronises with its stream. */
 LF_API lf_status lf_get_stats(lf_ctx* ctx, lf_stats* out);
 

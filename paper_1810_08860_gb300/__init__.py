@@ -69,7 +69,8 @@ EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_
            "lf_render_batch", "lf_render_inspect", "lf_render_static", "lf_tune_batch", "lf_get_stats",
            "lf_status_string", "lf_last_error", "lf_load_refiner", "lf_refine_set_kernel", "lf_get_refiner",
            "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined", "lf_render_host",
-           "lf_host_wait", "lf_prefilter", "lf_prefilter_cameras", "lf_set_disk_ovals"]
+           "lf_host_wait", "lf_prefilter", "lf_prefilter_cameras", "lf_set_disk_ovals",
+           "lf_cache_create", "lf_cache_destroy", "lf_cache_frame", "lf_cache_pages"]
 HOST_FRAMES_IN_FLIGHT = 3
 HOST_FORMS = {"plain": 0, "refined": 1, "batch": 2}
 
@@ -164,6 +165,14 @@ def load_library(path: str = LIB_PATH):
     lib.lf_host_wait.restype = ctypes.c_int
     lib.lf_prefilter.argtypes = [vp, vp, i32, i32, i32, vp, i32, vp, vp]
     lib.lf_prefilter.restype = ctypes.c_int
+    lib.lf_cache_create.argtypes = [i32, i32, ctypes.POINTER(vp)]
+    lib.lf_cache_create.restype = ctypes.c_int
+    lib.lf_cache_destroy.argtypes = [vp]
+    lib.lf_cache_destroy.restype = None
+    lib.lf_cache_frame.argtypes = [vp, i32, vp, i32, ctypes.POINTER(i32), vp, vp]
+    lib.lf_cache_frame.restype = ctypes.c_int
+    lib.lf_cache_pages.argtypes = [vp, vp]
+    lib.lf_cache_pages.restype = ctypes.c_int
     lib.lf_set_disk_ovals.argtypes = [vp, vp]
     lib.lf_set_disk_ovals.restype = ctypes.c_int
     lib.lf_prefilter_cameras.argtypes = [vp, i32, i32, vp, i32, vp, vp]
@@ -197,6 +206,48 @@ def _stream_handle(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+class PageCache:
+    """Host-side page cache of streamed images (lf_cache_*): which of n_items
+    images occupy which of `capacity` device pages, FIFO eviction of images the
+    frame does not want, at most `budget` admissions per frame."""
+
+    def __init__(self, n_items: int, capacity: int):
+        self.lib = load_library()
+        self.h = ctypes.c_void_p()
+        st = self.lib.lf_cache_create(int(n_items), int(capacity), ctypes.byref(self.h))
+        if st != LF_OK:
+            raise LFError(st, "lf_cache_create failed")
+        self.n_items = int(n_items)
+
+    def frame(self, wanted, budget: int):
+        """Admit missing wanted images (most important first); returns [(item, page)]."""
+        w = np.ascontiguousarray(np.asarray(wanted, dtype=np.int32).ravel())
+        items = np.zeros(max(int(budget), 1), np.int32)
+        pages = np.zeros(max(int(budget), 1), np.int32)
+        n = ctypes.c_int32(0)
+        st = self.lib.lf_cache_frame(self.h, w.size, w.ctypes.data_as(ctypes.c_void_p), int(budget), ctypes.byref(n),
+                                     items.ctypes.data_as(ctypes.c_void_p), pages.ctypes.data_as(ctypes.c_void_p))
+        if st != LF_OK:
+            raise LFError(st, "lf_cache_frame failed")
+        return list(zip(items[:n.value].tolist(), pages[:n.value].tolist()))
+
+    def pages(self) -> np.ndarray:
+        out = np.zeros(self.n_items, np.int32)
+        self.lib.lf_cache_pages(self.h, out.ctypes.data_as(ctypes.c_void_p))
+        return out
+
+    def close(self):
+        if self.h:
+            self.lib.lf_cache_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Renderer:
