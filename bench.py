@@ -347,6 +347,7 @@ def quality_vs_oracle(r, lf, head, n_pixels):
     out = r.render(head)
     torch.cuda.synchronize()
     diffs, mism = [], 0
+    n_rec = n_rec_diff = 0
     for eye, img in zip(head, out):
         pix = np.stack([rng.integers(0, eye.width, n_pixels), rng.integers(0, eye.height, n_pixels)], axis=1)
         ref = oracle.render(lf, eye, pixels=pix)["rgba"]
@@ -354,6 +355,24 @@ def quality_vs_oracle(r, lf, head, n_pixels):
         valid = (ref[:, 3] > 0) & (g[:, 3] > 0)
         mism += int(np.sum((ref[:, 3] > 0) != (g[:, 3] > 0)))
         diffs.append(g[valid][:, :3] - ref[valid][:, :3])
+        # coverage records at the same pixels against the FP64-decision oracle (the definition)
+        got = r.render_inspect(eye, max_records=32)
+        ref64 = oracle.render(lf, eye, pixels=pix, fragments=True, max_slots=32, decisions="fp64")
+        want = {}
+        for f in ref64["frags"]:
+            i, j = pix[int(f["pixel"])]
+            want[(int(j) * eye.width + int(i), int(f["view"]))] = (
+                int(f["n_cover"]), int(f["winner"]), int(f["min_id"]), int(f["max_id"]), int(f["id_hash"]))
+        have = {}
+        for i, j in pix:
+            k = int(j) * eye.width + int(i)
+            for rec in got["records"][k][:min(int(got["counts"][k]), 32)]:
+                have[(k, int(rec["view"]))] = (int(rec["n_cover"]), int(rec["winner"]), int(rec["min_id"]),
+                                               int(rec["max_id"]), int(rec["id_hash"]))
+        keys = set(want) | set(have)
+        n_rec += len(keys)
+        n_rec_diff += sum(1 for k in keys if want.get(k) != have.get(k))
+        del got
     d = np.concatenate(diffs)
     mse = float(np.mean(d * d)) if d.size else 0.0
     # reconstruction error of the method itself: every valid pixel of both eyes
@@ -370,6 +389,10 @@ def quality_vs_oracle(r, lf, head, n_pixels):
         n_truth += e.size
     mse_t = sq / n_truth if n_truth else 0.0
     return {"vs": "FP64 oracle", "pixels": int(d.shape[0]), "max_abs": float(np.abs(d).max()) if d.size else 0.0,
+            "records_vs_fp64_decisions": {"compared": n_rec, "differ": n_rec_diff,
+                                          "frac": n_rec_diff / n_rec if n_rec else 0.0,
+                                          "what": "(pixel, view) coverage records of the sampled pixels against "
+                                                  "the oracle taking its snap, depth and disk decisions in FP64"},
             "psnr_db": (10.0 * math.log10(1.0 / mse)) if mse > 0 else float("inf"), "valid_mask_mismatches": mism,
             "psnr_vs_analytic_truth_db": (10.0 * math.log10(1.0 / mse_t)) if mse_t > 0 else float("inf"),
             "truth": "analytic ray cast of the scene, every valid pixel of both eyes"}

@@ -8,10 +8,16 @@ imports this package and shares no code with it.
 as a plain per-pixel loop: Eq. 1 (one ray query per eye pixel), Eq. 2 (disk
 weighted, normalised sum over views), the linear disk kernel of Sec. 4.1, and
 the intra-image occlusion test of Sec. 4.2.2, rasterising each view's mesh
-with a 1/256-pixel snapped int64 edge-function rasteriser.  Values are FP64;
-the integer decisions (snap, depth winner, disk membership) are FP32, the
-precision of the fast renderer, with the operation order fixed in the C
-source.
+with a 1/256-pixel snapped int64 edge-function rasteriser.  Values are FP64.
+The integer decisions (near-plane test, snap, depth winner, disk membership)
+take one of two modes, `decisions=`:
+  "fp64"  the definition: FP64 transform through world coordinates, llrint of
+          the FP64 projection, nearest FP64 depth, FP64 disk test;
+  "fp32"  the fast renderer's reading of it: the same decisions in FP32 with
+          the operation order fixed in the C source (the default, so that the
+          CUDA path can be compared with it bit for bit).
+`margins` says how close a (pixel, view) lies to each decision boundary, which
+explains every place where the two modes differ.
 """
 from __future__ import annotations
 
@@ -45,7 +51,10 @@ class LightFieldC(ctypes.Structure):
                 ("rgba", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("disk_c", ctypes.c_void_p),
                 ("disk_r", ctypes.c_void_p), ("sphere_c", ctypes.c_double * 3),
                 ("sphere_r", ctypes.c_double), ("z_near", ctypes.c_float), ("pad", ctypes.c_int32),
-                ("disk_ext", ctypes.c_void_p)]
+                ("disk_ext", ctypes.c_void_p), ("decisions", ctypes.c_int32), ("pad2", ctypes.c_int32)]
+
+
+DECISIONS = {"fp32": 0, "fp64": 1}
 
 
 class EyeC(ctypes.Structure):
@@ -79,6 +88,8 @@ def _load():
         lib.orc_view_triangles.restype = ctypes.c_int64
         lib.orc_cover_raw.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32]
         lib.orc_cover_raw.restype = ctypes.c_int
+        lib.orc_margins.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
+        lib.orc_margins.restype = ctypes.c_int
         lib.orc_mix32.argtypes = [ctypes.c_uint32]
         lib.orc_mix32.restype = ctypes.c_uint32
         _lib = lib
@@ -88,7 +99,7 @@ def _load():
 class _Bound:
     """Keeps the numpy arrays behind a LightFieldC alive."""
 
-    def __init__(self, lf, z_near: float):
+    def __init__(self, lf, z_near: float, decisions: str = "fp32"):
         self.poses = np.ascontiguousarray(lf.poses, dtype=np.float64)
         self.intr = np.ascontiguousarray(lf.intr, dtype=np.float64)
         self.rgba = np.ascontiguousarray(lf.images, dtype=np.uint8)
@@ -111,6 +122,9 @@ class _Bound:
         ext = getattr(lf, "disk_ext", None)
         self.disk_ext = None if ext is None else np.ascontiguousarray(ext, dtype=np.float32).reshape(-1, 4)
         c.disk_ext = None if self.disk_ext is None else self.disk_ext.ctypes.data
+        if decisions not in DECISIONS:
+            raise ValueError("decisions must be 'fp32' or 'fp64'")
+        c.decisions = DECISIONS[decisions]
         self.c = c
 
 
@@ -129,14 +143,14 @@ def _threads(n):
 
 
 def render(lf, eye, pixels=None, z_near: float = 0.1, max_slots: int = 32, fragments: bool = False,
-           texel_bits: bool = False, threads: int | None = None):
+           texel_bits: bool = False, threads: int | None = None, decisions: str = "fp32"):
     """Render one eye (all pixels, or an (n, 2) int array of (i, j)).
 
     Returns a dict: rgba (n x 4 float64, or H x W x 4 when pixels is None),
     stats, and optionally frags (structured records with a `pixel` index into
     the pixel list), n_slots, and unique_texels."""
     lib = _load()
-    b = _Bound(lf, z_near)
+    b = _Bound(lf, z_near, decisions)
     e = _eye_c(eye)
     if pixels is None:
         n = eye.width * eye.height
@@ -174,10 +188,10 @@ def render(lf, eye, pixels=None, z_near: float = 0.1, max_slots: int = 32, fragm
     return res
 
 
-def select_views(lf, eye, pixels=None, threads: int | None = None) -> np.ndarray:
+def select_views(lf, eye, pixels=None, threads: int | None = None, decisions: str = "fp32") -> np.ndarray:
     """Boolean mask of views whose disk contains the sphere crossing of some pixel."""
     lib = _load()
-    b = _Bound(lf, 0.1)
+    b = _Bound(lf, 0.1, decisions)
     e = _eye_c(eye)
     active = np.zeros(lf.n_views, dtype=np.uint8)
     if pixels is None:
@@ -192,10 +206,11 @@ def select_views(lf, eye, pixels=None, threads: int | None = None) -> np.ndarray
     return active.astype(bool)
 
 
-def pixel_fragments(lf, eye, i: int, j: int, view: int, z_near: float = 0.1, cap: int = 64):
+def pixel_fragments(lf, eye, i: int, j: int, view: int, z_near: float = 0.1, cap: int = 64,
+                    decisions: str = "fp32"):
     """All covering fragments of (pixel, view): ids, FP32 1/z key, FP64 depth."""
     lib = _load()
-    b = _Bound(lf, z_near)
+    b = _Bound(lf, z_near, decisions)
     e = _eye_c(eye)
     ids = np.zeros(cap, dtype=np.int32)
     iz = np.zeros(cap, dtype=np.float32)
@@ -207,10 +222,10 @@ def pixel_fragments(lf, eye, i: int, j: int, view: int, z_near: float = 0.1, cap
     return ids[:n], iz[:n], z[:n]
 
 
-def view_triangles(lf, eye, view: int, z_near: float = 0.1):
+def view_triangles(lf, eye, view: int, z_near: float = 0.1, decisions: str = "fp32"):
     """Snapped, clipped, positively oriented triangles of one view: (n x 7 int64, stats)."""
     lib = _load()
-    b = _Bound(lf, z_near)
+    b = _Bound(lf, z_near, decisions)
     e = _eye_c(eye)
     cap = 4 * (lf.grid_n - 1) ** 2 + 4
     rows = np.zeros((cap, 7), dtype=np.int64)
@@ -233,3 +248,21 @@ def covers(X, Y, i: int, j: int) -> int:
 
 def mix32(x: int) -> int:
     return int(_load().orc_mix32(x))
+
+
+def margins(lf, eye, pixel_views, z_near: float = 0.1, decisions: str = "fp64") -> np.ndarray:
+    """Distances of (i, j, view) triples to the decision boundaries, (n, 3):
+    disk (|p - c|/r - 1, or rho - 1 for ovals; NaN without a crossing),
+    coverage (subpixels from the pixel centre to the nearest snapped edge of
+    the view's sub-triangles near it), depth ((z2 - z1)/z1 of the two nearest
+    covering parents)."""
+    lib = _load()
+    b = _Bound(lf, z_near, decisions)
+    e = _eye_c(eye)
+    pv = np.ascontiguousarray(pixel_views, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros((pv.shape[0], 3), dtype=np.float64)
+    rc = lib.orc_margins(ctypes.byref(b.c), ctypes.byref(e), pv.ctypes.data if pv.size else None, pv.shape[0],
+                         out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("orc_margins failed with code %d" % rc)
+    return out

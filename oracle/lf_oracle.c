@@ -33,14 +33,24 @@
  * crossing is involved in this mode.
  *
  * Precision.  Colour, weights, depths and texture coordinates are FP64.  The
- * discrete decisions - the snapped vertex positions, which triangle wins the
- * depth test, and whether p lies inside a disk - are taken in FP32 with the
- * fixed operation order written below, because those are the precision of
- * the fast renderer they are compared with (a float deciding an integer is
- * decided in the same precision on both sides).  The per-view pose
- * composition feeding them is FP64, rounded once to FP32.  Build with
- * -ffp-contract=off so no multiply-add is fused behind the code's back; every
- * fused multiply-add below is an explicit fmaf().
+ * discrete decisions - whether a vertex lies in front of the near plane, the
+ * snapped vertex positions, which triangle wins the depth test, and whether p
+ * lies inside a disk - are taken in one of two modes (orc_lightfield.decisions):
+ *   ORC_DECIDE_FP64  the definition: the vertex goes to the eye through world
+ *       coordinates, X_eye = R_eye^T (R_i X_cam + t_i - t_eye), in FP64 with no
+ *       fused operations; the snap is llrint(256 (f x / z + c)) of the FP64
+ *       projection; the clip point is interpolated in FP64; the depth winner is
+ *       the smallest FP64 depth z = d / (n . e) of the parent triangle's plane
+ *       (fragments with n . e = 0 or z <= 0 are dropped); disk membership is
+ *       |p - c_i|^2 < r_i^2 in FP64 at the FP64 sphere crossing.
+ *   ORC_DECIDE_FP32  the fast renderer's reading: the same decisions in FP32,
+ *       with the operation order written below (the pose composition is FP64,
+ *       rounded once to FP32), so that a float deciding an integer is decided in
+ *       the same precision on both sides and the two can be compared bit for bit.
+ * The two modes differ only where a quantity lies within FP32 rounding of a
+ * decision boundary; orc_margins measures how close each (pixel, view) is.
+ * Build with -ffp-contract=off so no multiply-add is fused behind the code's
+ * back; every fused multiply-add below is an explicit fmaf().
  */
 #include <math.h>
 #include <pthread.h>
@@ -63,7 +73,11 @@ typedef struct {
   float z_near;
   int32_t pad;
   const float* disk_ext; /* n x 4 oval extents (+u, -u, +v, -v) in metres, or NULL: round disks */
+  int32_t decisions;     /* ORC_DECIDE_FP32 or ORC_DECIDE_FP64 */
+  int32_t pad2;
 } orc_lightfield;
+
+enum { ORC_DECIDE_FP32 = 0, ORC_DECIDE_FP64 = 1 };
 
 typedef struct {
   double pose[12];
@@ -156,6 +170,7 @@ typedef struct {
   int32_t id;            /* parent triangle id */
   int64_t X[3], Y[3];    /* snapped, oriented so the signed area is positive */
   uint8_t tl[3];         /* edge k (v_k -> v_{k+1}) is top or left */
+  uint8_t culled;        /* zero area or off screen: kept only for orc_margins, covers nothing */
   int32_t bx0, by0, bx1, by1; /* pixel-centre bounding box, clamped to the eye */
   float ia, ib, ic;      /* FP32 inverse-depth plane: 1/z = ia ex + ib ey + ic */
   double n64[3], d64;    /* FP64 plane of the parent: n . X = d */
@@ -169,13 +184,24 @@ typedef struct {
 
 typedef struct {
   float x, y, z;         /* FP32 eye coordinates */
-  int in;                /* z >= z_near */
+  int in;                /* z >= z_near, in the precision of the decision mode */
   int far;               /* snapped value beyond the 2^29 limit */
   int64_t SX, SY;        /* snapped 1/256-pixel coordinates (valid when in && !far) */
-  double X64[3];         /* FP64 eye coordinates */
+  double X64[3];         /* FP64 eye coordinates, through world coordinates */
 } orc_vert;
 
-/* Snap an eye-space point (x, y, z) with z >= z_near to 1/256 pixel. */
+/* FP64 snap of an eye-space point with z >= z_near: llrint(256 (f x / z + c)),
+   round half to even (the default rounding mode). */
+static int orc_snap64(double x, double y, double z, const double* K, int64_t* SX, int64_t* SY) {
+  const double su = 256.0 * (K[0] * x / z + K[2]);
+  const double sv = 256.0 * (K[1] * y / z + K[3]);
+  if (!(fabs(su) < 536870912.0) || !(fabs(sv) < 536870912.0)) return 0;
+  *SX = llrint(su);
+  *SY = llrint(sv);
+  return 1;
+}
+
+/* Snap an eye-space point (x, y, z) with z >= z_near to 1/256 pixel (FP32 reading). */
 static int orc_snap(float x, float y, float z, float fx, float fy, float cx, float cy,
                     int64_t* SX, int64_t* SY) {
   float qx = x / z, qy = y / z;
@@ -207,6 +233,9 @@ int orc_covers(const int64_t X[3], const int64_t Y[3], const uint8_t tl[3], int3
 static int orc_setup_tri(orc_tri* t, int32_t id, const int64_t sx[3], const int64_t sy[3],
                          int W, int H) {
   int64_t X[3] = {sx[0], sx[1], sx[2]}, Y[3] = {sy[0], sy[1], sy[2]};
+  t->id = id;
+  t->culled = 1;
+  for (int k = 0; k < 3; ++k) { t->X[k] = X[k]; t->Y[k] = Y[k]; }
   int64_t A = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
   if (A == 0) return 0;
   if (A < 0) {
@@ -227,9 +256,9 @@ static int orc_setup_tri(orc_tri* t, int32_t id, const int64_t sx[3], const int6
   if (j0 < 0) j0 = 0;
   if (i1 > W - 1) i1 = W - 1;
   if (j1 > H - 1) j1 = H - 1;
-  if (i0 > i1 || j0 > j1) return 0;
-  t->id = id;
   for (int k = 0; k < 3; ++k) { t->X[k] = X[k]; t->Y[k] = Y[k]; }
+  if (i0 > i1 || j0 > j1) return 0;
+  t->culled = 0;
   for (int k = 0; k < 3; ++k) {
     int k1 = (k + 1) % 3;
     t->tl[k] = (uint8_t)orc_top_left(X[k], Y[k], X[k1], Y[k1]);
@@ -238,15 +267,21 @@ static int orc_setup_tri(orc_tri* t, int32_t id, const int64_t sx[3], const int6
   return 1;
 }
 
-/* Build the clipped, snapped, set-up triangle list of one view for one eye. */
+/* Build the clipped, snapped, set-up triangle list of one view for one eye.
+   keep_culled: also keep zero-area and off-screen sub-triangles (flagged
+   culled, covering nothing) for orc_margins. */
 static int orc_build_mesh(const orc_lightfield* lf, const orc_eye* eye, int view,
-                          const orc_viewpose* vp, orc_mesh* mesh, int64_t* stats) {
+                          const orc_viewpose* vp, orc_mesh* mesh, int64_t* stats, int keep_culled) {
   const int G = lf->G, W = eye->W, H = eye->H;
+  const int fp64 = lf->decisions == ORC_DECIDE_FP64;
   const double* K = lf->intr + (size_t)view * 4;
+  const double* Ri = lf->poses + (size_t)view * 12;
+  const double* Re = eye->pose;
   const float* dep = lf->depth + (size_t)view * G * G;
   const float fxe = (float)eye->intr[0], fye = (float)eye->intr[1];
   const float cxe = (float)eye->intr[2], cye = (float)eye->intr[3];
   const float zn = lf->z_near;
+  const double zn64 = (double)lf->z_near;
   orc_vert* V = (orc_vert*)malloc(sizeof(orc_vert) * (size_t)G * G);
   float* af = (float*)malloc(sizeof(float) * G);
   float* bf = (float*)malloc(sizeof(float) * G);
@@ -271,20 +306,29 @@ static int orc_build_mesh(const orc_lightfield* lf, const orc_eye* eye, int view
     for (int j = 0; j < G; ++j) {
       orc_vert* v = &V[k * G + j];
       float z = dep[k * G + j];
-      /* FP32 path: X_cam = z (a_j, b_k, 1); X_eye = Mf X_cam + mf (fused in the fixed order) */
+      /* FP32 reading: X_cam = z (a_j, b_k, 1); X_eye = Mf X_cam + mf (fused in the fixed order) */
       float Xc[3] = {z * af[j], z * bf[k], z};
       float e[3];
       for (int r = 0; r < 3; ++r)
         e[r] = fmaf(vp->Mf[r * 3 + 0], Xc[0], fmaf(vp->Mf[r * 3 + 1], Xc[1], fmaf(vp->Mf[r * 3 + 2], Xc[2], vp->mf[r])));
       v->x = e[0]; v->y = e[1]; v->z = e[2];
-      v->in = (e[2] >= zn);
-      v->far = 0;
-      if (v->in) v->far = !orc_snap(e[0], e[1], e[2], fxe, fye, cxe, cye, &v->SX, &v->SY);
-      /* FP64 path for values */
+      /* FP64 definition: X_world = R_i X_cam + t_i, X_eye = R_eye^T (X_world - t_eye), no fusion */
       double z64 = (double)z;
       double X64[3] = {z64 * a64[j], z64 * b64[k], z64};
-      for (int r = 0; r < 3; ++r)
-        v->X64[r] = vp->M[r * 3 + 0] * X64[0] + vp->M[r * 3 + 1] * X64[1] + vp->M[r * 3 + 2] * X64[2] + vp->m[r];
+      double d[3];
+      for (int r = 0; r < 3; ++r) {
+        double w = Ri[r * 3 + 0] * X64[0] + Ri[r * 3 + 1] * X64[1] + Ri[r * 3 + 2] * X64[2] + Ri[9 + r];
+        d[r] = w - Re[9 + r];
+      }
+      for (int r = 0; r < 3; ++r) v->X64[r] = Re[0 * 3 + r] * d[0] + Re[1 * 3 + r] * d[1] + Re[2 * 3 + r] * d[2];
+      v->far = 0;
+      if (fp64) {
+        v->in = (v->X64[2] >= zn64);
+        if (v->in) v->far = !orc_snap64(v->X64[0], v->X64[1], v->X64[2], eye->intr, &v->SX, &v->SY);
+      } else {
+        v->in = (e[2] >= zn);
+        if (v->in) v->far = !orc_snap(e[0], e[1], e[2], fxe, fye, cxe, cye, &v->SX, &v->SY);
+      }
     }
   int32_t n = 0;
   for (int k = 0; k < G - 1; ++k)
@@ -296,21 +340,24 @@ static int orc_build_mesh(const orc_lightfield* lf, const orc_eye* eye, int view
         else { tv[0] = &V[k * G + j + 1]; tv[1] = &V[(k + 1) * G + j + 1]; tv[2] = &V[(k + 1) * G + j]; }
         int n_in = tv[0]->in + tv[1]->in + tv[2]->in;
         if (n_in == 0) { stats[ORC_STAT_TRI_BEHIND]++; continue; }
-        /* FP32 inverse-depth plane of the parent triangle (original vertex order) */
-        float e1[3] = {tv[1]->x - tv[0]->x, tv[1]->y - tv[0]->y, tv[1]->z - tv[0]->z};
-        float e2[3] = {tv[2]->x - tv[0]->x, tv[2]->y - tv[0]->y, tv[2]->z - tv[0]->z};
-        float nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-        float v0[3] = {tv[0]->x, tv[0]->y, tv[0]->z};
-        float dd = dot3f(nn, v0);
-        float ia = nn[0] / dd, ib = nn[1] / dd, ic = nn[2] / dd;
-        if (dd == 0.0f || !isfinite(ia) || !isfinite(ib) || !isfinite(ic)) { stats[ORC_STAT_TRI_DEGENERATE]++; continue; }
-        /* FP64 plane for values */
+        /* FP64 plane of the parent through its unsnapped vertices: n . X = d */
         double f1[3], f2[3], n64[3];
         for (int r = 0; r < 3; ++r) { f1[r] = tv[1]->X64[r] - tv[0]->X64[r]; f2[r] = tv[2]->X64[r] - tv[0]->X64[r]; }
         n64[0] = f1[1] * f2[2] - f1[2] * f2[1];
         n64[1] = f1[2] * f2[0] - f1[0] * f2[2];
         n64[2] = f1[0] * f2[1] - f1[1] * f2[0];
         double d64 = n64[0] * tv[0]->X64[0] + n64[1] * tv[0]->X64[1] + n64[2] * tv[0]->X64[2];
+        float ia = 0.0f, ib = 0.0f, ic = 0.0f;
+        if (!fp64) {
+          /* FP32 inverse-depth plane of the parent triangle (original vertex order) */
+          float e1[3] = {tv[1]->x - tv[0]->x, tv[1]->y - tv[0]->y, tv[1]->z - tv[0]->z};
+          float e2[3] = {tv[2]->x - tv[0]->x, tv[2]->y - tv[0]->y, tv[2]->z - tv[0]->z};
+          float nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+          float v0[3] = {tv[0]->x, tv[0]->y, tv[0]->z};
+          float dd = dot3f(nn, v0);
+          ia = nn[0] / dd; ib = nn[1] / dd; ic = nn[2] / dd;
+          if (dd == 0.0f || !isfinite(ia) || !isfinite(ib) || !isfinite(ic)) { stats[ORC_STAT_TRI_DEGENERATE]++; continue; }
+        }
         /* Near clip (Sutherland-Hodgman against z >= z_near), then fan. */
         int64_t px[4], py[4];
         int np = 0, far = 0;
@@ -324,10 +371,19 @@ static int orc_build_mesh(const orc_lightfield* lf, const orc_eye* eye, int view
             const orc_vert* b = tv[(q + 1) % 3];
             if (a->in) { px[np] = a->SX; py[np] = a->SY; far |= a->far; ++np; }
             if (a->in != b->in) {
-              float tt = (zn - a->z) / (b->z - a->z);
-              float ix = fmaf(tt, b->x - a->x, a->x);
-              float iy = fmaf(tt, b->y - a->y, a->y);
-              if (!orc_snap(ix, iy, zn, fxe, fye, cxe, cye, &px[np], &py[np])) far = 1;
+              int ok;
+              if (fp64) {
+                double tt = (zn64 - a->X64[2]) / (b->X64[2] - a->X64[2]);
+                double ix = a->X64[0] + tt * (b->X64[0] - a->X64[0]);
+                double iy = a->X64[1] + tt * (b->X64[1] - a->X64[1]);
+                ok = orc_snap64(ix, iy, zn64, eye->intr, &px[np], &py[np]);
+              } else {
+                float tt = (zn - a->z) / (b->z - a->z);
+                float ix = fmaf(tt, b->x - a->x, a->x);
+                float iy = fmaf(tt, b->y - a->y, a->y);
+                ok = orc_snap(ix, iy, zn, fxe, fye, cxe, cye, &px[np], &py[np]);
+              }
+              if (!ok) far = 1;
               ++np;
             }
           }
@@ -336,11 +392,12 @@ static int orc_build_mesh(const orc_lightfield* lf, const orc_eye* eye, int view
         for (int f = 0; f + 2 < np; ++f) {
           int64_t sx[3] = {px[0], px[f + 1], px[f + 2]}, sy[3] = {py[0], py[f + 1], py[f + 2]};
           orc_tri* t = &mesh->tri[n];
-          if (!orc_setup_tri(t, id, sx, sy, W, H)) continue;
+          int kept = orc_setup_tri(t, id, sx, sy, W, H);
+          if (!kept && !keep_culled) continue;
           t->ia = ia; t->ib = ib; t->ic = ic;
           t->n64[0] = n64[0]; t->n64[1] = n64[1]; t->n64[2] = n64[2]; t->d64 = d64;
           ++n;
-          stats[ORC_STAT_TRI_KEPT]++;
+          if (kept) stats[ORC_STAT_TRI_KEPT]++;
         }
       }
   mesh->n_tri = n;
@@ -438,8 +495,31 @@ static double orc_weight_oval(const orc_ray* r, const orc_viewpose* vp) {
   return w > 0.0 ? w : 0.0;
 }
 
-/* FP32 disk membership: |p - c_i|^2 < r_i^2 with sphere-centred coordinates. */
-static int orc_inside(const orc_ray* r, const orc_viewpose* vp) {
+/* Oval rho^2 in FP64 at the FP64 ray's plane hit (t >= 0); 2 when the ray
+   does not meet the plane in front of the eye. */
+static double orc_rho2_oval64(const orc_ray* r, const orc_viewpose* vp) {
+  const double* e = r->e64;
+  const double den = vp->on64[0] * e[0] + vp->on64[1] * e[1] + vp->on64[2] * e[2];
+  if (den == 0.0) return 2.0;
+  const double t = vp->ok64 / den;
+  if (!(t >= 0.0)) return 2.0;
+  const double u = t * (vp->ox64[0] * e[0] + vp->ox64[1] * e[1] + vp->ox64[2] * e[2]) - vp->ou064;
+  const double v = t * (vp->oy64[0] * e[0] + vp->oy64[1] * e[1] + vp->oy64[2] * e[2]) - vp->ov064;
+  const double a = u * (u >= 0.0 ? vp->oru64[0] : vp->oru64[1]);
+  const double b = v * (v >= 0.0 ? vp->orv64[0] : vp->orv64[1]);
+  return a * a + b * b;
+}
+
+/* Disk membership in the decision mode: |p - c_i|^2 < r_i^2 (FP32 with
+   sphere-centred coordinates, or FP64 at the FP64 crossing), or the oval's
+   rho^2 < 1. */
+static int orc_inside(const orc_ray* r, const orc_viewpose* vp, int fp64) {
+  if (fp64) {
+    if (vp->oval) return orc_rho2_oval64(r, vp) < 1.0;
+    if (!r->has_p64) return 0;
+    double dx = r->p64[0] - vp->c64[0], dy = r->p64[1] - vp->c64[1], dz = r->p64[2] - vp->c64[2];
+    return dx * dx + dy * dy + dz * dz < vp->r64 * vp->r64;
+  }
   if (vp->oval) return orc_inside_oval(r, vp);
   if (!r->has_p32) return 0;
   float df[3] = {r->p32[0] - vp->cc[0], r->p32[1] - vp->cc[1], r->p32[2] - vp->cc[2]};
@@ -511,39 +591,58 @@ static void orc_shade_pixel(orc_job* job, int64_t pidx, int64_t* stats) {
   else { i = (int32_t)(pidx % eye->W); j = (int32_t)(pidx / eye->W); }
   orc_ray ray;
   orc_pixel_ray(lf, eye, i, j, &ray);
+  const int fp64 = lf->decisions == ORC_DECIDE_FP64;
+  const double* Re = eye->pose;
   double acc[3] = {0, 0, 0}, wsum = 0.0;
   int32_t slots = 0;
   for (int v = 0; v < lf->n_views; ++v) {
     const orc_viewpose* vp = &job->vps[v];
-    if (!orc_inside(&ray, vp)) continue;
+    if (!orc_inside(&ray, vp, fp64)) continue;
     const orc_mesh* mesh = &job->meshes[v];
     int32_t n_cover = 0, winner = -1, min_id = 0x7fffffff, max_id = -1;
     uint32_t hash = 0;
     float best = 0.0f;
+    double best_z = 0.0;
     const orc_tri* wt = NULL;
     for (int32_t q = 0; q < mesh->n_tri; ++q) {
       const orc_tri* t = &mesh->tri[q];
+      if (t->culled) continue;
       if (i < t->bx0 || i > t->bx1 || j < t->by0 || j > t->by1) continue;
       if (!orc_covers(t->X, t->Y, t->tl, i, j)) continue;
       ++n_cover;
       if (t->id < min_id) min_id = t->id;
       if (t->id > max_id) max_id = t->id;
       hash ^= orc_mix32((uint32_t)t->id);
-      /* Intra-view depth test: largest 1/z wins, ties keep the earlier (lower) id. */
-      float iz = fmaf(t->ia, ray.ex, fmaf(t->ib, ray.ey, t->ic));
-      if (iz > 0.0f && (winner < 0 || iz > best)) { best = iz; winner = t->id; wt = t; }
+      /* Intra-view depth test: the nearest fragment wins, ties to the lower id. */
+      if (fp64) {
+        double ne = t->n64[0] * ray.e64[0] + t->n64[1] * ray.e64[1] + t->n64[2] * ray.e64[2];
+        if (ne == 0.0) continue;
+        double z = t->d64 / ne;
+        if (z > 0.0 && isfinite(z) && (winner < 0 || z < best_z || (z == best_z && t->id < winner))) {
+          best_z = z; winner = t->id; wt = t;
+        }
+      } else {
+        /* FP32 1/z; the list is in id order, so a tie keeps the earlier (lower) id */
+        float iz = fmaf(t->ia, ray.ex, fmaf(t->ib, ray.ey, t->ic));
+        if (iz > 0.0f && (winner < 0 || iz > best)) { best = iz; winner = t->id; wt = t; }
+      }
     }
     stats[ORC_STAT_FRAG_COVER] += n_cover;
     double w = orc_weight(&ray, vp);
     double s = NAN, tt = NAN;
     if (wt) {
       stats[ORC_STAT_FRAG_WIN]++;
-      /* FP64 ray/plane hit of the winner, into source view v (Eq. 2's I_i(s_i, t_i)). */
+      /* FP64 ray/plane hit of the winner, X_eye = z e, taken through world
+         coordinates into source view v (Eq. 2's I_i(s_i, t_i)). */
       double ne = wt->n64[0] * ray.e64[0] + wt->n64[1] * ray.e64[1] + wt->n64[2] * ray.e64[2];
       double z = wt->d64 / ne;
-      double X[3] = {z * ray.e64[0] - vp->m[0], z * ray.e64[1] - vp->m[1], z * ray.e64[2] - vp->m[2]};
+      const double* Ri = lf->poses + (size_t)v * 12;
+      double Xe[3] = {z * ray.e64[0], z * ray.e64[1], z * ray.e64[2]};
+      double X[3];
+      for (int r = 0; r < 3; ++r)
+        X[r] = Re[r * 3 + 0] * Xe[0] + Re[r * 3 + 1] * Xe[1] + Re[r * 3 + 2] * Xe[2] + Re[9 + r] - Ri[9 + r];
       double Xs[3];
-      for (int r = 0; r < 3; ++r) Xs[r] = vp->M[0 * 3 + r] * X[0] + vp->M[1 * 3 + r] * X[1] + vp->M[2 * 3 + r] * X[2];
+      for (int r = 0; r < 3; ++r) Xs[r] = Ri[0 * 3 + r] * X[0] + Ri[1 * 3 + r] * X[1] + Ri[2 * 3 + r] * X[2];
       const double* K = lf->intr + (size_t)v * 4;
       if (Xs[2] > 0.0) {
         s = K[0] * Xs[0] / Xs[2] + K[2];
@@ -688,7 +787,7 @@ static void* orc_sel_worker(void* arg) {
       orc_ray ray;
       orc_pixel_ray(job->lf, job->eye, i, j, &ray);
       for (int v = 0; v < nv; ++v)
-        if (!job->active[v] && orc_inside(&ray, &job->vps[v]))
+        if (!job->active[v] && orc_inside(&ray, &job->vps[v], job->lf->decisions == ORC_DECIDE_FP64))
           __atomic_store_n(&job->active[v], (uint8_t)1, __ATOMIC_RELAXED);
     }
   }
@@ -750,7 +849,7 @@ int orc_render(const orc_lightfield* lf, const orc_eye* eye, const int32_t* pixe
   memset(&job, 0, sizeof(job));
   int rc = 0;
   for (int v = 0; v < lf->n_views; ++v)
-    if (need[v] && !orc_build_mesh(lf, eye, v, &vps[v], &meshes[v], job.stats)) { rc = 1; break; }
+    if (need[v] && !orc_build_mesh(lf, eye, v, &vps[v], &meshes[v], job.stats, 0)) { rc = 1; break; }
   if (rc == 0) {
     job.lf = lf; job.eye = eye; job.vps = vps; job.meshes = meshes; job.pixels = pixels;
     job.n_pixels = n_pixels; job.out = out_rgba; job.frags = frags; job.max_slots = max_slots;
@@ -780,7 +879,7 @@ int orc_pixel_fragments(const orc_lightfield* lf, const orc_eye* eye, int32_t i,
   memset(&mesh, 0, sizeof(mesh));
   int64_t st[ORC_N_STATS];
   memset(st, 0, sizeof(st));
-  if (!orc_build_mesh(lf, eye, view, &vp, &mesh, st)) return -1;
+  if (!orc_build_mesh(lf, eye, view, &vp, &mesh, st, 0)) return -1;
   orc_ray ray;
   orc_pixel_ray(lf, eye, i, j, &ray);
   int n = 0;
@@ -790,9 +889,10 @@ int orc_pixel_fragments(const orc_lightfield* lf, const orc_eye* eye, int32_t i,
     if (!orc_covers(t->X, t->Y, t->tl, i, j)) continue;
     if (n < cap) {
       ids[n] = t->id;
-      inv_z[n] = fmaf(t->ia, ray.ex, fmaf(t->ib, ray.ey, t->ic));
       double ne = t->n64[0] * ray.e64[0] + t->n64[1] * ray.e64[1] + t->n64[2] * ray.e64[2];
       z64[n] = t->d64 / ne;
+      inv_z[n] = lf->decisions == ORC_DECIDE_FP64 ? (float)(ne / t->d64)
+                                                  : fmaf(t->ia, ray.ex, fmaf(t->ib, ray.ey, t->ic));
     }
     ++n;
   }
@@ -815,7 +915,7 @@ int64_t orc_view_triangles(const orc_lightfield* lf, const orc_eye* eye, int32_t
   memset(&mesh, 0, sizeof(mesh));
   int64_t st[ORC_N_STATS];
   memset(st, 0, sizeof(st));
-  if (!orc_build_mesh(lf, eye, view, &vp, &mesh, st)) return -1;
+  if (!orc_build_mesh(lf, eye, view, &vp, &mesh, st, 0)) return -1;
   int64_t n = mesh.n_tri < cap ? mesh.n_tri : cap;
   for (int64_t q = 0; q < n; ++q) {
     const orc_tri* t = &mesh.tri[q];
@@ -848,4 +948,96 @@ int orc_cover_raw(const int64_t sx[3], const int64_t sy[3], int32_t i, int32_t j
     tl[k] = (uint8_t)orc_top_left(X[k], Y[k], X[k1], Y[k1]);
   }
   return orc_covers(X, Y, tl, i, j);
+}
+
+/* Distance in subpixels from point (px, py) to segment a-b (exact inputs, FP64). */
+static double orc_seg_dist(double px, double py, double ax, double ay, double bx, double by) {
+  const double dx = bx - ax, dy = by - ay;
+  const double L2 = dx * dx + dy * dy;
+  double t = L2 > 0.0 ? ((px - ax) * dx + (py - ay) * dy) / L2 : 0.0;
+  if (t < 0.0) t = 0.0;
+  if (t > 1.0) t = 1.0;
+  const double ex = ax + t * dx - px, ey = ay + t * dy - py;
+  return sqrt(ex * ex + ey * ey);
+}
+
+/*
+ * How close each listed (pixel, view) lies to the boundaries of the three
+ * decisions, with the meshes and crossings of the light field's decision mode:
+ *   out[3k+0]  disk: |p - c| / r - 1 for round disks, rho - 1 for ovals
+ *              (negative inside); NaN when the ray has no crossing
+ *   out[3k+1]  coverage: distance in subpixels from the pixel centre to the
+ *              nearest edge of any snapped sub-triangle of the view - zero-area
+ *              ones included - whose snapped box, grown by one pixel, holds
+ *              the centre; +inf when there is none
+ *   out[3k+2]  depth: (z2 - z1) / z1 for the two nearest covering parent
+ *              triangles by FP64 depth (z > 0); +inf with fewer than two
+ * pv lists n triples (i, j, view).  A difference between the two decision
+ * modes at a (pixel, view) is explained when one of these is within the
+ * rounding of FP32.  Returns 0, 1 on allocation failure, 2 on bad arguments.
+ */
+int orc_margins(const orc_lightfield* lf, const orc_eye* eye, const int32_t* pv, int64_t n, double* out) {
+  if (!lf || !eye || (!pv && n > 0) || !out) return 2;
+  orc_viewpose* vps = (orc_viewpose*)calloc((size_t)lf->n_views + 1, sizeof(orc_viewpose));
+  orc_mesh* meshes = (orc_mesh*)calloc((size_t)lf->n_views + 1, sizeof(orc_mesh));
+  if (!vps || !meshes) { free(vps); free(meshes); return 1; }
+  orc_init_viewposes(lf, eye, vps);
+  int rc = 0;
+  int64_t st[ORC_N_STATS];
+  for (int64_t k = 0; k < n && rc == 0; ++k) {
+    const int32_t i = pv[3 * k], j = pv[3 * k + 1], v = pv[3 * k + 2];
+    double* o = out + 3 * k;
+    if (v < 0 || v >= lf->n_views) { rc = 2; break; }
+    orc_ray ray;
+    orc_pixel_ray(lf, eye, i, j, &ray);
+    const orc_viewpose* vp = &vps[v];
+    if (vp->oval) {
+      const double r2 = orc_rho2_oval64(&ray, vp);
+      o[0] = r2 >= 2.0 ? NAN : sqrt(r2) - 1.0;
+    } else if (ray.has_p64) {
+      double dx = ray.p64[0] - vp->c64[0], dy = ray.p64[1] - vp->c64[1], dz = ray.p64[2] - vp->c64[2];
+      o[0] = sqrt(dx * dx + dy * dy + dz * dz) / vp->r64 - 1.0;
+    } else {
+      o[0] = NAN;
+    }
+    if (!meshes[v].built) {
+      memset(st, 0, sizeof(st));
+      if (!orc_build_mesh(lf, eye, v, vp, &meshes[v], st, 1)) { rc = 1; break; }
+    }
+    const orc_mesh* m = &meshes[v];
+    const double cx = 256.0 * i + 128.0, cy = 256.0 * j + 128.0;
+    double edge = INFINITY, z1 = INFINITY, z2 = INFINITY;
+    int32_t id1 = -1;
+    for (int32_t q = 0; q < m->n_tri; ++q) {
+      const orc_tri* t = &m->tri[q];
+      int64_t mnx = t->X[0], mxx = t->X[0], mny = t->Y[0], mxy = t->Y[0];
+      for (int c = 1; c < 3; ++c) {
+        if (t->X[c] < mnx) mnx = t->X[c];
+        if (t->X[c] > mxx) mxx = t->X[c];
+        if (t->Y[c] < mny) mny = t->Y[c];
+        if (t->Y[c] > mxy) mxy = t->Y[c];
+      }
+      if (cx < (double)mnx - 256.0 || cx > (double)mxx + 256.0 || cy < (double)mny - 256.0 || cy > (double)mxy + 256.0)
+        continue;
+      for (int c = 0; c < 3; ++c) {
+        const int c1 = (c + 1) % 3;
+        const double d = orc_seg_dist(cx, cy, (double)t->X[c], (double)t->Y[c], (double)t->X[c1], (double)t->Y[c1]);
+        if (d < edge) edge = d;
+      }
+      if (t->culled || !orc_covers(t->X, t->Y, t->tl, i, j)) continue;
+      const double ne = t->n64[0] * ray.e64[0] + t->n64[1] * ray.e64[1] + t->n64[2] * ray.e64[2];
+      if (ne == 0.0) continue;
+      const double z = t->d64 / ne;
+      if (!(z > 0.0) || !isfinite(z)) continue;
+      if (t->id == id1) continue;  /* the other sub-triangle of the nearest parent */
+      if (z < z1) { z2 = z1; z1 = z; id1 = t->id; }
+      else if (z < z2) { z2 = z; }
+    }
+    o[1] = edge;
+    o[2] = isfinite(z2) ? (z2 - z1) / z1 : INFINITY;
+  }
+  for (int v = 0; v < lf->n_views; ++v) free(meshes[v].tri);
+  free(vps);
+  free(meshes);
+  return rc;
 }

@@ -214,6 +214,67 @@ def test_render_matches_inspect_and_batch(lfmod, tiny):
     r.close()
 
 
+# ---------------------------------------------------------------- against the FP64 definition
+
+# The kernels take the integer decisions in FP32 (the oracle's "fp32" mode, matched
+# bit for bit above).  Against the definition - the oracle's "fp64" mode - a record
+# may differ only where FP32 rounding can move a decision: within DISK_MARGIN of a
+# disk rim (relative), EDGE_MARGIN subpixels of a snapped edge, or DEPTH_MARGIN of a
+# depth tie (relative); and no more than MAX_MISMATCH of the records may differ.
+DISK_MARGIN, EDGE_MARGIN, DEPTH_MARGIN, MAX_MISMATCH = 1e-5, 2.0, 1e-4, 1e-4
+
+
+def _against_definition(r, lf, eye, pixels=None, max_records=32):
+    """GPU records, selection and colour against the FP64-decision oracle; returns
+    (records compared, records that differ)."""
+    got = r.render_inspect(eye, max_records=max_records)
+    ref = oracle.render(lf, eye, pixels=pixels, fragments=True, max_slots=max_records, decisions="fp64")
+    W = eye.width
+    if pixels is None:
+        flat = list(range(W * eye.height))
+        pix = None
+    else:
+        flat = [int(j) * W + int(i) for i, j in pixels]
+        pix = pixels
+    g = _gpu_records(got, flat)
+    o = _ref_records(ref, W, pixels=pix)
+    gk = {(k, rec[0]): rec for k in g for rec in g[k]}
+    ok_ = {(k, rec[0]): rec for k in o for rec in o[k]}
+    keys = set(gk) | set(ok_)
+    diff = sorted(k for k in keys if gk.get(k) != ok_.get(k))
+    assert len(diff) <= MAX_MISMATCH * max(1, len(keys)), (len(diff), len(keys))
+    if diff:
+        pv = np.array([[k % W, k // W, v] for (k, v) in diff], dtype=np.int32)
+        m = oracle.margins(lf, eye, pv)
+        ok = (np.abs(np.nan_to_num(m[:, 0], nan=1.0)) <= DISK_MARGIN) | (m[:, 1] <= EDGE_MARGIN) | \
+            (m[:, 2] <= DEPTH_MARGIN)
+        assert ok.all(), [(d, tuple(x)) for d, x, y in zip(diff, m, ok) if not y][:5]
+    img = got["rgba"].cpu().numpy().astype(np.float64).reshape(-1, 4)[flat]
+    want = ref["rgba"].reshape(-1, 4)
+    both = (img[:, 3] > 0) & (want[:, 3] > 0)
+    if both.any():
+        assert np.max(np.abs(img[both, :3] - want[both, :3])) <= COLOUR_TOL
+    odd = {flat[q] for q in np.nonzero((img[:, 3] > 0) != (want[:, 3] > 0))[0]}
+    assert odd <= {k for (k, _) in diff}
+    sel = oracle.select_views(lf, eye, decisions="fp64")
+    for v in np.nonzero(got["active"] != sel)[0]:
+        pv = np.array([[i, j, v] for j in range(eye.height) for i in range(eye.width)], dtype=np.int32)
+        assert np.nanmin(np.abs(oracle.margins(lf, eye, pv)[:, 0])) <= DISK_MARGIN, v
+    return len(keys), len(diff)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_tiny_frames_against_the_fp64_definition(lfmod, seed):
+    lf = scene.tiny_light_field(seed)
+    r = lfmod.Renderer(0)
+    r.load_views(lf)
+    r.build_meshes(lf)
+    n, nd = _against_definition(r, lf, lf.eyes[0])
+    assert n > 30000
+    print("tiny seed %d: %d of %d records differ from the FP64 definition" % (seed, nd, n))
+    r.close()
+
+
 # ---------------------------------------------------------------- hand-built geometry
 
 
@@ -332,6 +393,9 @@ def test_rig_scale_sampled(lfmod, rig, disks):
         assert np.array_equal(got["active"], sel)
         assert st["active_views"][e] == int(sel.sum())
         assert (got["rgba"].cpu() == out[e].cpu()).all()
+        # the same samples against the FP64 definition
+        n, nd = _against_definition(r, rig, eye, pixels=pix)
+        print("rig %s eye %d: %d of %d sampled records differ from the FP64 definition" % (disks, e, nd, n))
     r.close()
 
 
