@@ -398,6 +398,14 @@ def quality_vs_oracle(r, lf, head, n_pixels):
             "truth": "analytic ray cast of the scene, every valid pixel of both eyes"}
 
 
+def workload_config(args, desc: str, n_heads: int, world: int) -> dict:
+    """The `config` of the default workload's line, the same in both arms."""
+    return {"workload": desc, "texture_storage": args.tex, "mesh_storage": args.mesh, "tile": args.tile,
+            "disks": args.disk, "head_poses": n_heads,
+            "l2": "flushed (256 MiB write) between steps, outside the timed events",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -409,10 +417,11 @@ def run_reference(args):
 
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(11)
-    per_step = 4000 if args.workload == "rig" else 20000
-    # each oracle call also builds the meshes of the views it selects (about
-    # 0.2 s at rig scale), so a long --steps run stops once this much CPU time
-    # is spent, after at least 3 timed steps; the line reports the steps run
+    # a step is the oracle on a bounded random sample of both eyes of one head pose:
+    # large enough that each call's mesh building (about 0.2 s per eye at rig scale)
+    # is a small part of it, as in the measured arm's cpu_baseline; a long --steps
+    # run stops once this much CPU time is spent, after at least 3 timed steps
+    per_step = 200000
     budget_s = 150.0
     times, pixels = [], 0
     t_start = time.perf_counter()
@@ -435,9 +444,11 @@ def run_reference(args):
            "steps": len(times), "steps_requested": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000 * total / len(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": desc, "sample": "%d random pixels per step over both eyes" % per_step},
+           "config": workload_config(args, desc, len(heads), world),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": "%d random pixels per step, %d steps" % (per_step, len(times))},
+                            "sample": "%d random pixels per step over both eyes of one head pose (each oracle "
+                                      "call also builds the meshes of the views it selects), %d steps, %.1f s"
+                                      % (per_step, len(times), total)},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -1163,10 +1174,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "texture_storage": args.tex, "mesh_storage": args.mesh, "tile": args.tile,
-                   "disks": args.disk,
-                   "head_poses": len(heads), "l2": "flushed (256 MiB write) between steps, outside the timed events",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(args, desc, len(heads), world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "raster_kernel", "peak_source": peak_kind + " (HBM copy)",
                      "algorithmic_bytes_per_launch": raster_bytes,

@@ -234,8 +234,11 @@ class PageCache:
         return list(zip(items[:n.value].tolist(), pages[:n.value].tolist()))
 
     def pages(self) -> np.ndarray:
+        """The page of every image after the last frame (-1: not resident)."""
         out = np.zeros(self.n_items, np.int32)
-        self.lib.lf_cache_pages(self.h, out.ctypes.data_as(ctypes.c_void_p))
+        st = self.lib.lf_cache_pages(self.h, out.ctypes.data_as(ctypes.c_void_p))
+        if st != LF_OK:
+            raise LFError(st, "lf_cache_pages failed")
         return out
 
     def close(self):

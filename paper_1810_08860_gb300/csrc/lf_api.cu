@@ -277,8 +277,11 @@ FrameArgs frame_args(lf_ctx* c, const Layout& L) {
 }
 
 // The per-call device work: clear, set up views, set up triangles, raster.
-lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persistent, cudaStream_t s) {
-  const bool t = c->cfg.timing != 0;
+// `timed` = false records no timing events and leaves what lf_get_stats
+// reports (the last lf_render-style call) untouched.
+lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persistent, cudaStream_t s,
+                        bool timed = true) {
+  const bool t = timed && c->cfg.timing != 0;
   LF_CUDA(c, cudaMemsetAsync(a.tile_masks, 0, sizeof(uint32_t) * (size_t)a.total_tiles * a.mask_words, s));
   // the counter block starts at zero each call
   LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, kCounterBlock, s));
@@ -293,7 +296,7 @@ lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persis
   const int blocks = std::min(c->persistent_blocks, std::max(1, a.total_tiles));
   LF_CUDA(c, launch_raster(a, inspect, persistent, blocks, s));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[3], s));
-  c->timed_call = t;
+  if (timed) c->timed_call = t;
   return LF_OK;
 }
 
@@ -893,8 +896,9 @@ extern "C" lf_status lf_render_static(lf_ctx* c, const lf_pose* eye, const lf_in
   a.pool = reinterpret_cast<TriRec*>(base + kOffPool);
   a.pool_capacity = kStaticTris;
   use_counters(a, base + kOffCounters);
-  // enqueue_frame zeroes the masks, counters and flags that must start at zero
-  return enqueue_frame(c, a, false, false, s);
+  // enqueue_frame zeroes the masks, counters and flags that must start at zero;
+  // no timing events, so lf_get_stats keeps reporting the last lf_render call
+  return enqueue_frame(c, a, false, false, s, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -1214,7 +1218,8 @@ lf_status host_enqueue(lf_ctx* c, int slot, int32_t n_eyes, const lf_pose* eyes,
   unsigned char* counters = static_cast<unsigned char*>(H.counters.p) + kCounterBlock * slot;
   use_counters(a, counters);
   if (form == LF_HOST_BATCH && (st = ensure_persistent_blocks(c)) != LF_OK) return st;
-  if ((st = enqueue_frame(c, a, false, form == LF_HOST_BATCH, s)) != LF_OK) return st;
+  // lf_get_stats does not report host-delivered frames: no timing events
+  if ((st = enqueue_frame(c, a, false, form == LF_HOST_BATCH, s, false)) != LF_OK) return st;
   if (refined)
     for (int e = 0; e < n_eyes; ++e)
       if ((st = refine_apply(c, 1, intr[e].width, intr[e].height, target[e], dev[e], s)) != LF_OK) return st;
