@@ -99,7 +99,9 @@ typedef struct {
                                bins get max(4 x this, 32 per screen tile) entries */
   float z_near;             /* eye-space near clip plane in metres [0.1] */
   int32_t pad1;
-  int64_t wait_limit;       /* iteration bound on device spin waits [1<<24] */
+  int64_t wait_limit;       /* bound in nanoseconds (%globaltimer) on each device wait - the
+                               fused refinement's mbarrier waits - after which the kernel
+                               gives up, reports LF_ERR_TIMEOUT and returns [2e9 = 2 s] */
 } lf_config;
 
 /* Counters of the last completed render call on the context. */
@@ -485,6 +487,14 @@ LF_API lf_status lf_cache_frame(lf_cache* cache, int32_t n_wanted, const int32_t
 
 /* The page of every image after the last frame (-1: not resident), n_items entries (host). */
 LF_API lf_status lf_cache_pages(const lf_cache* cache, int32_t* page_of_item);
+
+/* Set lf_config.wait_limit of a live context: each later device wait gives
+ * up after wait_ns nanoseconds (0: the default, 2 s).  A wait that gives up
+ * leaves that call's output incomplete and makes lf_get_refiner return
+ * LF_ERR_TIMEOUT; the context stays usable.  No counterpart in the paper: it
+ * bounds the library's own waits (failure detection without hanging a GPU).
+ * Errors: LF_ERR_INVALID_ARG for a negative value. */
+LF_API lf_status lf_set_wait_limit(lf_ctx* ctx, int64_t wait_ns);
 
 /* Counters of the last render call; synchronises with its stream. */
 LF_API lf_status lf_get_stats(lf_ctx* ctx, lf_stats* out);

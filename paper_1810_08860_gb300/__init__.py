@@ -70,7 +70,7 @@ EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_
            "lf_status_string", "lf_last_error", "lf_load_refiner", "lf_refine_set_kernel", "lf_get_refiner",
            "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined", "lf_render_host",
            "lf_host_wait", "lf_prefilter", "lf_prefilter_cameras", "lf_set_disk_ovals",
-           "lf_cache_create", "lf_cache_destroy", "lf_cache_frame", "lf_cache_pages"]
+           "lf_cache_create", "lf_cache_destroy", "lf_cache_frame", "lf_cache_pages", "lf_set_wait_limit"]
 HOST_FRAMES_IN_FLIGHT = 3
 HOST_FORMS = {"plain": 0, "refined": 1, "batch": 2}
 
@@ -177,6 +177,8 @@ def load_library(path: str = LIB_PATH):
     lib.lf_set_disk_ovals.restype = ctypes.c_int
     lib.lf_prefilter_cameras.argtypes = [vp, i32, i32, vp, i32, vp, vp]
     lib.lf_prefilter_cameras.restype = ctypes.c_int
+    lib.lf_set_wait_limit.argtypes = [vp, i64]
+    lib.lf_set_wait_limit.restype = ctypes.c_int
     lib.lf_status_string.argtypes = [ctypes.c_int]
     lib.lf_status_string.restype = ctypes.c_char_p
     lib.lf_last_error.argtypes = [vp]
@@ -487,6 +489,10 @@ class Renderer:
     def set_refine_kernel(self, kind: str):
         """'fused' (one tcgen05 kernel per tile) or 'layers' (three mma.sync launches)."""
         self._check(self.lib.lf_refine_set_kernel(self.ctx, REFINE_KERNELS[kind]), "lf_refine_set_kernel")
+
+    def set_wait_limit(self, wait_ns: int):
+        """Bound each later device wait to wait_ns nanoseconds (0: the default, 2 s)."""
+        self._check(self.lib.lf_set_wait_limit(self.ctx, int(wait_ns)), "lf_set_wait_limit")
 
     def get_refiner(self) -> dict:
         arrs = {k: np.zeros(REFINE_N_PARAMS, np.float32) for k in ("params", "grad", "m", "v")}

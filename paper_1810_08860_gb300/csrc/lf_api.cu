@@ -44,6 +44,7 @@ namespace {
 constexpr int kRing = 4;
 constexpr int kHostSlots = LF_HOST_FRAMES_IN_FLIGHT;
 constexpr size_t kCounterBlock = 32;  // triangles, error word, work counter, bin offsets, bin entries
+constexpr int64_t kDefaultWaitNs = 2000000000;  // 2 s: far beyond any legitimate wait, even under a profiler
 
 struct Buffer {
   void* p = nullptr;
@@ -413,7 +414,7 @@ void lf_config_default(lf_config* cfg) {
   cfg->max_eyes = 2;
   cfg->tri_capacity = (int64_t)8 << 20;
   cfg->z_near = 0.1f;
-  cfg->wait_limit = (int64_t)1 << 24;
+  cfg->wait_limit = kDefaultWaitNs;
 }
 
 const char* lf_status_string(lf_status s) {
@@ -432,6 +433,13 @@ const char* lf_status_string(lf_status s) {
 
 const char* lf_last_error(const lf_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
 
+lf_status lf_set_wait_limit(lf_ctx* c, int64_t wait_ns) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (wait_ns < 0) return fail(c, LF_ERR_INVALID_ARG, "wait limit must be >= 0");
+  c->cfg.wait_limit = wait_ns ? wait_ns : kDefaultWaitNs;
+  return LF_OK;
+}
+
 lf_status lf_create(int32_t device, const lf_config* cfg, lf_ctx** out) {
   if (!out) return LF_ERR_INVALID_ARG;
   *out = nullptr;
@@ -445,7 +453,7 @@ lf_status lf_create(int32_t device, const lf_config* cfg, lf_ctx** out) {
     if (cfg->wait_limit) c.wait_limit = cfg->wait_limit;
     c.timing = cfg->timing ? 1 : 0;
   }
-  if (!valid_tile(c.tile_w, c.tile_h) || c.max_eyes < 1 || c.max_eyes > 128 || c.tri_capacity < 1 ||
+  if (!valid_tile(c.tile_w, c.tile_h) || c.max_eyes < 1 || c.max_eyes > 128 || c.tri_capacity < 1 || c.wait_limit < 1 ||
       c.tri_capacity > ((int64_t)1 << 31) || !(c.z_near > 0.0f))
     return LF_ERR_INVALID_ARG;
   int n_dev = 0;
@@ -977,7 +985,7 @@ lf_status refine_apply(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float* 
   if (c->rf.kernel == LF_REFINE_FUSED_TC) {
     int32_t* err = reinterpret_cast<int32_t*>(static_cast<char*>(c->rf.scal.p) + 8);
     LF_CUDA(c, launch_refine_fused(n, w, h, in, out, rf_params(c), static_cast<const __nv_bfloat16*>(c->rf.packed.p),
-                                   c->sm_count, err, s));
+                                   c->sm_count, err, (uint64_t)c->cfg.wait_limit, s));
     return LF_OK;
   }
   lf_status st = refine_hidden(c, (int64_t)n * w * h, false);

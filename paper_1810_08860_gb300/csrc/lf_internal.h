@@ -217,6 +217,7 @@ cudaError_t launch_refine_adam(float* p, float* m, float* v, const float* g, int
 cudaError_t launch_refine_pack(const float* params, __nv_bfloat16* w, cudaStream_t s);
 // Fused inference (lf_refine_tc.cu): all three layers per tile, tcgen05 MMAs.
 cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, const float* params,
-                                const __nv_bfloat16* packed, int sm_count, int32_t* error, cudaStream_t s);
+                                const __nv_bfloat16* packed, int sm_count, int32_t* error, uint64_t wait_ns,
+                                cudaStream_t s);
 
 }  // namespace lfk

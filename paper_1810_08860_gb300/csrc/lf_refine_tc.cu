@@ -18,14 +18,16 @@
 // constant 1 in channel 3 that meets b1 in the centre weights, and layers 2
 // and 3 add one MMA of a constant-1 operand against a bias block.
 //
-// Roles: lane 0 of warps 8 and 9 issues the MMAs (even and odd M-tiles) into a
+// Roles: lane 0 of warps 16 and 17 issues the MMAs (even and odd M-tiles) into a
 // ring of 5 TMEM slots of 96 columns, committing each M-tile to the slot's
 // "full" mbarrier; warps 0-15 (four groups of 4 taking M-tiles in turn; warp
 // w reads TMEM lanes 32*(w%4) ..) wait on "full", read the accumulators, release the slot on its
 // "empty" mbarrier, combine the kernel columns, apply ReLU, zero positions outside the image
 // (the next layer's zero padding) and store BF16 rows for the next layer.  A
 // "layer done" mbarrier lets the issuer start a layer once every row of the
-// previous one is in shared memory.  The next tile's FP32 halo streams into a
+// previous one is in shared memory.  At the end each issuing thread commits to
+// its own "drain" mbarrier and waits for it, so no MMA it issued is still
+// running when the CTA deallocates its tensor memory, also after an abort.  The next tile's FP32 halo streams into a
 // staging buffer with cp.async while the current tile computes; the residual
 // add uses FP32 inputs loaded into registers while layer 3 runs.  Every wait
 // is bounded and reports through an error flag instead of hanging.
@@ -59,7 +61,7 @@ constexpr int kWB = kW1B + kW2B + kW3B + kB2Blk + kB3Blk;  // 34,304 bytes
 constexpr int kOnesB = 2 * 128 * 16;         // A operand: channel 0 = 1 on 128 rows
 constexpr int kXsB = kHH * kHW * 16;         // FP32 RGBA halo of the next tile
 constexpr int kSlots = 5, kSlotCols = 96;    // TMEM ring
-constexpr int kNumBars = 2 * kSlots + 1;     // full[5], empty[5], layer_done
+constexpr int kNumBars = 2 * kSlots + 3;     // full[5], empty[5], layer_done, drain[2]
 constexpr int kSmemBytes = 2 * kBufB + kWB + kOnesB + kXsB + kNumBars * 8 + 8;
 constexpr int kStart1 = 32, kTiles1 = 9;     // layer 1 rows [32, 1184): halo rows 1..36
 constexpr int kStart2 = 64, kTiles2 = 8;     // layer 2 rows [64, 1088): halo rows 2..33
@@ -69,8 +71,12 @@ constexpr int kEpiWarps = 16;                // epilogue warps: 4 groups of 4 (o
 constexpr int kEpiGroups = kEpiWarps / 4;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kThreads = kEpiThreads + 64;   // + two MMA warps
-constexpr int kErrIssuerLayer = 2, kErrIssuerSlot = 4, kErrEpilogueFull = 8;  // which wait ran out of time
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: far beyond any legitimate wait, even under a profiler
+// which wait ran out of time (bit 0: the CTA aborted)
+constexpr int kErrIssuerLayer = 2, kErrIssuerSlot = 4, kErrEpilogueFull = 8, kErrDrain = 16;
+// The drain wait is not cut short by a small configured limit: MMAs that are
+// still running when their issuer gives up finish in microseconds, and the
+// tensor memory must not be freed under them.
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -109,24 +115,28 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Wait for the phase of `bar` with the given parity.  Returns 0 once it
-// completed, 2 after kWaitNs of wall time, 1 at once when another warp already
-// gave up.
-__device__ __forceinline__ int wait_phase_status(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  uint64_t t0 = 0;
+// completed, 2 once limit_ns of wall time (%globaltimer) have passed without
+// it, 1 at once when another warp already gave up (abort_flag may be null: the
+// wait then ignores aborts).  The first probe does not block.
+__device__ __forceinline__ int wait_phase_status(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                 uint64_t limit_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  if (done) return 0;
+  const uint64_t t0 = global_ns();
   for (uint32_t it = 0;; ++it) {
-    uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(su32(bar)), "r"(parity)
         : "memory");
     if (done) return 0;
-    if ((it & 255) == 0) {
-      if (*abort_flag) return 1;
-      const uint64_t t = global_ns();
-      if (it == 0) t0 = t;
-      else if (t - t0 > kWaitNs) return 2;
-    }
+    if (abort_flag && (it & 15) == 0 && *abort_flag) return 1;
+    if (global_ns() - t0 >= limit_ns) return 2;
   }
 }
 
@@ -165,6 +175,7 @@ struct FusedArgs {
   float* out;
   const __nv_bfloat16* wtc;  // B operands: L1, L2, L3 blocks
   int32_t* error;            // set to 1 if a wait gave up
+  uint64_t wait_ns;          // bound on each mbarrier wait
 };
 
 __device__ __forceinline__ void tile_origin(const FusedArgs& A, int tile, int& img, int& x0, int& y0) {
@@ -201,7 +212,8 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
   uint64_t* full = reinterpret_cast<uint64_t*>(xs + kXsB);
   uint64_t* empty = full + kSlots;
   uint64_t* layer_done = empty + kSlots;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(layer_done + 1);
+  uint64_t* drain = layer_done + 1;  // one per issuing thread
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
   __shared__ volatile int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool issuer = warp >= kEpiWarps;
@@ -221,6 +233,8 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(empty + b)), "r"(4));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(layer_done)), "r"(kEpiWarps));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(drain + 0)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(drain + 1)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -261,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       bool ok = true;
       auto wait_layer = [&]() {
         if (ok) {
-          const int w = wait_phase_status(layer_done, done_phase, &s_abort);
+          const int w = wait_phase_status(layer_done, done_phase, &s_abort, A.wait_ns);
           if (w == 2) atomicOr(A.error, kErrIssuerLayer);
           ok = w == 0;
         }
@@ -272,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       auto slot_col = [&]() -> uint32_t {
         const int slot = c % kSlots;
         if (ok) {
-          const int w = wait_phase_status(empty + slot, ((uint32_t)(c / kSlots) & 1u) ^ 1u, &s_abort);
+          const int w = wait_phase_status(empty + slot, ((uint32_t)(c / kSlots) & 1u) ^ 1u, &s_abort, A.wait_ns);
           if (w == 2) atomicOr(A.error, kErrIssuerSlot);
           ok = w == 0;
         }
@@ -321,6 +335,12 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
         }
       }
       if (!ok) s_abort = 1;
+      // Drain: the commit arrives once every MMA this thread issued has completed.
+      // Waited for even after an abort (the abort flag does not cut it short), so
+      // the tensor memory is never deallocated under a running MMA.
+      commit(drain + parity);
+      if (wait_phase_status(drain + parity, 0u, nullptr, A.wait_ns > kDrainNs ? A.wait_ns : kDrainNs) == 2)
+        atomicOr(A.error, kErrDrain);
     }
   } else {
     // ---------------------------------------------------------------- epilogue warps
@@ -332,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       const int slot = c % kSlots;
       int got = 1;
       if (lane == 0) {
-        const int w = wait_phase_status(full + slot, (uint32_t)(c / kSlots) & 1u, &s_abort);
+        const int w = wait_phase_status(full + slot, (uint32_t)(c / kSlots) & 1u, &s_abort, A.wait_ns);
         if (w == 2) atomicOr(A.error, kErrEpilogueFull);
         got = w == 0;
       }
@@ -470,7 +490,8 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
 }
 
 cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, const float* params,
-                                const __nv_bfloat16* packed, int sm_count, int32_t* error, cudaStream_t s) {
+                                const __nv_bfloat16* packed, int sm_count, int32_t* error, uint64_t wait_ns,
+                                cudaStream_t s) {
   (void)params;  // the biases are packed with the weights
   cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(refine_fused_kernel), kSmemBytes);
   if (e != cudaSuccess) return e;
@@ -485,6 +506,7 @@ cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in
   a.out = out;
   a.wtc = packed + kPackTc;
   a.error = error;
+  a.wait_ns = wait_ns;
   if (a.n_tiles == 0) return cudaSuccess;
   const int grid = a.n_tiles < sm_count ? a.n_tiles : sm_count;
   refine_fused_kernel<<<grid, kThreads, kSmemBytes, s>>>(a);

@@ -97,6 +97,40 @@ def test_refine_matches_oracle_ragged_multi_tile(lfmod, kernel):
     r.close()
 
 
+def test_fused_wait_that_runs_out_reports_timeout_and_leaves_the_context_usable(lfmod):
+    """Failure detection without hanging the GPU: with a 1 ns wait limit the
+    first mbarrier wait of the fused kernel that is not already complete gives
+    up (typically the MMA warps' wait for the first layer's input, before any
+    MMA is issued).  The kernel must return, lf_get_refiner must report
+    LF_ERR_TIMEOUT, and after restoring the default limit the same context must
+    refine correctly (the issuers drain their MMAs before the tensor memory is
+    freed, also on the abort path)."""
+    import torch
+
+    rng = np.random.default_rng(11)
+    params = _params(lfmod, 5)
+    imgs = [_smooth_image(rng, 90, 120) for _ in range(2)]
+    x = torch.from_numpy(np.stack(imgs)).cuda()
+    r = lfmod.Renderer(0)
+    r.load_refiner(params)
+    r.set_refine_kernel("fused")
+    r.set_wait_limit(1)
+    for _ in range(3):
+        r.refine(x)
+    torch.cuda.synchronize()
+    with pytest.raises(lfmod.LFError) as info:
+        r.get_refiner()
+    assert info.value.status == 5  # LF_ERR_TIMEOUT
+    with pytest.raises(lfmod.LFError):
+        r.set_wait_limit(-1)
+    r.set_wait_limit(0)  # back to the default bound
+    r.load_refiner(params)  # clears the error flag with the Adam state
+    y = r.refine(x).cpu().numpy()
+    _check_forward(list(y), imgs, params)
+    assert r.get_refiner()["step"] == 0
+    r.close()
+
+
 def test_refine_of_an_actual_render(lfmod):
     import torch
 
