@@ -45,7 +45,8 @@ def parse_args():
                         "work so the clock sampler sees the load")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["rig", "rig256", "tiny", "batch", "learned", "refine", "prefilter"],
+    p.add_argument("--workload", choices=["rig", "rig256", "tiny", "batch", "learned", "refine", "prefilter",
+                                          "twolevel"],
                    default="rig")
     p.add_argument("--samples", type=int, default=32, help="prefilter: Monte Carlo samples per pixel (Eq. 5)")
     p.add_argument("--supersample", type=int, default=1, help="prefilter: scale of the Lbar renders")
@@ -60,6 +61,10 @@ def parse_args():
     p.add_argument("--tile", default="16x16")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="bound on the CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the batched, reduced-precision and learned forms")
+    p.add_argument("--pages", type=int, default=256, help="twolevel: device pages of the fine level")
+    p.add_argument("--budget", type=int, default=32, help="twolevel: page uploads per frame")
+    p.add_argument("--save-refiner", default=None, help="learned: write the trained weights and their quality here")
     # learned refinement workload
     p.add_argument("--pairs", type=int, default=4096, help="learned: 256x256 training crops")
     p.add_argument("--train-steps", type=int, default=1500, help="learned: Adam steps (batch 16)")
@@ -1028,6 +1033,18 @@ def run_learned(args):
     e2e_value, e2e_latency = host_e2e(rf, heads, [o.shape for o in outs], flush, stream,
                                       max(20, args.steps // 4), px, world, form="refined")
     st = rf.get_refiner()  # raises if the fused kernel reported a failed wait
+    if args.save_refiner and rank == 0:
+        # the trained weights, with the held-out quality they scored, for the default line's learned form
+        meta = {"vs": "dense reference (method, %d views, %d^2 meshes, 2x2 supersampled)" % (
+                    args.dense_views, args.dense_grid),
+                "eval_eyes": len(eval_eyes), "eye": "1440x1600, 100 deg",
+                "psnr_plain_db": float(np.mean(p_plain)), "psnr_refined_db": float(np.mean(p_ref)),
+                "gain_db": float(np.mean(p_ref) - np.mean(p_plain)),
+                "training": {"pairs": args.pairs, "crop": 256, "steps": args.train_steps, "batch": 16,
+                             "scene": "8 spheres (seed 1), fast light field 1024 Fibonacci views 1024^2 at 120 deg, "
+                                      "64^2 meshes"},
+                "written_by": "python bench.py --workload learned --save-refiner <path>"}
+        np.savez(args.save_refiner, params=st["params"].astype(np.float32), meta=json.dumps(meta))
     total = max_over_ranks(sum(ms_refined))
     value = whole_job_rate(px * args.steps, total, world)
     kern = statistics.mean(ms_kernel)
@@ -1080,6 +1097,299 @@ def run_learned(args):
     if rank == 0:
         print(json.dumps(result), flush=True)
     rf.close()
+    finish_dist(world)
+    return 0
+
+
+REFINER_WEIGHTS = os.path.join(ROOT, "paper_1810_08860_gb300", "refiner_weights.npz")
+
+
+def time_steps(fn, n, flush, stream):
+    """CUDA-event durations (ms) of n calls of fn(k), each after an L2 flush outside the events."""
+    import torch
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for k in range(n):
+        flush.zero_()
+        ev[k][0].record(stream)
+        fn(k)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def form_quality(r, lf, head, n_pixels, seed=5):
+    """Max-abs and PSNR against the FP64 oracle on random pixels of one head pose,
+    and PSNR against the analytic ray cast over every valid pixel."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import scene
+
+    rng = np.random.default_rng(seed)
+    out = r.render(head)
+    torch.cuda.synchronize()
+    d, sq, nt = [], 0.0, 0
+    for eye, img in zip(head, out):
+        g = img.cpu().numpy().astype(np.float64)
+        pix = np.stack([rng.integers(0, eye.width, n_pixels), rng.integers(0, eye.height, n_pixels)], axis=1)
+        ref = oracle.render(lf, eye, pixels=pix)["rgba"]
+        gs = g[pix[:, 1], pix[:, 0]]
+        v = (ref[:, 3] > 0) & (gs[:, 3] > 0)
+        d.append(gs[v, :3] - ref[v, :3])
+        t = scene.truth_image(lf, eye).astype(np.float64) / 255.0
+        ok = g[..., 3] > 0
+        e = g[ok][:, :3] - t[ok][:, :3]
+        sq += float(np.sum(e * e))
+        nt += e.size
+    d = np.concatenate(d)
+    mse = float(np.mean(d * d)) if d.size else 0.0
+    return {"max_abs_vs_fp64_oracle": float(np.abs(d).max()) if d.size else 0.0,
+            "psnr_vs_fp64_oracle_db": 10.0 * math.log10(1.0 / mse) if mse > 0 else float("inf"),
+            "psnr_vs_analytic_truth_db": 10.0 * math.log10(nt / sq) if sq > 0 else float("inf"),
+            "oracle_pixels": int(d.shape[0])}
+
+
+def forms_block(args, lfm, r, lf, heads, plain, flush, stream, local, peak, mean_u):
+    """The batched, reduced-precision and learned forms, each timed on this GPU in
+    this process beside the plain FP32 form (`plain`: its Mpix/s), with its own
+    roofline fraction and quality."""
+    import numpy as np
+    import torch
+
+    px = sum(e.width * e.height for e in heads[0])
+    out_bytes = px * 16
+    steps = 2 * len(heads)
+    forms = {}
+    # ---- precision (pattern 1): the same 8 stereo poses with u8 / BF16 / FP8 textures and FP16 meshes
+    outs = [torch.empty((e.height, e.width, 4), dtype=torch.float32, device="cuda") for e in heads[0]]
+    for fmt, tb in (("u8", 4), ("bf16", 8), ("fp8", 4)):
+        rq = lfm.Renderer(local, timing=True)
+        rq.load_views(lf, tex_format=fmt)
+        rq.build_meshes(lf, mesh_format="f16")
+        for k in range(3):
+            rq.render(heads[k % len(heads)], out=outs)
+        raster = []
+
+        def step(k):
+            rq.render(heads[k % len(heads)], out=outs, stream=stream)
+
+        ms = []
+        for k in range(steps):
+            ms += time_steps(lambda _: step(k), 1, flush, stream)
+            raster.append(rq.stats()["ms_raster"])
+        mean_ms, mean_raster = statistics.mean(ms), statistics.mean(raster)
+        rbytes = mean_u * tb + out_bytes
+        forms["texture_%s_mesh_f16" % fmt] = {
+            "value": px / (mean_ms / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": mean_ms, "steps": steps,
+            "vs_plain": px / (mean_ms / 1000.0) / 1e6 / plain,
+            "roofline": {"bound": "hbm", "frac": rbytes / (mean_raster / 1000.0) / 1e9 / peak,
+                         "algorithmic_bytes_per_launch": rbytes, "ms_per_launch": mean_raster},
+            "quality": form_quality(rq, lf, heads[0], 1000)}
+        rq.close()
+    # ---- batch (pattern 2): 128 eyes of mixed sizes, autotuned, one graph replay per step
+    blf, beyes, bdesc = make_batch(0)
+    rb = lfm.Renderer(local, max_eyes=len(beyes))
+    rb.load_views(blf)
+    rb.build_meshes(blf)
+    bouts = [torch.empty((e.height, e.width, 4), dtype=torch.float32, device="cuda") for e in beyes]
+    bpx = sum(e.width * e.height for e in beyes)
+    tune = rb.tune_batch(beyes, out=bouts, replays=1)
+    buniq = rb.unique_texels(beyes, blf.width, blf.height)
+    for _ in range(2):
+        rb.render_batch(beyes, out=bouts)
+    bms = time_steps(lambda k: rb.render_batch(beyes, out=bouts), 6, flush, stream)
+    assert rb.stats()["error_word"] == 0
+    rt = lfm.Renderer(local, tile=tune["tile"], max_eyes=len(beyes), timing=True)
+    rt.load_views(blf)
+    rt.build_meshes(blf)
+    braster = []
+    for k in range(4):
+        flush.zero_()
+        rt.render_batch(beyes, out=bouts)
+        if k:
+            braster.append(rt.stats()["ms_raster"])
+    rt.close()
+    bq = {}
+    rng = np.random.default_rng(9)
+    dmax = 0.0
+    import oracle
+
+    for k in range(0, len(beyes), 32):  # four eyes of the batch against the oracle
+        e = beyes[k]
+        pix = np.stack([rng.integers(0, e.width, 500), rng.integers(0, e.height, 500)], axis=1)
+        ref = oracle.render(blf, e, pixels=pix)["rgba"]
+        g = bouts[k].cpu().numpy().astype(np.float64)[pix[:, 1], pix[:, 0]]
+        v = (ref[:, 3] > 0) & (g[:, 3] > 0)
+        bq["valid_mismatches"] = bq.get("valid_mismatches", 0) + int(np.sum((ref[:, 3] > 0) != (g[:, 3] > 0)))
+        if v.any():
+            dmax = max(dmax, float(np.abs(g[v, :3] - ref[v, :3]).max()))
+    bq["max_abs_vs_fp64_oracle"] = dmax
+    bmean, brast = statistics.mean(bms), statistics.mean(braster)
+    bbytes = buniq * 16 + bpx * 16
+    forms["batch_128_eyes"] = {
+        "value": bpx / (bmean / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": bmean, "pixels_per_step": bpx,
+        "vs_plain": bpx / (bmean / 1000.0) / 1e6 / plain, "workload": bdesc,
+        "autotune": {"tile": list(tune["tile"]), "blocks_per_sm": tune["blocks_per_sm"]},
+        "roofline": {"bound": "hbm", "frac": bbytes / (brast / 1000.0) / 1e9 / peak,
+                     "algorithmic_bytes_per_launch": bbytes, "ms_per_launch": brast},
+        "quality": bq}
+    rb.close()
+    del bouts
+    # ---- learned (pattern 4): the refined stereo render with the stored trained weights
+    stored = None
+    if os.path.exists(REFINER_WEIGHTS):
+        z = np.load(REFINER_WEIGHTS)
+        r.load_refiner(z["params"].astype(np.float32))
+        stored = json.loads(str(z["meta"]))
+    else:
+        r.load_refiner(lfm.init_refiner_params(1, out_scale=0.1))
+    r.set_refine_kernel("fused")
+    for k in range(3):
+        r.render_refined(heads[k % len(heads)], out=outs)
+    lms = time_steps(lambda k: r.render_refined(heads[k % len(heads)], out=outs), steps, flush, stream)
+    pair = torch.stack([o.clone() for o in outs])
+    refined = torch.empty_like(pair)
+    kms = time_steps(lambda k: r.refine(pair, out=refined), 8, flush, stream)
+    r.get_refiner()  # raises if a wait of the fused kernel gave up
+    tpeak, tkind = measured_tensor_peak()
+    kern = statistics.mean(kms)
+    lmean = statistics.mean(lms)
+    forms["learned_refined"] = {
+        "value": px / (lmean / 1000.0) / 1e6, "unit": UNIT, "ms_per_step": lmean, "steps": steps,
+        "vs_plain": px / (lmean / 1000.0) / 1e6 / plain,
+        "roofline": {"bound": "tensor", "kernel": "refine_fused_kernel", "ms_per_launch": kern,
+                     "frac": REFINE_FLOP_PER_PX * px / (kern / 1000.0) / 1e12 / tpeak,
+                     "peak_source": tkind + " bf16 (burst)"},
+        "quality": stored if stored is not None else "no stored weights: timed with untrained weights"}
+    return forms
+
+
+def run_twolevel(args):
+    """Two-level progressive rendering (Sec. 7.2) at rig scale: the rig light
+    field is the streamed fine level (1,024 views of 1024^2, a page pool of a
+    quarter of them), a 256-view light field of the same scene the resident
+    coarse level.  The head turns 0.6 degrees per frame; each frame renders the
+    stereo pair with what is resident, reads the fine views it selected, lets
+    the host cache (FIFO) admit up to --budget of the missing ones, and copies
+    those images from pinned host memory into their pages."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    init_dist(world)
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_08860_gb300 as lfm
+    import scene
+
+    prims = scene.sphere_scene(1, 24)
+    fine = scene.build_light_field(prims, scene.fibonacci_directions(1024), 1024, 1024, 120.0, 64, name="fine")
+    coarse = scene.build_light_field(prims, scene.fibonacci_directions(256), 1024, 1024, 120.0, 64, name="coarse")
+    import dataclasses
+
+    both = dataclasses.replace(
+        fine, poses=np.concatenate([fine.poses, coarse.poses]), intr=np.concatenate([fine.intr, coarse.intr]),
+        images=np.concatenate([fine.images, coarse.images]), depth=np.concatenate([fine.depth, coarse.depth]),
+        disk_c=np.concatenate([fine.disk_c, coarse.disk_c]), disk_r=np.concatenate([fine.disk_r, coarse.disk_r]),
+        name="two-level")
+    nf, pages = fine.n_views, args.pages
+    r = lfm.Renderer(local, timing=True)
+    r.load_views(both)
+    r.build_meshes(both)
+    r.set_levels(nf, pages)
+    host = torch.from_numpy(fine.images).pin_memory().numpy()  # the streamed images, pinned
+    cache = lfm.PageCache(nf, pages)
+    rng = scene.SplitMix64(8191 + 104729 * rank)
+    centre = rng.in_ball(0.2)
+    yaw0 = rng.uniform(0.0, 2 * math.pi)
+    K = scene.intrinsics_for_fov(1440, 1600, 100.0)
+
+    def head(f):
+        R = scene.look_rotation(scene.yaw_pitch_dir(yaw0 + math.radians(0.6) * f, 0.0))
+        right = R[:, 0]
+        return [scene.Eye(scene.pose_array(R, centre - 0.032 * right), K, 1440, 1600),
+                scene.Eye(scene.pose_array(R, centre + 0.032 * right), K, 1440, 1600)]
+
+    outs = [torch.empty((1600, 1440, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
+    px = 2 * 1440 * 1600
+    stream = torch.cuda.current_stream()
+    rec = []
+    clocks = ClockSampler(local)
+    for f in range(args.warmup + args.steps):
+        if f == args.warmup:
+            torch.cuda.synchronize()
+            barrier_all()
+            clocks.start()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.render(head(f), out=outs, stream=stream)
+        e1.record(stream)
+        wanted = r.levels_wanted()  # waits for the frame
+        st = r.stats()
+        miss = int((cache.pages()[wanted] < 0).sum()) if len(wanted) else 0
+        adm = cache.frame(wanted, args.budget)
+        if adm:
+            r.upload_pages([v for v, _ in adm], [p for _, p in adm], [host[v] for v, _ in adm], stream=stream)
+        t1 = time.perf_counter()
+        if f >= args.warmup:
+            rec.append({"render_ms": e0.elapsed_time(e1), "frame_ms": 1000 * (t1 - t0), "wanted": int(len(wanted)),
+                        "missing": miss, "admitted": len(adm), "drawn": sum(st["active_views"]),
+                        "raster_ms": st["ms_raster"]})
+    clk = clocks.stop()
+    render_ms = max_over_ranks(sum(x["render_ms"] for x in rec)) / len(rec)
+    frame_ms = max_over_ranks(sum(x["frame_ms"] for x in rec)) / len(rec)
+    # quality of the last frame against the analytic truth, beside the fine level alone
+    last = head(args.warmup + args.steps - 1)
+    prog = [o.cpu().numpy().astype(np.float64) for o in r.render(last, out=outs)]
+    rf = lfm.Renderer(local)
+    rf.load_views(fine)
+    rf.build_meshes(fine)
+    full = [o.cpu().numpy().astype(np.float64) for o in rf.render(last)]
+    rf.close()
+
+    def psnr(imgs):
+        sq, n = 0.0, 0
+        for e, g in zip(last, imgs):
+            t = scene.truth_image(fine, e).astype(np.float64) / 255.0
+            v = g[..., 3] > 0
+            d = g[v][:, :3] - t[v][:, :3]
+            sq += float(np.sum(d * d))
+            n += d.size
+        return 10.0 * math.log10(n / sq) if sq > 0 else float("inf")
+
+    valid = [float((g[..., 3] > 0).mean()) for g in prog]
+    result = {
+        "metric": METRIC, "value": whole_job_rate(px, render_ms, world), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": render_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "two-level progressive (Sec. 7.2): fine level 1024 Fibonacci views 1024^2 (120 deg), "
+                               "64^2 meshes, streamed into %d device pages; coarse level 256 views, resident; "
+                               "24 spheres; stereo 2x1440x1600 eyes, head turning 0.6 deg per frame" % pages,
+                   "pages": pages, "budget_per_frame": args.budget, "texture_storage": "f32"},
+        "loop": {"value": whole_job_rate(px, frame_ms, world), "unit": UNIT, "ms_per_frame": frame_ms,
+                 "what": "render + wanted views read back + cache decision + page uploads from pinned host memory"},
+        "frames": {"mean_wanted": statistics.mean(x["wanted"] for x in rec),
+                   "mean_missing": statistics.mean(x["missing"] for x in rec),
+                   "mean_admitted": statistics.mean(x["admitted"] for x in rec),
+                   "mean_drawn_views": statistics.mean(x["drawn"] for x in rec),
+                   "raster_ms": statistics.mean(x["raster_ms"] for x in rec),
+                   "upload_bytes_per_frame": 1024 * 1024 * 4 * statistics.mean(x["admitted"] for x in rec)},
+        "quality": {"psnr_vs_analytic_truth_db": psnr(prog), "fine_level_alone_db": psnr(full),
+                    "valid_fraction": valid},
+        "e2e": {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "see loop (the streamed images are this workload's host traffic)"},
+        "gpu_launches": 7 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    cache.close()
+    r.close()
     finish_dist(world)
     return 0
 
@@ -1194,6 +1504,10 @@ def run_ours(args):
     # sampled pixels of the GPU frame against it
     if rank == 0 and not args.no_cpu_baseline and args.quality_pixels > 0:
         result["quality"] = quality_vs_oracle(r, lf, heads[0], args.quality_pixels)
+    # the other forms of the method beside this plain one (their quality checks also run the oracle)
+    if rank == 0 and not args.no_cpu_baseline and not args.no_forms and args.workload == "rig" and \
+            args.tex == "f32" and args.disk == "round":
+        result["forms"] = forms_block(args, lfm, r, lf, heads, value / world, flush, stream, local, peak, mean_u)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(lf, heads[0][0], args.cpu_seconds)
     if rank == 0:
@@ -1207,7 +1521,7 @@ def main():
     args = parse_args()
     if args.steps is None:
         args.steps = 20 if args.impl == "reference" else {"rig": 2000, "batch": 60, "learned": 1000,
-                                                          "refine": 1000, "prefilter": 10}.get(args.workload, 400)
+                                                          "refine": 1000, "prefilter": 10, "twolevel": 120}.get(args.workload, 400)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
@@ -1218,6 +1532,8 @@ def main():
         return run_prefilter(args)
     if args.workload == "refine":
         return run_refine(args)
+    if args.workload == "twolevel":
+        return run_twolevel(args)
     return run_ours(args)
 
 

@@ -488,6 +488,48 @@ LF_API lf_status lf_cache_frame(lf_cache* cache, int32_t n_wanted, const int32_t
 /* The page of every image after the last frame (-1: not resident), n_items entries (host). */
 LF_API lf_status lf_cache_pages(const lf_cache* cache, int32_t* page_of_item);
 
+/* ------------------------------------------------------------------------
+ * Two-level progressive rendering (Sec. 7.2), with the image cache of Sec.
+ * 4.2.1 on the device.  The loaded views are split into two light fields of
+ * the same scene: views [0, n_fine) the fine level, whose images are streamed
+ * into a fixed pool of device pages, and views [n_fine, n_views) the coarse
+ * level, resident.  Every render call then draws, per eye:
+ *   - each fine view the eye selects (its disk holds some pixel's crossing)
+ *     whose image is resident in a page;
+ *   - each coarse view the eye selects whose disk overlaps (centre distance
+ *     below the sum of the radii, FP64) a fine disk the eye selects whose
+ *     image is missing - the coarse level "in that region";
+ * and Eq. 2 blends whatever mix results.  Residency is per view (the paper
+ * streams 64 x 64 tiles).  lf_cache_* decides which images enter which pages.
+ * ------------------------------------------------------------------------ */
+
+/* Split the loaded views into the two levels (see above) and give the fine
+ * level a pool of n_pages device pages (1 <= n_pages <= n_fine < n_views).
+ * The fine images leave the device; every fine view starts not resident.  The
+ * coarse level keeps its images.  The split holds until lf_load_views.  Waits
+ * for all work on the device.  Errors: LF_ERR_STATE (no views, or levels set
+ * already), LF_ERR_INVALID_ARG, LF_ERR_OOM, LF_ERR_CUDA. */
+LF_API lf_status lf_set_levels(lf_ctx* ctx, int32_t n_fine, int32_t n_pages);
+
+/* Copy n fine images into pages (the admissions of lf_cache_frame): view
+ * views[k] (a fine view) into page pages[k], from host RGBA8 rgba8[k]
+ * (width*height*4 bytes, converted to the context's texture format).  The
+ * previous image of each page is no longer resident.  No view or page twice
+ * in one call.  Waits for `stream` first (renders that read the replaced pages
+ * must run on it or be complete) and returns once the pages and the page table
+ * are on the device.  Errors: LF_ERR_STATE (no levels), LF_ERR_INVALID_ARG,
+ * LF_ERR_CUDA. */
+LF_API lf_status lf_upload_pages(lf_ctx* ctx, int32_t n, const int32_t* views, const int32_t* pages,
+                                 const uint8_t* const* rgba8, void* stream);
+
+/* The fine views that any eye of the last render call selected, in
+ * increasing order - what the next frames want resident (progressive: a frame
+ * draws what is resident and asks for what it missed).  Writes up to cap ids
+ * to views (host) and their number to *n; LF_ERR_CAPACITY when there are more
+ * than cap.  Waits for the last call.  Errors: LF_ERR_STATE (no levels, or no
+ * render yet), LF_ERR_INVALID_ARG. */
+LF_API lf_status lf_levels_wanted(lf_ctx* ctx, int32_t cap, int32_t* views, int32_t* n);
+
 /* Set lf_config.wait_limit of a live context: each later device wait gives
  * up after wait_ns nanoseconds (0: the default, 2 s).  A wait that gives up
  * leaves that call's output incomplete and makes lf_get_refiner return

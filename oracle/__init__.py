@@ -90,6 +90,8 @@ def _load():
         lib.orc_cover_raw.restype = ctypes.c_int
         lib.orc_margins.argtypes = [vp, vp, vp, ctypes.c_int64, vp]
         lib.orc_margins.restype = ctypes.c_int
+        lib.orc_set_mutation.argtypes = [ctypes.c_int]
+        lib.orc_set_mutation.restype = None
         lib.orc_mix32.argtypes = [ctypes.c_uint32]
         lib.orc_mix32.restype = ctypes.c_uint32
         _lib = lib
@@ -266,3 +268,13 @@ def margins(lf, eye, pixel_views, z_near: float = 0.1, decisions: str = "fp64") 
     if rc != 0:
         raise RuntimeError("orc_margins failed with code %d" % rc)
     return out
+
+
+MUTATIONS = {"fill_rule_flipped": 1, "eye_rotation_transposed": 2, "depth_test_reversed": 3,
+             "quadratic_kernel": 4, "smaller_sphere_root": 5, "no_half_texel_shift": 6, "cx_cy_swapped": 7}
+
+
+def set_mutation(name=None):
+    """Plant one of the MUTATIONS in the oracle (None: the correct oracle).
+    For the pin tests only: they show that each plausible slip fails a pin."""
+    _load().orc_set_mutation(0 if name is None else MUTATIONS[name])

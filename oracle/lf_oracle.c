@@ -106,6 +106,16 @@ enum { ORC_STAT_TRI_KEPT = 0, ORC_STAT_TRI_CLIPPED, ORC_STAT_TRI_FAR, ORC_STAT_T
 
 /* ------------------------------------------------------------------ helpers */
 
+/* Planted mistakes for the pin tests (0: none).  Each code breaks one step of
+   the method the way a plausible slip would, so the tests can show that some
+   pin catches it:
+     1 fill rule flipped           2 eye rotation transposed
+     3 depth test reversed         4 quadratic disk kernel
+     5 smaller sphere root         6 bilinear half-texel shift dropped
+     7 cx and cy swapped in the eye projection */
+static int g_mutation = 0;
+void orc_set_mutation(int m) { g_mutation = m; }
+
 uint32_t orc_mix32(uint32_t x) {
   /* murmur3 32-bit finaliser */
   x ^= x >> 16; x *= 0x85EBCA6Bu;
@@ -123,6 +133,15 @@ static int64_t floor_div(int64_t a, int64_t b) { /* b > 0 */
   int64_t q = a / b;
   if ((a % b) != 0 && a < 0) --q;
   return q;
+}
+
+/* The eye as the entry points see it: with mutation 2 its rotation transposed. */
+static const orc_eye* orc_eye_used(const orc_eye* eye, orc_eye* tmp) {
+  if (g_mutation != 2 || !eye) return eye;
+  *tmp = *eye;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) tmp->pose[r * 3 + c] = eye->pose[c * 3 + r];
+  return tmp;
 }
 
 /* ------------------------------------------------------------------ per-eye, per-view setup */
@@ -215,7 +234,8 @@ static int orc_snap(float x, float y, float z, float fx, float fy, float cx, flo
 
 /* Top-left rule in a y-down screen for a positively oriented triangle. */
 static int orc_top_left(int64_t ax, int64_t ay, int64_t bx, int64_t by) {
-  return (ay == by && bx > ax) || (by < ay);
+  const int tl = (ay == by && bx > ax) || (by < ay);
+  return g_mutation == 1 ? !tl : tl;
 }
 
 /* Pixel-centre coverage of an oriented snapped triangle (exact int64). */
@@ -279,7 +299,12 @@ static int orc_build_mesh(const orc_lightfield* lf, const orc_eye* eye, int view
   const double* Re = eye->pose;
   const float* dep = lf->depth + (size_t)view * G * G;
   const float fxe = (float)eye->intr[0], fye = (float)eye->intr[1];
-  const float cxe = (float)eye->intr[2], cye = (float)eye->intr[3];
+  float cxe = (float)eye->intr[2], cye = (float)eye->intr[3];
+  double Ksnap[4] = {eye->intr[0], eye->intr[1], eye->intr[2], eye->intr[3]};
+  if (g_mutation == 7) {
+    const float tf = cxe; cxe = cye; cye = tf;
+    Ksnap[2] = eye->intr[3]; Ksnap[3] = eye->intr[2];
+  }
   const float zn = lf->z_near;
   const double zn64 = (double)lf->z_near;
   orc_vert* V = (orc_vert*)malloc(sizeof(orc_vert) * (size_t)G * G);
@@ -324,7 +349,7 @@ static int orc_build_mesh(const orc_lightfield* lf, const orc_eye* eye, int view
       v->far = 0;
       if (fp64) {
         v->in = (v->X64[2] >= zn64);
-        if (v->in) v->far = !orc_snap64(v->X64[0], v->X64[1], v->X64[2], eye->intr, &v->SX, &v->SY);
+        if (v->in) v->far = !orc_snap64(v->X64[0], v->X64[1], v->X64[2], Ksnap, &v->SX, &v->SY);
       } else {
         v->in = (e[2] >= zn);
         if (v->in) v->far = !orc_snap(e[0], e[1], e[2], fxe, fye, cxe, cye, &v->SX, &v->SY);
@@ -376,7 +401,7 @@ static int orc_build_mesh(const orc_lightfield* lf, const orc_eye* eye, int view
                 double tt = (zn64 - a->X64[2]) / (b->X64[2] - a->X64[2]);
                 double ix = a->X64[0] + tt * (b->X64[0] - a->X64[0]);
                 double iy = a->X64[1] + tt * (b->X64[1] - a->X64[1]);
-                ok = orc_snap64(ix, iy, zn64, eye->intr, &px[np], &py[np]);
+                ok = orc_snap64(ix, iy, zn64, Ksnap, &px[np], &py[np]);
               } else {
                 float tt = (zn - a->z) / (b->z - a->z);
                 float ix = fmaf(tt, b->x - a->x, a->x);
@@ -435,7 +460,7 @@ static void orc_pixel_ray(const orc_lightfield* lf, const orc_eye* eye, int32_t 
   float disc = b * b - a * c;
   r->has_p32 = 0;
   if (disc >= 0.0f) {
-    float t = (sqrtf(disc) - b) / a;
+    float t = g_mutation == 5 ? (-sqrtf(disc) - b) / a : (sqrtf(disc) - b) / a;
     if (t >= 0.0f) {
       r->has_p32 = 1;
       for (int k = 0; k < 3; ++k) r->p32[k] = fmaf(t, d[k], o[k]);
@@ -456,7 +481,7 @@ static void orc_pixel_ray(const orc_lightfield* lf, const orc_eye* eye, int32_t 
   double D = B * B - A * C;
   r->has_p64 = 0;
   if (D >= 0.0) {
-    double t = (-B + sqrt(D)) / A;
+    double t = g_mutation == 5 ? (-B - sqrt(D)) / A : (-B + sqrt(D)) / A;
     if (t >= 0.0) {
       r->has_p64 = 1;
       for (int k = 0; k < 3; ++k) r->p64[k] = Re[9 + k] + t * dw[k];
@@ -531,7 +556,8 @@ static double orc_weight(const orc_ray* r, const orc_viewpose* vp) {
   if (vp->oval) return orc_weight_oval(r, vp);
   if (!r->has_p64) return 0.0;
   double dx = r->p64[0] - vp->c64[0], dy = r->p64[1] - vp->c64[1], dz = r->p64[2] - vp->c64[2];
-  double w = 1.0 - sqrt(dx * dx + dy * dy + dz * dz) / vp->r64;
+  double w = g_mutation == 4 ? 1.0 - (dx * dx + dy * dy + dz * dz) / (vp->r64 * vp->r64)
+                             : 1.0 - sqrt(dx * dx + dy * dy + dz * dz) / vp->r64;
   return w > 0.0 ? w : 0.0;
 }
 
@@ -539,6 +565,7 @@ static double orc_weight(const orc_ray* r, const orc_viewpose* vp) {
 static void orc_bilinear(const orc_lightfield* lf, int view, double s, double t, double rgb[3],
                          int32_t ti[4], int32_t tj[4]) {
   double u = s - 0.5, v = t - 0.5;
+  if (g_mutation == 6) { u = s; v = t; }
   if (u < -1.0) u = -1.0;
   if (u > (double)lf->W) u = (double)lf->W;
   if (v < -1.0) v = -1.0;
@@ -618,13 +645,15 @@ static void orc_shade_pixel(orc_job* job, int64_t pidx, int64_t* stats) {
         double ne = t->n64[0] * ray.e64[0] + t->n64[1] * ray.e64[1] + t->n64[2] * ray.e64[2];
         if (ne == 0.0) continue;
         double z = t->d64 / ne;
-        if (z > 0.0 && isfinite(z) && (winner < 0 || z < best_z || (z == best_z && t->id < winner))) {
+        const int nearer = g_mutation == 3 ? z > best_z : z < best_z;
+        if (z > 0.0 && isfinite(z) && (winner < 0 || nearer || (z == best_z && t->id < winner))) {
           best_z = z; winner = t->id; wt = t;
         }
       } else {
         /* FP32 1/z; the list is in id order, so a tie keeps the earlier (lower) id */
         float iz = fmaf(t->ia, ray.ex, fmaf(t->ib, ray.ey, t->ic));
-        if (iz > 0.0f && (winner < 0 || iz > best)) { best = iz; winner = t->id; wt = t; }
+        const int nearer = g_mutation == 3 ? iz < best : iz > best;
+        if (iz > 0.0f && (winner < 0 || nearer)) { best = iz; winner = t->id; wt = t; }
       }
     }
     stats[ORC_STAT_FRAG_COVER] += n_cover;
@@ -801,6 +830,8 @@ static void* orc_sel_worker(void* arg) {
  */
 int orc_select_views(const orc_lightfield* lf, const orc_eye* eye, const int32_t* pixels,
                      int64_t n_pixels, uint8_t* active, int n_threads) {
+  orc_eye eye_tmp;
+  eye = orc_eye_used(eye, &eye_tmp);
   orc_viewpose* vps = (orc_viewpose*)calloc((size_t)lf->n_views, sizeof(orc_viewpose));
   if (!vps) return 1;
   orc_init_viewposes(lf, eye, vps);
@@ -835,6 +866,8 @@ int orc_select_views(const orc_lightfield* lf, const orc_eye* eye, const int32_t
 int orc_render(const orc_lightfield* lf, const orc_eye* eye, const int32_t* pixels, int64_t n_pixels,
                double* out_rgba, orc_frag* frags, int32_t max_slots, int32_t* n_slots,
                uint64_t* texel_bits, int64_t* stats, int n_threads) {
+  orc_eye eye_tmp;
+  eye = orc_eye_used(eye, &eye_tmp);
   if (!lf || !eye || !out_rgba || lf->n_views < 0 || lf->G < 2 || eye->W <= 0 || eye->H <= 0) return 2;
   if (!pixels) n_pixels = (int64_t)eye->W * eye->H;
   orc_viewpose* vps = (orc_viewpose*)calloc((size_t)lf->n_views + 1, sizeof(orc_viewpose));
@@ -871,6 +904,8 @@ int orc_render(const orc_lightfield* lf, const orc_eye* eye, const int32_t* pixe
  */
 int orc_pixel_fragments(const orc_lightfield* lf, const orc_eye* eye, int32_t i, int32_t j, int32_t view,
                         int32_t* ids, float* inv_z, double* z64, int32_t cap) {
+  orc_eye eye_tmp;
+  eye = orc_eye_used(eye, &eye_tmp);
   if (view < 0 || view >= lf->n_views) return -1;
   orc_viewpose vp;
   memset(&vp, 0, sizeof(vp));
@@ -907,6 +942,8 @@ int orc_pixel_fragments(const orc_lightfield* lf, const orc_eye* eye, int32_t i,
  */
 int64_t orc_view_triangles(const orc_lightfield* lf, const orc_eye* eye, int32_t view,
                            int64_t* rows, int64_t cap, int64_t* stats) {
+  orc_eye eye_tmp;
+  eye = orc_eye_used(eye, &eye_tmp);
   if (view < 0 || view >= lf->n_views) return -1;
   orc_viewpose vp;
   memset(&vp, 0, sizeof(vp));
@@ -977,6 +1014,8 @@ static double orc_seg_dist(double px, double py, double ax, double ay, double bx
  * rounding of FP32.  Returns 0, 1 on allocation failure, 2 on bad arguments.
  */
 int orc_margins(const orc_lightfield* lf, const orc_eye* eye, const int32_t* pv, int64_t n, double* out) {
+  orc_eye eye_tmp;
+  eye = orc_eye_used(eye, &eye_tmp);
   if (!lf || !eye || (!pv && n > 0) || !out) return 2;
   orc_viewpose* vps = (orc_viewpose*)calloc((size_t)lf->n_views + 1, sizeof(orc_viewpose));
   orc_mesh* meshes = (orc_mesh*)calloc((size_t)lf->n_views + 1, sizeof(orc_mesh));

@@ -38,6 +38,15 @@ Readings where the paper leaves a choice (each stated once here):
   (s, t) with the grid triangle holding (s, t) (the cell's diagonal runs from
   (j+1, k) to (j, k+1), as in the renderer).
 - Output: (num / den, 1) where den > 0, else (0, 0, 0, 0); no clamping.
+- Two ways to take Lbar (`lbar=`):
+    "render"  the reading above: one pinhole render per (view, sample), read
+              bilinearly at each mesh point's projection (the fast renderer's
+              design; the resampling is its one approximation);
+    "ray"     the definition: each ray from o_j through X(s, t) is its own
+              query - a 1 x 1 eye at o_j with view i's rotation whose pixel
+              centre ray passes exactly through X, at 8 x the view's focal
+              length (the method's 1/256-pixel raster grid then lies 1/2048 of
+              a source pixel apart) - weighted by that query's alpha.
 """
 from __future__ import annotations
 
@@ -130,8 +139,30 @@ def _bilinear_premultiplied(img, u, v):
             + (1 - al)[..., None] * be[..., None] * pm[jb, ia] + al[..., None] * be[..., None] * pm[jb, ib])
 
 
+def _per_ray(target, dense, view: int, smp, X):
+    """(alpha rgb, alpha) of the method's ray query for each ray from the
+    sample's aperture point through the camera-frame points X (K x 3)."""
+    import oracle
+    import scene
+
+    Rv, tv = _view_R_t(target, view)
+    ow = aperture_point(target, view, smp[0], smp[1])
+    o = Rv.T @ (ow - tv)
+    f = 8.0 * float(target.intr[view][0])
+    out = np.zeros((X.shape[0], 4))
+    for q in range(X.shape[0]):
+        x = X[q] - o
+        if not x[2] > 0.0:
+            continue
+        K = np.array([f, f, 0.5 - f * x[0] / x[2], 0.5 - f * x[1] / x[2]])
+        v = oracle.render(dense, scene.Eye(scene.pose_array(Rv, ow), K, 1, 1), threads=1)["rgba"].reshape(4)
+        out[q, :3] = v[:3] * v[3]
+        out[q, 3] = v[3]
+    return out
+
+
 def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=None, threads=None,
-              renders=None, details: bool = False, sparse: bool = False):
+              renders=None, details: bool = False, sparse: bool = False, lbar: str = "render"):
     """Eq. 5 for view `view` of the real-time model `target`, with Lbar from
     the light field `dense`.  samples: J x 4 (a, b, ds, dt).  pixels: K x 2
     integer (i, j), or None for the whole image.  Returns H x W x 4 (or K x 4)
@@ -148,7 +179,9 @@ def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=No
     else:
         pix = np.asarray(pixels, dtype=np.int64).reshape(-1, 2)
     Rv, tv = _view_R_t(target, view)
-    if renders is None and not sparse:
+    if lbar not in ("render", "ray"):
+        raise ValueError("lbar must be 'render' or 'ray'")
+    if renders is None and not sparse and lbar == "render":
         renders = virtual_renders(target, dense, view, samples, supersample, threads)
     Ks, Ws, Hs = virtual_intrinsics(target, view, supersample)
     num = np.zeros((pix.shape[0], 3))
@@ -158,6 +191,12 @@ def prefilter(target, dense, view: int, samples, supersample: int = 1, pixels=No
         a, b, ds, dt = smp
         w = sample_weight(smp)
         X = mesh_points(target, view, pix[:, 0] + 0.5 + ds, pix[:, 1] + 0.5 + dt)
+        if lbar == "ray":
+            val = _per_ray(target, dense, view, smp, X)
+            num += w * val[:, :3]
+            den += w * val[:, 3]
+            den_abs += abs(w) * val[:, 3]
+            continue
         o = Rv.T @ (aperture_point(target, view, a, b) - tv)   # the sample's origin in view i's frame
         x = X - o
         qx = Ks[0] * x[:, 0] / x[:, 2] + Ks[2]

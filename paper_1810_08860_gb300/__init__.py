@@ -70,7 +70,8 @@ EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_
            "lf_status_string", "lf_last_error", "lf_load_refiner", "lf_refine_set_kernel", "lf_get_refiner",
            "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined", "lf_render_host",
            "lf_host_wait", "lf_prefilter", "lf_prefilter_cameras", "lf_set_disk_ovals",
-           "lf_cache_create", "lf_cache_destroy", "lf_cache_frame", "lf_cache_pages", "lf_set_wait_limit"]
+           "lf_cache_create", "lf_cache_destroy", "lf_cache_frame", "lf_cache_pages", "lf_set_wait_limit",
+           "lf_set_levels", "lf_upload_pages", "lf_levels_wanted"]
 HOST_FRAMES_IN_FLIGHT = 3
 HOST_FORMS = {"plain": 0, "refined": 1, "batch": 2}
 
@@ -177,6 +178,12 @@ def load_library(path: str = LIB_PATH):
     lib.lf_set_disk_ovals.restype = ctypes.c_int
     lib.lf_prefilter_cameras.argtypes = [vp, i32, i32, vp, i32, vp, vp]
     lib.lf_prefilter_cameras.restype = ctypes.c_int
+    lib.lf_set_levels.argtypes = [vp, i32, i32]
+    lib.lf_set_levels.restype = ctypes.c_int
+    lib.lf_upload_pages.argtypes = [vp, i32, vp, vp, vp, vp]
+    lib.lf_upload_pages.restype = ctypes.c_int
+    lib.lf_levels_wanted.argtypes = [vp, i32, vp, ctypes.POINTER(i32)]
+    lib.lf_levels_wanted.restype = ctypes.c_int
     lib.lf_set_wait_limit.argtypes = [vp, i64]
     lib.lf_set_wait_limit.restype = ctypes.c_int
     lib.lf_status_string.argtypes = [ctypes.c_int]
@@ -307,6 +314,7 @@ class Renderer:
         self._check(self.lib.lf_load_views(self.ctx, n, poses, intr, ptrs, dc.ctypes.data, dr.ctypes.data, sc,
                                            float(lf.sphere_r), TEX_FORMATS[tex_format]), "lf_load_views")
         self.n_views = n
+        self.n_fine = 0
         self._src_hw = (lf.height, lf.width)
         if getattr(lf, "disk_ext", None) is not None:
             self.set_disk_ovals(lf.disk_ext)
@@ -489,6 +497,32 @@ class Renderer:
     def set_refine_kernel(self, kind: str):
         """'fused' (one tcgen05 kernel per tile) or 'layers' (three mma.sync launches)."""
         self._check(self.lib.lf_refine_set_kernel(self.ctx, REFINE_KERNELS[kind]), "lf_refine_set_kernel")
+
+    def set_levels(self, n_fine: int, n_pages: int):
+        """Views [0, n_fine) become the streamed fine level with n_pages device pages (Sec. 7.2)."""
+        self._check(self.lib.lf_set_levels(self.ctx, int(n_fine), int(n_pages)), "lf_set_levels")
+        self.n_fine = int(n_fine)
+
+    def upload_pages(self, views, pages, images, stream=None):
+        """Copy fine images (host uint8 H x W x 4 each) into pages; images[k] goes with views[k]."""
+        v = np.ascontiguousarray(np.asarray(views, dtype=np.int32).ravel())
+        p = np.ascontiguousarray(np.asarray(pages, dtype=np.int32).ravel())
+        imgs = [np.ascontiguousarray(im, dtype=np.uint8) for im in images]
+        if not (len(imgs) == v.size == p.size):
+            raise ValueError("one image per (view, page)")
+        ptrs = (ctypes.c_void_p * max(1, len(imgs)))(*[im.ctypes.data for im in imgs])
+        self._check(self.lib.lf_upload_pages(self.ctx, int(v.size), v.ctypes.data_as(ctypes.c_void_p),
+                                             p.ctypes.data_as(ctypes.c_void_p), ptrs, _stream_handle(stream)),
+                    "lf_upload_pages")
+
+    def levels_wanted(self) -> np.ndarray:
+        """Fine views the last render call selected (what the next frames want resident)."""
+        cap = getattr(self, "n_fine", 0) or self.n_views
+        out = np.zeros(max(1, cap), np.int32)
+        n = ctypes.c_int32(0)
+        self._check(self.lib.lf_levels_wanted(self.ctx, int(cap), out.ctypes.data_as(ctypes.c_void_p),
+                                              ctypes.byref(n)), "lf_levels_wanted")
+        return out[:n.value].copy()
 
     def set_wait_limit(self, wait_ns: int):
         """Bound each later device wait to wait_ns nanoseconds (0: the default, 2 s)."""

@@ -113,6 +113,14 @@ struct lf_ctx {
   struct Prefilter {
     Buffer renders, params, err;
   } pf;
+  // two-level progressive rendering (lf_set_levels): views [0, n_fine) are the
+  // streamed fine level, whose images live in pool pages; the rest the coarse level
+  struct Levels {
+    int32_t n_fine = 0, n_pages = 0;
+    Buffer pool, table, page_of_view, overlap_off, overlap_ids, enable, visible, stage;
+    std::vector<int32_t> view_page, page_view;  // host mirrors of the page table
+    std::vector<const void*> table_host;        // host mirror of the texture table
+  } lv;
 };
 
 namespace {
@@ -212,6 +220,10 @@ lf_status ensure_scratch(lf_ctx* c, int32_t n_eyes, int32_t total_tiles) {
   LF_CUDA(c, ensure(c->pool, sizeof(TriRec) * (size_t)cap));
   LF_CUDA(c, ensure(c->bin_offsets, sizeof(int32_t) * (size_t)bin_offsets_capacity(c, total_tiles)));
   LF_CUDA(c, ensure(c->bin_entries, sizeof(int32_t) * (size_t)bin_entries_capacity(c, total_tiles)));
+  if (c->lv.n_fine > 0) {
+    LF_CUDA(c, ensure(c->lv.enable, sizeof(uint32_t) * (size_t)n_eyes * mask_words(c)));
+    LF_CUDA(c, ensure(c->lv.visible, (size_t)n_eyes * c->n_views));
+  }
   return LF_OK;
 }
 
@@ -274,6 +286,15 @@ FrameArgs frame_args(lf_ctx* c, const Layout& L) {
   a.total_tiles = L.total_tiles;
   a.tile_w = c->cfg.tile_w;
   a.tile_h = c->cfg.tile_h;
+  if (c->lv.n_fine > 0) {
+    a.tex_table = static_cast<const void* const*>(c->lv.table.p);
+    a.enable_bits = static_cast<uint32_t*>(c->lv.enable.p);
+    a.visible = static_cast<uint8_t*>(c->lv.visible.p);
+    a.page_of_view = static_cast<const int32_t*>(c->lv.page_of_view.p);
+    a.overlap_off = static_cast<const int32_t*>(c->lv.overlap_off.p);
+    a.overlap_ids = static_cast<const int32_t*>(c->lv.overlap_ids.p);
+    a.n_fine = c->lv.n_fine;
+  }
   return a;
 }
 
@@ -287,8 +308,17 @@ lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persis
   // the counter block starts at zero each call
   LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, kCounterBlock, s));
   LF_CUDA(c, cudaMemsetAsync(a.active, 0, (size_t)a.n_eyes * a.n_views, s));
+  if (a.n_fine > 0) {
+    LF_CUDA(c, cudaMemsetAsync(a.visible, 0, (size_t)a.n_eyes * a.n_views, s));
+    LF_CUDA(c, cudaMemsetAsync(a.enable_bits, 0, sizeof(uint32_t) * (size_t)a.n_eyes * a.mask_words, s));
+  }
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[0], s));
   LF_CUDA(c, launch_view_setup(a, s));
+  if (a.n_fine > 0) {
+    // two-level frame (Sec. 7.2): which views each eye selects, then which it draws
+    LF_CUDA(c, launch_select(a, s));
+    LF_CUDA(c, launch_drawn(a, s));
+  }
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[1], s));
   LF_CUDA(c, launch_tri_setup(a, s));
   LF_CUDA(c, launch_bin(a, s));
@@ -503,6 +533,9 @@ void lf_destroy(lf_ctx* ctx) {
   }
   release(ctx->hp.counters);
   for (Buffer* b : {&ctx->pf.renders, &ctx->pf.params, &ctx->pf.err}) release(*b);
+  for (Buffer* b : {&ctx->lv.pool, &ctx->lv.table, &ctx->lv.page_of_view, &ctx->lv.overlap_off, &ctx->lv.overlap_ids,
+                    &ctx->lv.enable, &ctx->lv.visible, &ctx->lv.stage})
+    release(*b);
   if (ctx->hp.err) cudaFreeHost(ctx->hp.err);
   if (ctx->hp.copy) cudaStreamDestroy(ctx->hp.copy);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -544,6 +577,14 @@ lf_status lf_load_views(lf_ctx* c, int32_t n_views, const lf_pose* poses, const 
   c->n_views = 0;
   c->G = 0;
   release(c->depth); release(c->tab_a); release(c->tab_b);
+  // one level again
+  for (Buffer* b : {&c->lv.pool, &c->lv.table, &c->lv.page_of_view, &c->lv.overlap_off, &c->lv.overlap_ids,
+                    &c->lv.enable, &c->lv.visible, &c->lv.stage})
+    release(*b);
+  c->lv.n_fine = c->lv.n_pages = 0;
+  c->lv.view_page.clear();
+  c->lv.page_view.clear();
+  c->lv.table_host.clear();
   cudaStream_t s = c->work_stream;
   LF_CUDA(c, ensure(c->views, sizeof(ViewStatic) * (size_t)n_views));
   LF_CUDA(c, cudaMemcpyAsync(c->views.p, vs.data(), sizeof(ViewStatic) * (size_t)n_views, cudaMemcpyHostToDevice, s));
@@ -585,6 +626,7 @@ lf_status lf_load_views(lf_ctx* c, int32_t n_views, const lf_pose* poses, const 
   c->n_views = n_views;
   c->views_host = std::move(vs);
   c->disk_mode = 0;
+  c->persistent_blocks = 0;  // the raster's occupancy depends on the texture format
   c->src_w = W;
   c->src_h = H;
   c->tex_fmt = fmt;
@@ -710,7 +752,9 @@ lf_status lf_render_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const 
                               (int64_t)(intptr_t)c->masks.p, (int64_t)(intptr_t)c->pool.p,
                               (int64_t)(intptr_t)c->active.p, (int64_t)(intptr_t)c->small.p,
                               (int64_t)(intptr_t)c->tex.p, (int64_t)(intptr_t)c->depth.p, c->persistent_blocks,
-                              c->cfg.tile_w, c->cfg.tile_h, c->cfg.timing, c->disk_mode};
+                              c->cfg.tile_w, c->cfg.tile_h, c->cfg.timing, c->disk_mode, c->lv.n_fine,
+                              (int64_t)(intptr_t)c->lv.pool.p, (int64_t)(intptr_t)c->lv.enable.p,
+                              (int64_t)(intptr_t)c->lv.visible.p};
   for (int e = 0; e < n_eyes; ++e) { sig.push_back(intr[e].width); sig.push_back(intr[e].height); }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (c->cfg.timing) {
@@ -746,6 +790,136 @@ lf_status lf_render_batch(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const 
   c->last_tiles = L.total_tiles;
   c->has_call = true;
   return LF_OK;
+}
+
+lf_status lf_set_levels(lf_ctx* c, int32_t n_fine, int32_t n_pages) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  if (c->n_views <= 0) return fail(c, LF_ERR_STATE, "views not loaded");
+  if (c->lv.n_fine > 0) return fail(c, LF_ERR_STATE, "the levels are set already: load the views again first");
+  if (n_fine < 1 || n_fine >= c->n_views || n_pages < 1 || n_pages > n_fine)
+    return fail(c, LF_ERR_INVALID_ARG, "need 1 <= n_pages <= n_fine < n_views");
+  lf_status st = quiesce(c);
+  if (st != LF_OK) return st;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_sig.clear(); }
+  const int nc = c->n_views - n_fine;
+  // per coarse view, the fine views whose disks overlap its disk: chord distance
+  // between the centres below the sum of the radii (FP64)
+  std::vector<int32_t> off(nc + 1, 0), ids;
+  for (int k = 0; k < nc; ++k) {
+    const ViewStatic& C = c->views_host[n_fine + k];
+    for (int f = 0; f < n_fine; ++f) {
+      const ViewStatic& F = c->views_host[f];
+      const double dx = (double)C.disk_c[0] - (double)F.disk_c[0], dy = (double)C.disk_c[1] - (double)F.disk_c[1];
+      const double dz = (double)C.disk_c[2] - (double)F.disk_c[2];
+      if (std::sqrt(dx * dx + dy * dy + dz * dz) < (double)C.disk_r + (double)F.disk_r) ids.push_back(f);
+    }
+    off[k + 1] = (int32_t)ids.size();
+  }
+  // the coarse images move to their own buffer; the fine ones leave the device
+  const size_t texel_bytes = c->tex_fmt == LF_TEX_F32 ? 16 : c->tex_fmt == LF_TEX_BF16 ? 8 : 4;
+  const size_t per = texel_bytes * (size_t)c->src_w * c->src_h;
+  Buffer coarse;
+  LF_CUDA(c, ensure(coarse, per * nc));
+  LF_CUDA(c, cudaMemcpy(coarse.p, static_cast<char*>(c->tex.p) + per * n_fine, per * nc, cudaMemcpyDeviceToDevice));
+  release(c->tex);
+  c->tex = coarse;
+  auto& L = c->lv;
+  LF_CUDA(c, ensure(L.pool, per * (size_t)n_pages));
+  LF_CUDA(c, ensure(L.table, sizeof(void*) * (size_t)c->n_views));
+  LF_CUDA(c, ensure(L.page_of_view, sizeof(int32_t) * (size_t)n_fine));
+  LF_CUDA(c, ensure(L.overlap_off, sizeof(int32_t) * off.size()));
+  LF_CUDA(c, ensure(L.overlap_ids, sizeof(int32_t) * std::max<size_t>(1, ids.size())));
+  L.view_page.assign(n_fine, -1);
+  L.page_view.assign(n_pages, -1);
+  L.table_host.assign(c->n_views, nullptr);
+  for (int k = 0; k < nc; ++k) L.table_host[n_fine + k] = static_cast<const char*>(c->tex.p) + per * k;
+  LF_CUDA(c, cudaMemcpy(L.table.p, L.table_host.data(), sizeof(void*) * L.table_host.size(), cudaMemcpyHostToDevice));
+  LF_CUDA(c, cudaMemcpy(L.page_of_view.p, L.view_page.data(), sizeof(int32_t) * n_fine, cudaMemcpyHostToDevice));
+  LF_CUDA(c, cudaMemcpy(L.overlap_off.p, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice));
+  if (!ids.empty())
+    LF_CUDA(c, cudaMemcpy(L.overlap_ids.p, ids.data(), sizeof(int32_t) * ids.size(), cudaMemcpyHostToDevice));
+  L.n_fine = n_fine;
+  L.n_pages = n_pages;
+  return LF_OK;
+}
+
+lf_status lf_upload_pages(lf_ctx* c, int32_t n, const int32_t* views, const int32_t* pages,
+                          const uint8_t* const* rgba8, void* stream) {
+  if (!c) return LF_ERR_INVALID_ARG;
+  auto& L = c->lv;
+  if (L.n_fine <= 0) return fail(c, LF_ERR_STATE, "no levels set (lf_set_levels)");
+  if (n < 0 || (n > 0 && (!views || !pages || !rgba8))) return fail(c, LF_ERR_INVALID_ARG, "bad upload arguments");
+  std::vector<uint8_t> seen_v(L.n_fine, 0), seen_p(L.n_pages, 0);
+  for (int k = 0; k < n; ++k) {
+    if (views[k] < 0 || views[k] >= L.n_fine || pages[k] < 0 || pages[k] >= L.n_pages || !rgba8[k])
+      return fail(c, LF_ERR_INVALID_ARG, "upload view, page or image out of range");
+    if (seen_v[views[k]]++ || seen_p[pages[k]]++)
+      return fail(c, LF_ERR_INVALID_ARG, "a view or page appears twice in one upload");
+  }
+  if (n == 0) return LF_OK;
+  LF_CUDA(c, cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LF_CUDA(c, cudaStreamSynchronize(s));  // renders that read the pages being replaced are done
+  const size_t texel_bytes = c->tex_fmt == LF_TEX_F32 ? 16 : c->tex_fmt == LF_TEX_BF16 ? 8 : 4;
+  const int64_t per_view = (int64_t)c->src_w * c->src_h;
+  const size_t per = texel_bytes * (size_t)per_view;
+  char* pool = static_cast<char*>(L.pool.p);
+  if (c->tex_fmt != LF_TEX_U8) LF_CUDA(c, ensure(L.stage, (size_t)n * per_view * 4));
+  for (int k = 0; k < n; ++k) {
+    char* dst = pool + per * pages[k];
+    if (c->tex_fmt == LF_TEX_U8) {
+      LF_CUDA(c, cudaMemcpyAsync(dst, rgba8[k], (size_t)per_view * 4, cudaMemcpyHostToDevice, s));
+      continue;
+    }
+    uint8_t* st8 = static_cast<uint8_t*>(L.stage.p) + (size_t)k * per_view * 4;
+    LF_CUDA(c, cudaMemcpyAsync(st8, rgba8[k], (size_t)per_view * 4, cudaMemcpyHostToDevice, s));
+    ViewStatic* vs = static_cast<ViewStatic*>(c->views.p) + views[k];
+    const float* scale = nullptr;
+    if (c->tex_fmt == LF_TEX_FP8E4M3) {
+      // the view's FP8 scale, from this image (as lf_load_views computes it)
+      float* sc = reinterpret_cast<float*>(&vs->tex_scale);
+      LF_CUDA(c, launch_view_scale(st8, 1, per_view, sc, vs, s));
+      scale = sc;
+    }
+    LF_CUDA(c, launch_convert_textures(st8, dst, per_view, c->tex_fmt, scale, per_view, s));
+  }
+  LF_CUDA(c, cudaStreamSynchronize(s));
+  // the page table: a page's previous view is no longer resident
+  for (int k = 0; k < n; ++k) {
+    const int v = views[k], p = pages[k];
+    const int w = L.page_view[p];
+    if (w >= 0 && w != v) { L.view_page[w] = -1; L.table_host[w] = nullptr; }
+    const int q = L.view_page[v];
+    if (q >= 0 && q != p) L.page_view[q] = -1;
+    L.page_view[p] = v;
+    L.view_page[v] = p;
+    L.table_host[v] = pool + per * p;
+  }
+  LF_CUDA(c, cudaMemcpy(L.table.p, L.table_host.data(), sizeof(void*) * (size_t)L.n_fine, cudaMemcpyHostToDevice));
+  LF_CUDA(c, cudaMemcpy(L.page_of_view.p, L.view_page.data(), sizeof(int32_t) * (size_t)L.n_fine,
+                        cudaMemcpyHostToDevice));
+  return LF_OK;
+}
+
+lf_status lf_levels_wanted(lf_ctx* c, int32_t cap, int32_t* views, int32_t* n) {
+  if (!c || !n || cap < 0 || (cap > 0 && !views)) return LF_ERR_INVALID_ARG;
+  *n = 0;
+  if (c->lv.n_fine <= 0) return fail(c, LF_ERR_STATE, "no levels set (lf_set_levels)");
+  if (!c->has_call || !c->lv.visible.p) return fail(c, LF_ERR_STATE, "no render call yet");
+  LF_CUDA(c, cudaSetDevice(c->device));
+  LF_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  std::vector<uint8_t> vis((size_t)c->last_eyes * c->n_views);
+  LF_CUDA(c, cudaMemcpy(vis.data(), c->lv.visible.p, vis.size(), cudaMemcpyDeviceToHost));
+  int32_t k = 0;
+  for (int v = 0; v < c->lv.n_fine; ++v) {
+    bool any = false;
+    for (int e = 0; e < c->last_eyes && !any; ++e) any = vis[(size_t)e * c->n_views + v] != 0;
+    if (!any) continue;
+    if (k < cap) views[k] = v;
+    ++k;
+  }
+  *n = k;
+  return k > cap ? fail(c, LF_ERR_CAPACITY, "more wanted views than cap") : LF_OK;
 }
 
 lf_status lf_get_stats(lf_ctx* c, lf_stats* out) {
@@ -854,6 +1028,7 @@ extern "C" lf_status lf_render_static(lf_ctx* c, const lf_pose* eye, const lf_in
                                       void* stream) {
   lf_status st = check_ready(c);
   if (st != LF_OK) return st;
+  if (c->lv.n_fine > 0) return fail(c, LF_ERR_UNSUPPORTED, "lf_render_static: two-level frames need per-call buffers");
   if (c->n_views > kStaticMaxViews)
     return fail(c, LF_ERR_CAPACITY, "lf_render_static: more than 32 views are loaded");
   if (c->G > kStaticMaxGrid) return fail(c, LF_ERR_CAPACITY, "lf_render_static: mesh grid larger than 33 x 33");

@@ -17,6 +17,10 @@
 //   bin offsets / bin entries     per (eye, view): its triangles binned into the screen
 //                                 tiles of its footprint (pool indices), plus a list of
 //                                 triangles spanning more than bin_max_tiles tiles
+// Two-level progressive rendering (lf_set_levels): the coarse views' textures,
+// a pool of pages holding fine views' textures, a per-view texture table and
+// page table, per coarse view the fine views whose disks overlap it (CSR), and
+// per call the exact view selection and the drawn-view bits of each eye.
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -86,6 +90,7 @@ struct __align__(16) ViewRec {
   // k = n.c', u0 = x.c', v0 = y.c' (c' the disk centre), reciprocal extents
   float ov_n[3], ov_x[3], ov_y[3], ov_k, ov_u0, ov_v0;
   float ov_ru[2], ov_rv[2];   // 1 / e_u+, 1 / e_u-, 1 / e_v+, 1 / e_v-
+  const void* tex;            // the view's first texel (a pool page for a fine view of a two-level frame)
 };
 
 struct __align__(16) TriRec {
@@ -146,6 +151,14 @@ struct FrameArgs {
   uint32_t* texel_bits;
   // persistent batch raster
   int32_t* work_counter;
+  // two-level progressive rendering (all null / 0 with one level)
+  const void* const* tex_table;  // per view: its texels (a pool page for fine views; null when not resident)
+  uint32_t* enable_bits;         // n_eyes x mask_words: the views each eye draws
+  uint8_t* visible;              // n_eyes x n_views: exact view selection of every view
+  const int32_t* page_of_view;   // per fine view: its page, -1 when not resident
+  const int32_t* overlap_off;    // per coarse view: its range in overlap_ids (n_views - n_fine + 1 entries)
+  const int32_t* overlap_ids;    // fine views whose disks overlap the coarse view's
+  int32_t n_fine;                // views [0, n_fine) are the streamed fine level
 };
 
 // launchers (return cudaGetLastError())
@@ -160,6 +173,11 @@ cudaError_t launch_bin(const FrameArgs& a, cudaStream_t s);
 cudaError_t launch_raster(const FrameArgs& a, bool inspect, bool persistent, int persistent_blocks,
                           cudaStream_t s);
 cudaError_t raster_occupancy(int tile_w, int tile_h, int tex_format, int disk_mode, int* blocks_per_sm);
+// Two-level frames: the exact view selection of every view into a.visible (the
+// raster's disk tests alone), then the drawn views into a.enable_bits, which
+// are then ANDed into the tile masks.
+cudaError_t launch_select(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_drawn(const FrameArgs& a, cudaStream_t s);
 // FP8 textures: per-view scale = max(RGB) / 255 / 448, also stored in views[v].tex_scale.
 cudaError_t launch_view_scale(const uint8_t* rgba8, int n_views, int64_t texels_per_view, float* scale,
                               ViewStatic* views, cudaStream_t s);

@@ -86,11 +86,11 @@ __device__ __forceinline__ float3 bilinear(const void* tex, int W, int H, float 
   const int iu = (int)fu, jv = (int)fv;
   const int i0 = min(max(iu, 0), W - 1), i1 = min(max(iu + 1, 0), W - 1);
   const int j0 = min(max(jv, 0), H - 1), j1 = min(max(jv + 1, 0), H - 1);
-  const int r0 = j0 * W, r1 = j1 * W;
-  const float3 c00 = texel<FMT>(tex, r0 + i0, scale), c10 = texel<FMT>(tex, r0 + i1, scale);
-  const float3 c01 = texel<FMT>(tex, r1 + i0, scale), c11 = texel<FMT>(tex, r1 + i1, scale);
+  const int t00 = j0 * W + i0, t10 = j0 * W + i1, t01 = j1 * W + i0, t11 = j1 * W + i1;
+  const float3 c00 = texel<FMT>(tex, t00, scale), c10 = texel<FMT>(tex, t10, scale);
+  const float3 c01 = texel<FMT>(tex, t01, scale), c11 = texel<FMT>(tex, t11, scale);
   if (bits) {
-    const int64_t t[4] = {bit_base + r0 + i0, bit_base + r0 + i1, bit_base + r1 + i0, bit_base + r1 + i1};
+    const int64_t t[4] = {bit_base + t00, bit_base + t10, bit_base + t01, bit_base + t11};
     for (int k = 0; k < 4; ++k) atomicOr(&bits[t[k] >> 5], 1u << (t[k] & 31));
   }
   // explicit roundings: the same image whatever code the caller is compiled into
@@ -201,7 +201,9 @@ __device__ __forceinline__ int collect_views(const uint32_t* mask, int mask_word
 // pixels, keeping the nearest fragment per view; (d) when the view changes, a
 // pixel's winner is buffered, and buffered winners are shaded (bilinear
 // fetch, weight, accumulate) with both pixels' texel loads in flight.
-template <int TW, int TH, int FMT, bool INSPECT, bool MANY_EYES, bool OVAL>
+// SELECT: only the disk tests - every view some pixel of the strip sees is
+// marked in A.visible, and nothing is drawn (the first pass of a two-level frame).
+template <int TW, int TH, int FMT, bool INSPECT, bool MANY_EYES, bool OVAL, bool SELECT>
 __device__ void raster_strip(const FrameArgs& A, const int item, const int strip, WarpSmem& S) {
   constexpr int ROWS = (32 / TW) * kPx;
   const int lane = threadIdx.x & 31;
@@ -286,8 +288,7 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
         S.cc[lane] = *reinterpret_cast<const float4*>(VR.cc);
         S.inv_r[lane] = VR.inv_r;
       }
-      const char* base = static_cast<const char*>(A.textures);
-      S.tex[lane] = base + (int64_t)S.views[lane] * tex_per_view * (FMT == LF_TEX_F32 ? 16 : FMT == LF_TEX_BF16 ? 8 : 4);
+      S.tex[lane] = VR.tex;
       int b0 = 0, bn = 0, g0 = 0, gn = 0;
       if (VR.bin_off >= 0) {
         const int lx = tx - VR.btx0, ly = ty - VR.bty0;
@@ -328,6 +329,11 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
 #pragma unroll
     for (int q = 1; q < kPx; ++q) wmask |= inmask[q];
     wmask = __reduce_or_sync(0xffffffffu, wmask);  // views some pixel of the strip sees
+    if constexpr (SELECT) {
+      if (lane < nv && ((wmask >> lane) & 1u)) A.visible[(int64_t)e * A.n_views + S.views[lane]] = 1;
+      __syncwarp();  // the view table is rewritten by the next round
+      continue;
+    }
     if (lane < nv && ((wmask >> lane) & 1u)) A.active[(int64_t)e * A.n_views + S.views[lane]] = 1;
     {
       // exclusive prefix of the seen views' entry counts
@@ -567,6 +573,7 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
     shade_flush();
     __syncwarp();  // the view table is rewritten by the next round
   }
+  if constexpr (SELECT) return;
 #pragma unroll
   for (int q = 0; q < kPx; ++q) {
     if (!valid[q]) continue;
@@ -588,14 +595,14 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
 
 // Non-persistent: one CTA per tile, warp w takes strip w.  Persistent: every
 // warp takes (tile, strip) work items from the device counter by itself.
-template <int TW, int TH, int FMT, bool INSPECT, bool PERSISTENT, bool OVAL>
+template <int TW, int TH, int FMT, bool INSPECT, bool PERSISTENT, bool OVAL, bool SELECT = false>
 __global__ void __launch_bounds__(TW * TH / kPx, 6) raster_kernel(FrameArgs A) {
   constexpr int WARPS = TW * TH / kPx / 32;
   using Smem = typename std::conditional<OVAL, WarpSmemOval, WarpSmem>::type;
   __shared__ Smem S[WARPS];
   const int warp = threadIdx.x >> 5;
   if constexpr (!PERSISTENT) {
-    raster_strip<TW, TH, FMT, INSPECT, false, OVAL>(A, blockIdx.x, warp, S[warp]);
+    raster_strip<TW, TH, FMT, INSPECT, false, OVAL, SELECT>(A, blockIdx.x, warp, S[warp]);
   } else {
     const int n_items = A.total_tiles * WARPS;
     for (;;) {
@@ -603,7 +610,7 @@ __global__ void __launch_bounds__(TW * TH / kPx, 6) raster_kernel(FrameArgs A) {
       if ((threadIdx.x & 31) == 0) item = atomicAdd(A.work_counter, 1);
       item = __shfl_sync(0xffffffffu, item, 0);
       if (item >= n_items) break;
-      raster_strip<TW, TH, FMT, INSPECT, true, OVAL>(A, item / WARPS, item % WARPS, S[warp]);
+      raster_strip<TW, TH, FMT, INSPECT, true, OVAL, SELECT>(A, item / WARPS, item % WARPS, S[warp]);
     }
   }
 }
@@ -666,6 +673,64 @@ static cudaError_t occupancy_disk(int fmt, int* n) {
 template <int TW, int TH>
 static cudaError_t occupancy_tile(int fmt, int disk_mode, int* n) {
   return disk_mode == 1 ? occupancy_disk<TW, TH, true>(fmt, n) : occupancy_disk<TW, TH, false>(fmt, n);
+}
+
+template <int TW, int TH>
+static cudaError_t launch_select_tile(const FrameArgs& a, cudaStream_t s) {
+  if (a.disk_mode == 1) raster_kernel<TW, TH, LF_TEX_F32, false, false, true, true><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
+  else raster_kernel<TW, TH, LF_TEX_F32, false, false, false, true><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select(const FrameArgs& a, cudaStream_t s) {
+  if (a.total_tiles <= 0) return cudaSuccess;
+  if (a.tile_w == 16 && a.tile_h == 16) return launch_select_tile<16, 16>(a, s);
+  if (a.tile_w == 32 && a.tile_h == 8) return launch_select_tile<32, 8>(a, s);
+  if (a.tile_w == 8 && a.tile_h == 8) return launch_select_tile<8, 8>(a, s);
+  return cudaErrorInvalidValue;
+}
+
+// The views each eye draws in a two-level frame (Sec. 7.2): a fine view that it
+// selects and whose image is resident; a coarse view that it selects and whose
+// disk overlaps a selected fine view whose image is missing.
+__global__ void drawn_kernel(FrameArgs A) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x, e = blockIdx.y;
+  if (v >= A.n_views) return;
+  const uint8_t* vis = A.visible + (int64_t)e * A.n_views;
+  bool on = false;
+  if (v < A.n_fine) {
+    on = vis[v] && A.page_of_view[v] >= 0;
+  } else if (vis[v]) {
+    const int c = v - A.n_fine;
+    for (int k = A.overlap_off[c]; k < A.overlap_off[c + 1] && !on; ++k) {
+      const int f = A.overlap_ids[k];
+      on = vis[f] && A.page_of_view[f] < 0;
+    }
+  }
+  if (on) atomicOr(A.enable_bits + (int64_t)e * A.mask_words + (v >> 5), 1u << (v & 31));
+}
+
+// Only the drawn views stay in the tile masks: one thread per (tile, mask word).
+__global__ void enable_masks_kernel(FrameArgs A) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)A.total_tiles * A.mask_words) return;
+  const int tile = (int)(idx / A.mask_words), w = (int)(idx % A.mask_words);
+  int e = 0;
+  for (int lo = 0, hi = A.n_eyes; hi - lo > 1;) {  // the last eye whose first tile is <= tile
+    const int mid = (lo + hi) >> 1;
+    if (A.eyes[mid].tile_base <= tile) lo = mid;
+    else hi = mid;
+    e = lo;
+  }
+  A.tile_masks[idx] &= A.enable_bits[(int64_t)e * A.mask_words + w];
+}
+
+cudaError_t launch_drawn(const FrameArgs& a, cudaStream_t s) {
+  dim3 grid((a.n_views + 127) / 128, a.n_eyes);
+  drawn_kernel<<<grid, 128, 0, s>>>(a);
+  const int64_t n = (int64_t)a.total_tiles * a.mask_words;
+  if (n > 0) enable_masks_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t raster_occupancy(int tile_w, int tile_h, int fmt, int disk_mode, int* n) {

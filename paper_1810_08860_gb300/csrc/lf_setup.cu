@@ -305,6 +305,10 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
         R.ov_rv[0] = __double2float_rn(__ddiv_rn(1.0, (double)V.disk_ext[2]));
         R.ov_rv[1] = __double2float_rn(__ddiv_rn(1.0, (double)V.disk_ext[3]));
       }
+      // the view's texels: its page in a two-level frame, else its slice of the texture array
+      const int tb = A.tex_format == LF_TEX_F32 ? 16 : A.tex_format == LF_TEX_BF16 ? 8 : 4;
+      R.tex = A.tex_table ? A.tex_table[v]
+                          : static_cast<const char*>(A.textures) + (int64_t)v * A.src_w * A.src_h * tb;
       R.tri_base = 0;
       R.bin_off = -1;
       R.big_base = 0;
@@ -548,6 +552,8 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
   ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
   const int bb0 = R.bb[0], bb1 = R.bb[1], bb2 = R.bb[2], bb3 = R.bb[3];
   if (bb0 > bb2 || bb1 > bb3) return;  // disk footprint misses the eye
+  // a two-level frame sets up only the views the eye draws
+  if (A.enable_bits && !((A.enable_bits[(int64_t)e * A.mask_words + (v >> 5)] >> (v & 31)) & 1u)) return;
   const EyeParams& E = A.eyes[e];
   const EyeFloat& EF = A.eyes_f[e];
   const int G = A.G;

@@ -48,13 +48,19 @@ def tiny_renderer(lfmod, tiny):
 
 
 def _ref_records(ref, W, pixels=None):
-    """Oracle records grouped by flat pixel index j*W+i, sorted by view."""
+    """Oracle records grouped by flat pixel index j*W+i, sorted by view.  A
+    pixel listed more than once (samples drawn with replacement) keeps the
+    records of its first listing."""
     out = {}
+    first = {}
     for f in ref["frags"]:
-        k = int(f["pixel"])
+        p = int(f["pixel"])
+        k = p
         if pixels is not None:
-            i, j = pixels[k]
+            i, j = pixels[p]
             k = int(j) * W + int(i)
+        if first.setdefault(k, p) != p:
+            continue
         out.setdefault(k, []).append((int(f["view"]), int(f["n_cover"]), int(f["winner"]), int(f["min_id"]),
                                       int(f["max_id"]), int(f["id_hash"])))
     return out
@@ -526,4 +532,48 @@ def test_tuner_never_picks_an_overflowing_configuration(lfmod, tiny):
     r.render(eyes[:1])
     with pytest.raises(lfmod.LFError):
         r.stats()
+    r.close()
+
+
+def test_batch_at_full_batch_sizes_against_the_oracle(lfmod, tiny):
+    """The batched form (persistent raster under a captured graph, autotuned)
+    on a batch shaped like the 128-eye benchmark batch - 64 stereo head poses
+    of sizes 512^2, 1024^2, 1440x1600, 2048^2 and two ragged ones - compared
+    directly with the oracle: every eye's sampled pixels in colour and valid
+    mask, and every eighth eye's coverage records at those pixels."""
+    import torch
+
+    rng = scene.SplitMix64(4243)
+    sizes = [(512, 512), (1024, 1024), (1440, 1600), (2048, 2048), (333, 517), (1025, 63)]
+    eyes = []
+    for k in range(64):
+        w, h = sizes[k % len(sizes)]
+        eyes += scene.head_pose_eyes(rng, w, h, 90.0, yaw_range=(-math.radians(10), math.radians(10)),
+                                     pitch_deg=10.0)
+    r = lfmod.Renderer(0, max_eyes=len(eyes))
+    r.load_views(tiny)
+    r.build_meshes(tiny)
+    tuned = [o.clone() for o in r.tune_batch(eyes, replays=1)["out"]]
+    replay = r.render_batch(eyes)  # the captured graph again
+    torch.cuda.synchronize()
+    assert r.stats()["error_word"] == 0
+    prng = np.random.default_rng(21)
+    for k, e in enumerate(eyes):
+        assert torch.equal(tuned[k], replay[k]), k
+        pix = np.stack([prng.integers(0, e.width, 200), prng.integers(0, e.height, 200)], axis=1)
+        ref = oracle.render(tiny, e, pixels=pix, fragments=(k % 8 == 0), max_slots=16)
+        g = replay[k].cpu().numpy().astype(np.float64)[pix[:, 1], pix[:, 0]]
+        want = ref["rgba"]
+        ok = want[:, 3] > 0
+        assert np.array_equal(g[:, 3] > 0, ok), k
+        if ok.any():
+            assert np.max(np.abs(g[ok, :3] - want[ok, :3])) <= COLOUR_TOL, k
+        if k % 8 == 0:
+            got = r.render_inspect(e, max_records=16)
+            assert torch.equal(got["rgba"], replay[k]), k
+            flat = [int(j) * e.width + int(i) for i, j in pix]
+            gr = _gpu_records(got, flat)
+            orr = _ref_records(ref, e.width, pixels=pix)
+            for q in set(flat):
+                assert gr.get(q, []) == orr.get(q, []), (k, q)
     r.close()
