@@ -237,9 +237,9 @@ def host_e2e(r, heads, shapes, flush, stream, steps, px_per_step, world, form="p
     return whole_job_rate(px_per_step * steps, total_ms, world), statistics.mean(lat)
 
 
-def ncu_traffic(profile: str, files=RASTER_SOURCES):
-    """DRAM bytes per launch from the committed ncu summary profiles/<profile>.txt,
-    if it was taken on the current source of the kernel (`files`); else None."""
+def ncu_value(profile: str, key: str, files=RASTER_SOURCES):
+    """A figure from the committed ncu summary profiles/<profile>.txt, if it was
+    taken on the current source of the kernel (`files`); else None."""
     path = os.path.join(ROOT, "profiles", profile + ".txt")
     try:
         vals = {}
@@ -250,9 +250,14 @@ def ncu_traffic(profile: str, files=RASTER_SOURCES):
                     vals[k.strip()] = v.strip()
         if vals.get("kernel_source_sha") != kernel_source_hash(files):
             return None
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except Exception:
         return None
+
+
+def ncu_traffic(profile: str, files=RASTER_SOURCES):
+    """DRAM bytes per launch from the committed ncu summary (see ncu_value)."""
+    return ncu_value(profile, "dram_bytes_per_launch", files)
 
 
 class ClockSampler:
@@ -1394,6 +1399,29 @@ def run_twolevel(args):
     return 0
 
 
+def issue_roofline(args, ms_launch, clk, raster_bytes, hbm_peak, px):
+    """The raster against the SM instruction-issue roofline: the warp instructions
+    per launch of the committed full-section capture (while its source hash
+    matches) over this run's launch time, against 4 issue slots per SM per clock
+    at the sampled SM clock - the bound that keeps the kernel below its HBM
+    roofline."""
+    import torch
+
+    prof = "raster_%s_%s_%s" % (args.workload, args.tex, args.tile)
+    inst = ncu_value(prof, "warp_instructions_per_launch")
+    if inst is None or args.disk != "round" or args.workload != "rig":
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak = sms * 4 * mhz * 1e6
+    floor_s = inst / peak
+    return {"bound": "issue", "unit": "warp inst/s", "achieved": inst / (ms_launch / 1000.0), "peak": peak,
+            "frac": inst / (ms_launch / 1000.0) / peak, "warp_inst_per_launch": inst, "warp_inst_per_pixel": inst / px,
+            "issue_active_pct_ncu": ncu_value(prof, "issue_active_pct"),
+            "hbm_frac_at_issue_peak": raster_bytes / floor_s / 1e9 / hbm_peak,
+            "source": "profiles/%s.txt (instructions of a rig256 capture of the same eyes and meshes)" % prof}
+
+
 def run_ours(args):
     import torch
 
@@ -1491,6 +1519,7 @@ def run_ours(args):
                      "unique_texels_per_step": mean_u, "ms_per_launch": mean_raster},
         "step_roofline": {"bytes_per_step": step_bytes, "achieved": step_achieved, "frac": step_achieved / peak,
                           "unit": "GB/s"},
+        "issue_roofline": issue_roofline(args, mean_raster, clk, raster_bytes, peak, px_per_step),
         "phases_ms": {"view_setup": statistics.mean(setup_v_ms), "tri_setup": statistics.mean(setup_t_ms),
                       "raster": mean_raster},
         "active_views_per_step": statistics.mean(active),
