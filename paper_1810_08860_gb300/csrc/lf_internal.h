@@ -192,11 +192,11 @@ constexpr int kRefineParams = 11011;  // W1 864, b1 32, W2 9216, b2 32, W3 864, 
 constexpr int kRefineOffW1 = 0, kRefineOffB1 = 864, kRefineOffW2 = 896, kRefineOffB2 = 10112;
 constexpr int kRefineOffW3 = 10144, kRefineOffB3 = 11008;
 // packed BF16 operands: w1f [32][32], w2f [9][32][32], w3f [9][8][32], w3b [32][32], w2b [9][32][32]
-// (mma.sync layers), then the fused kernel's B operands (kernel columns stacked along N):
-// L1 [3 dy][2 g][96][8], L2 [3 dy][2 kc][2 g][96][8], L3 [3 dy][2 kc][2 g][16][8], b2 [2][96][8], b3 [2][16][8]
+// (mma.sync layers), then the fused kernel's B operands: L1 [3 dy][2 g][32][8] (pair-packed
+// taps), L2 [3 dy][3 dx][2 kc][2 g][32][8], L3 [3 dy][2 kc][2 g][16][8] (kernel columns along N)
 constexpr int kPackW1f = 0, kPackW2f = 1024, kPackW3f = 10240, kPackW3b = 12544, kPackW2b = 13568;
 constexpr int kPackTc = 22784;
-constexpr int kRefinePackedElems = 22784 + 4608 + 9216 + 1536 + 1536 + 256;  // + b2, b3 blocks
+constexpr int kRefinePackedElems = 22784 + 1536 + 9216 + 1536;
 
 enum : int { kConvInRGBA = 0, kConvInBF16 = 1 };
 enum : int { kEpiRelu = 0, kEpiMask = 1, kEpiResid = 2, kEpiLoss = 3 };

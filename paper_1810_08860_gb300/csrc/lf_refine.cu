@@ -418,13 +418,12 @@ __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float*
 //   w3f[9][8 o][32 c]     W3[o][c][tap], o < 3
 //   w3b[32 c][32 k']      k' = tap * 3 + o < 27: W3[o][c][8 - tap]   (through layer 3's input)
 //   w2b[9][32 c][32 o]    W2[o][c][8 - tap]                         (through layer 2's input)
-//   then the fused kernel's B operands, one block per kernel row dy (and K half
-//   kc of 16 input channels), K-major groups g of 8 channels, the three kernel
-//   columns kx stacked along N: L1 [dy][g][kx*32 + o][8], L2 [dy][kc][g][kx*32 + o][8],
-//   L3 [dy][kc][g][kx*4 + o][8]; b1 sits in L1's centre block at input channel 3
-//   (a constant 1 in the kernel's input), and b2, b3 get blocks of their own
-//   ([g][n][8], the bias at K index 0 of the centre column) that meet a
-//   constant-1 operand in one extra MMA per M-tile
+//   then the fused kernel's B operands, K-major groups g of 8 channels:
+//   L1 [dy][g][o][8] over the pair-packed input (x[q-1], x[q]) | (x[q+1], x[q+2]),
+//   four channels R, G, B, 1 per position: kernel column kx = 2g + (e >= 4),
+//   b1 at the constant 1 of the centre tap; L2 [dy][dx][kc][g][o][8] with input
+//   channel c = kc*16 + g*8 + e; L3 [dy][kc][g][kx*4 + o][8] (kernel columns
+//   stacked along N).  b2 and b3 are read in FP32 by the fused kernel.
 __global__ void pack_weights_kernel(const float* __restrict__ prm, __nv_bfloat16* __restrict__ w) {
   constexpr int n1 = 32 * 32, n2 = 9 * 32 * 32, n3 = 9 * 8 * 32, n3b = 32 * 32, n2b = 9 * 32 * 32;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -444,25 +443,19 @@ __global__ void pack_weights_kernel(const float* __restrict__ prm, __nv_bfloat16
   } else if (i < n1 + n2 + n3 + n3b + n2b) {
     const int j = i - n1 - n2 - n3 - n3b, tap = j >> 10, c = (j >> 5) & 31, o = j & 31;
     v = prm[kRefineOffW2 + (o * 32 + c) * 9 + (8 - tap)];
-  } else if (i < kPackTc + 4608) {  // L1 [dy][g][n = kx*32 + o][e], channel c = g*8 + e < 3
-    const int j = i - kPackTc, dy = j / 1536, g = (j / 768) & 1, n = (j >> 3) % 96, c = g * 8 + (j & 7);
-    const int kx = n >> 5, o = n & 31;
-    if (c < 3) v = prm[kRefineOffW1 + o * 27 + c * 9 + dy * 3 + kx];
-    else if (c == 3 && dy == 1 && kx == 1) v = prm[kRefineOffB1 + o];  // b1 meets the constant input channel
-  } else if (i < kPackTc + 4608 + 9216) {  // L2 [dy][kc][g][n = kx*32 + o][e], c = kc*16 + g*8 + e
-    const int j = i - kPackTc - 4608, dy = j / 3072, kc = (j / 1536) & 1, g = (j / 768) & 1, n = (j >> 3) % 96;
-    const int c = kc * 16 + g * 8 + (j & 7), kx = n >> 5, o = n & 31;
+  } else if (i < kPackTc + 1536) {  // L1 [dy][g][o][e]: tap kx = 2g + e/4, channel e%4
+    const int j = i - kPackTc, dy = j / 512, g = (j / 256) & 1, o = (j >> 3) & 31, e = j & 7;
+    const int kx = 2 * g + (e >> 2), c = e & 3;
+    if (kx < 3 && c < 3) v = prm[kRefineOffW1 + o * 27 + c * 9 + dy * 3 + kx];
+    else if (kx == 1 && c == 3 && dy == 1) v = prm[kRefineOffB1 + o];  // b1 meets the constant input channel
+  } else if (i < kPackTc + 1536 + 9216) {  // L2 [dy][dx][kc][g][o][e], c = kc*16 + g*8 + e
+    const int j = i - kPackTc - 1536, dy = j / 3072, kx = (j / 1024) % 3, kc = (j / 512) & 1, g = (j / 256) & 1;
+    const int o = (j >> 3) & 31, c = kc * 16 + g * 8 + (j & 7);
     v = prm[kRefineOffW2 + (o * 32 + c) * 9 + dy * 3 + kx];
-  } else if (i < kPackTc + 4608 + 9216 + 1536) {  // L3 [dy][kc][g][n = kx*4 + o][e], o < 3
-    const int j = i - kPackTc - 4608 - 9216, dy = j / 512, kc = (j / 256) & 1, g = (j / 128) & 1, n = (j >> 3) & 15;
+  } else if (i < kRefinePackedElems) {  // L3 [dy][kc][g][n = kx*4 + o][e], o < 3
+    const int j = i - kPackTc - 1536 - 9216, dy = j / 512, kc = (j / 256) & 1, g = (j / 128) & 1, n = (j >> 3) & 15;
     const int c = kc * 16 + g * 8 + (j & 7), kx = n >> 2, o = n & 3;
     if (o < 3 && kx < 3) v = prm[kRefineOffW3 + (o * 32 + c) * 9 + dy * 3 + kx];
-  } else if (i < kPackTc + 4608 + 9216 + 1536 + 1536) {  // b2 block [g][n = kx*32 + o][e]: b2[o] at k = 0, kx = 1
-    const int j = i - kPackTc - 4608 - 9216 - 1536, g = j / 768, n = (j >> 3) % 96, e = j & 7;
-    if (g == 0 && e == 0 && (n >> 5) == 1) v = prm[kRefineOffB2 + (n & 31)];
-  } else if (i < kRefinePackedElems) {  // b3 block [g][n = kx*4 + o][e]: b3[o] at k = 0, kx = 1
-    const int j = i - kPackTc - 4608 - 9216 - 1536 - 1536, g = j / 128, n = (j >> 3) & 15, e = j & 7;
-    if (g == 0 && e == 0 && (n >> 2) == 1 && (n & 3) < 3) v = prm[kRefineOffB3 + (n & 3)];
   } else {
     return;
   }

@@ -5,37 +5,59 @@
 //
 // One persistent CTA per SM loops over output tiles of 26 x 30 pixels.  A
 // tile's input is a 32 x 36 halo of positions q = 32*hy + hx (3-pixel ring);
-// each halo row is exactly 32 positions, i.e. one warp quadrant of TMEM lanes.
-// Every layer is an implicit GEMM over M-tiles of 128 positions (4 halo rows):
-//   D[q][kx*C + o] = sum_{ky, c} a[q + 32*(ky-1)][c] * W[o][c][ky][kx]
-// so the three kernel rows are three shifted A operands (MMAs accumulating
-// into one D) and the three kernel columns are stacked along N; the epilogue
-// finishes the convolution with two warp shuffles,
-//   out[q][o] = D[q-1][0*C + o] + D[q][1*C + o] + D[q+1][2*C + o].
-// Per M-tile: layer 1 (3 input channels padded to K = 16, N = 96) 3 MMAs,
-// layer 2 (K = 32, N = 96) 6 MMAs, layer 3 (K = 32, N = 16, 3 real outputs
-// per kernel column) 6 MMAs.  The biases ride on the MMAs: the input carries a
-// constant 1 in channel 3 that meets b1 in the centre weights, and layers 2
-// and 3 add one MMA of a constant-1 operand against a bias block.
+// each halo row is exactly 32 positions, one warp quadrant of TMEM lanes.
+// Every layer is an implicit GEMM over M-tiles of 128 positions (4 halo rows).
+// Layers 1 and 2 run the whole 3x3 window in the MMAs, N = 32 outputs:
+//   D[q][o] = sum_{ky, kx, c} a[q + 32*(ky-1) + (kx-1)][c] * W[o][c][ky][kx],
+// each tap a shifted A operand (a position is 16 bytes per 8 channels, so a
+// shift moves the descriptor's start).  Layer 1's input is pair-packed:
+// position s holds (x[s], x[s+1]) as 8 channels (R, G, B, 1 twice), and its A
+// descriptor puts the second K group two positions on, so one K = 16 MMA
+// covers kernel columns -1..+2 (the last with zero weights): one MMA per
+// kernel row.  Layer 2 takes 18 MMAs (9 taps x 2 halves of 32 channels).
+// Layer 3 (3 outputs) stacks the kernel columns along N = 16 and finishes
+// with two warp shuffles per output:
+//   out[q][o] = D[q-1][o] + D[q][4 + o] + D[q+1][8 + o].
+// Measured on GB300, an M = 128, K = 16 MMA costs about max(45, 0.55 N)
+// cycles, so stacking layer 2's columns along N (N = 96) would take fewer
+// tensor cycles, but finishing them costs 64 shuffles and 64 adds per
+// position in the epilogue, which then bounds the kernel; with full windows
+// the epilogue is a TMEM load, the bias, ReLU with BF16 packing (one cvt per
+// pair) and four stores.  b1 meets the constant-1 input channel in the MMAs;
+// b2 and b3 are added in FP32 by the epilogue.
 //
-// Roles: lane 0 of warps 16 and 17 issues the MMAs (even and odd M-tiles) into a
-// ring of 5 TMEM slots of 96 columns, committing each M-tile to the slot's
-// "full" mbarrier; warps 0-15 (four groups of 4 taking M-tiles in turn; warp
-// w reads TMEM lanes 32*(w%4) ..) wait on "full", read the accumulators, release the slot on its
-// "empty" mbarrier, combine the kernel columns, apply ReLU, zero positions outside the image
-// (the next layer's zero padding) and store BF16 rows for the next layer.  A
-// "layer done" mbarrier lets the issuer start a layer once every row of the
-// previous one is in shared memory.  At the end each issuing thread commits to
-// its own "drain" mbarrier and waits for it, so no MMA it issued is still
-// running when the CTA deallocates its tensor memory, also after an abort.  The next tile's FP32 halo streams into a
-// staging buffer with cp.async while the current tile computes; the residual
-// add uses FP32 inputs loaded into registers while layer 3 runs.  Every wait
-// is bounded and reports through an error flag instead of hanging.
+// Roles: lane 0 of warps 16-19 issues the MMAs (issuer i takes the M-tiles
+// whose running number c has c % 4 == i) into a ring of 16 TMEM slots of 32
+// columns, committing each M-tile to a "full" mbarrier; warps 0-15 form four
+// groups of 4 (group g takes c % 4 == g; warp w reads TMEM lanes 32*(w%4) ..)
+// that wait on "full", read the accumulators, release the slot on an "empty"
+// mbarrier and store BF16 rows for the next layer (zero outside the image: the
+// next layer's zero padding).  Slot c % 16 thus always belongs to one issuer
+// and one group, so each ring mbarrier has one waiter taking its phases in
+// order and arrivals that come in phase order (a parity wait cannot tell a
+// phase from the one two phases earlier).
+//
+// Schedule: a tile's 25 M-tiles follow one fixed order (kSchedule) that the
+// issuers and the groups both walk, so the layers overlap.  Per-M-tile
+// "ready" mbarriers carry the dependencies: layer-2 M-tile m waits for
+// layer-1 M-tiles m-1, m and m+1 (its window reads rows of m and m+1 and one
+// position of m-1, and its output overwrites input rows that m-1..m+1 read),
+// layer-3 M-tile m for layer-2 M-tiles m and m+1.  The order leaves tensor work
+// between a producer and its consumer to hide the epilogue.  At a tile
+// boundary every group has taken all 25 M-tiles (so every MMA of the tile is
+// complete) before the next tile's input overwrites buffer 0.
+//
+// The next tile's FP32 halo streams into a staging buffer with cp.async while
+// the current tile computes; the residual add uses FP32 inputs loaded into
+// registers before layer 3's accumulators are read.  Every wait is bounded
+// (%globaltimer) and reports through an error flag instead of hanging; at the
+// end each issuer commits to its own "drain" mbarrier and waits for it, so no
+// MMA is running when the CTA frees its tensor memory, also after an abort.
 //
 // Shared-memory operands use the K-major layout without swizzling: a position
 // (row) holds 8 channels in 16 contiguous bytes, rows follow every 16 bytes
 // (8-row core matrices 128 bytes apart), and each further group of 8 channels
-// starts kGroupB bytes later.
+// starts kGroupB bytes later (layer 1's input: 32 bytes later, see above).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -53,24 +75,39 @@ constexpr int kTW = kHW - 6, kTH = kHH - 6;  // 26 x 30 output pixels
 constexpr int kRows = 1280;                  // positions held per buffer (10 x 128)
 constexpr int kGroupB = kRows * 16;          // bytes per group of 8 channels
 constexpr int kBufB = 4 * kGroupB;           // 32 channels
-// B operands: per kernel row (and K half) a block of 2 groups x N rows x 16 B
-constexpr int kW1Blk = 2 * 96 * 16, kW2Blk = 2 * 96 * 16, kW3Blk = 2 * 16 * 16;
-constexpr int kW1B = 3 * kW1Blk, kW2B = 6 * kW2Blk, kW3B = 6 * kW3Blk;
-constexpr int kB2Blk = 2 * 96 * 16, kB3Blk = 2 * 16 * 16;  // b2, b3 against the constant-1 operand
-constexpr int kWB = kW1B + kW2B + kW3B + kB2Blk + kB3Blk;  // 34,304 bytes
-constexpr int kOnesB = 2 * 128 * 16;         // A operand: channel 0 = 1 on 128 rows
+// B operands, K-major [2 K groups][N rows][16 B]:
+//   layer 1 per kernel row ky (pair-packed taps kx = -1..+2, N = 32),
+//   layer 2 per (ky, kx, half of the 32 input channels) (N = 32),
+//   layer 3 per (ky, half) (N = 16: kx*4 + o).
+constexpr int kW1Blk = 2 * 32 * 16, kW2Blk = 2 * 32 * 16, kW3Blk = 2 * 16 * 16;
+constexpr int kW1B = 3 * kW1Blk, kW2B = 18 * kW2Blk, kW3B = 6 * kW3Blk;
+constexpr int kWB = kW1B + kW2B + kW3B;  // 24,576 bytes
+static_assert(kWB == 2 * (kRefinePackedElems - kPackTc), "the packed operands are the shared-memory image");
 constexpr int kXsB = kHH * kHW * 16;         // FP32 RGBA halo of the next tile
-constexpr int kSlots = 5, kSlotCols = 96;    // TMEM ring
-constexpr int kNumBars = 2 * kSlots + 3;     // full[5], empty[5], layer_done, drain[2]
-constexpr int kSmemBytes = 2 * kBufB + kWB + kOnesB + kXsB + kNumBars * 8 + 8;
-constexpr int kStart1 = 32, kTiles1 = 9;     // layer 1 rows [32, 1184): halo rows 1..36
-constexpr int kStart2 = 64, kTiles2 = 8;     // layer 2 rows [64, 1088): halo rows 2..33
-constexpr int kStart3 = 96, kTiles3 = 8;     // layer 3 rows [96, 1120): halo rows 3..34
-constexpr uint32_t kTmemCols = 512;
+constexpr int kBiasB = 48 * 4;               // b2[32], b3[3]
+constexpr int kSlots = 16, kSlotCols = 32;   // TMEM ring
+constexpr int kIssuers = 4;                  // MMA warps
+constexpr int kRing = 16;                    // ring mbarriers, indexed by c % kRing
 constexpr int kEpiWarps = 16;                // epilogue warps: 4 groups of 4 (one warp per TMEM lane quadrant)
 constexpr int kEpiGroups = kEpiWarps / 4;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kThreads = kEpiThreads + 64;   // + two MMA warps
+constexpr int kThreads = kEpiThreads + 32 * kIssuers;
+static_assert(kRing % kSlots == 0 && kRing % kEpiGroups == 0 && kRing % kIssuers == 0 && kEpiGroups == kIssuers,
+              "each ring mbarrier belongs to one slot, one epilogue group and one issuer");
+constexpr int kStart1 = 32, kTiles1 = 9;     // layer 1 rows [32, 1184): halo rows 1..36
+constexpr int kStart2 = 64, kTiles2 = 8;     // layer 2 rows [64, 1088): halo rows 2..33
+constexpr int kStart3 = 96, kTiles3 = 8;     // layer 3 rows [96, 1120): halo rows 3..34
+constexpr int kMTiles = kTiles1 + kTiles2 + kTiles3;
+// full[16], empty[16], x_ready, drain[4], ready1[9], ready2[8]
+constexpr int kNumBars = 2 * kRing + 1 + kIssuers + kTiles1 + kTiles2;
+constexpr int kSmemBytes = kWB + 2 * kBufB + kXsB + kBiasB + kNumBars * 8 + 16;
+constexpr uint32_t kTmemCols = 512;
+static_assert(kSlots * kSlotCols <= (int)kTmemCols, "the ring fits the tensor memory");
+// The order of a tile's M-tiles (layer << 4 | m): all of layer 1, then layer 2
+// with layer 3 following two layer-2 M-tiles behind.
+__device__ __constant__ const uint8_t kSchedule[kMTiles] = {
+    0x10, 0x11, 0x12, 0x13, 0x14, 0x15, 0x16, 0x17, 0x18, 0x20, 0x21, 0x22, 0x23,
+    0x30, 0x24, 0x31, 0x25, 0x32, 0x26, 0x33, 0x27, 0x34, 0x35, 0x36, 0x37};
 // which wait ran out of time (bit 0: the CTA aborted)
 constexpr int kErrIssuerLayer = 2, kErrIssuerSlot = 4, kErrEpilogueFull = 8, kErrDrain = 16;
 // The drain wait is not cut short by a small configured limit: MMAs that are
@@ -156,11 +193,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld32(uint32_t addr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(addr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// max(lo, 0) and max(hi, 0) rounded to BF16 (nearest even), lo in the low half.
+__device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
@@ -174,6 +231,7 @@ struct FusedArgs {
   const float* in;
   float* out;
   const __nv_bfloat16* wtc;  // B operands: L1, L2, L3 blocks
+  const float* prm;          // FP32 parameters (b2, b3 read from here)
   int32_t* error;            // set to 1 if a wait gave up
   uint64_t wait_ns;          // bound on each mbarrier wait
 };
@@ -204,37 +262,43 @@ __device__ __forceinline__ void prefetch_halo(uint32_t xs, const FusedArgs& A, i
 
 __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* buf0 = sm;          // x (group 0), then a2
-  unsigned char* buf1 = sm + kBufB;  // a1
-  unsigned char* wts = sm + 2 * kBufB;
-  unsigned char* ones = wts + kWB;
-  unsigned char* xs = ones + kOnesB;
-  uint64_t* full = reinterpret_cast<uint64_t*>(xs + kXsB);
-  uint64_t* empty = full + kSlots;
-  uint64_t* layer_done = empty + kSlots;
-  uint64_t* drain = layer_done + 1;  // one per issuing thread
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
+  // The weights come first: layer 1's first window reaches one position before
+  // buffer 0 (an output column that is never used) and reads finite weights there.
+  unsigned char* wts = sm;
+  unsigned char* buf0 = wts + kWB;   // x (pair-packed, group 0), then a2
+  unsigned char* buf1 = buf0 + kBufB;  // a1
+  unsigned char* xs = buf1 + kBufB;
+  float* bias = reinterpret_cast<float*>(xs + kXsB);  // b2[32], b3[3]
+  uint64_t* full = reinterpret_cast<uint64_t*>(xs + kXsB + kBiasB);
+  uint64_t* empty = full + kRing;
+  uint64_t* x_ready = empty + kRing;  // x of the tile is in buffer 0
+  uint64_t* drain = x_ready + 1;      // one per issuer
+  uint64_t* ready1 = drain + kIssuers;  // layer-1 M-tile m is in buffer 1 (four arrivals)
+  uint64_t* ready2 = ready1 + kTiles1;  // layer-2 M-tile m is in buffer 0
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ready2 + kTiles2);
   __shared__ volatile int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool issuer = warp >= kEpiWarps;
 
   // Both activation buffers start at zero (rows never written stay finite),
-  // then the weights and the constant-1 operand; the first tile's halo is already on its way.
+  // then the weights and biases; the first tile's halo is already on its way.
   if (!issuer && blockIdx.x < A.n_tiles) prefetch_halo(su32(xs), A, blockIdx.x);
-  for (int i = tid; i < 2 * kBufB / 16; i += kThreads) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < 2 * kBufB / 16; i += kThreads) reinterpret_cast<uint4*>(buf0)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < kWB / 16; i += kThreads)
     reinterpret_cast<uint4*>(wts)[i] = reinterpret_cast<const uint4*>(A.wtc)[i];
-  for (int i = tid; i < kOnesB / 16; i += kThreads)  // row i (group 0): channel 0 = 1; group 1: zeros
-    reinterpret_cast<uint4*>(ones)[i] = make_uint4(i < 128 ? 0x3F80u : 0u, 0u, 0u, 0u);
+  if (tid < 32) bias[tid] = A.prm[kRefineOffB2 + tid];
+  else if (tid < 35) bias[tid] = A.prm[kRefineOffB3 + tid - 32];
   if (tid == 0) {
     s_abort = 0;
-    for (int b = 0; b < kSlots; ++b) {
+    for (int b = 0; b < kRing; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(full + b)), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(empty + b)), "r"(4));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(layer_done)), "r"(kEpiWarps));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(drain + 0)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(drain + 1)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(x_ready)), "r"(kEpiWarps));
+    for (int b = 0; b < kIssuers; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(drain + b)), "r"(1));
+    for (int b = 0; b < kTiles1 + kTiles2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(ready1 + b)), "r"(4));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -251,206 +315,193 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
 
   if (issuer) {
     // ------------------------------------------------------------ MMA warps (lane 0 of each)
-    // Warp 8 issues the even M-tiles, warp 9 the odd ones, so two threads keep
-    // the tensor core fed; descriptors are precomputed and only their start
-    // address (in 16-byte units, the low field) moves.
+    // Descriptors are precomputed; only their start address (in 16-byte
+    // units, the low field) moves with the M-tile and the tap.
     if (lane == 0) {
-      const int parity = warp - kEpiWarps;
-      const uint64_t a0 = smem_desc(su32(buf0), kGroupB, 128), a1 = smem_desc(su32(buf1), kGroupB, 128);
-      const uint64_t a_ones = smem_desc(su32(ones), 128 * 16, 128);
+      const int me = warp - kEpiWarps;
       const uint32_t sw = su32(wts);
-      const uint64_t b2bias = smem_desc(sw + kW1B + kW2B + kW3B, 96 * 16, 128);
-      const uint64_t b3bias = smem_desc(sw + kW1B + kW2B + kW3B + kB2Blk, 16 * 16, 128);
-      uint64_t b1d[3], b2d[6], b3d[6];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) b1d[k] = smem_desc(sw + k * kW1Blk, 96 * 16, 128);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        b2d[k] = smem_desc(sw + kW1B + k * kW2Blk, 96 * 16, 128);
-        b3d[k] = smem_desc(sw + kW1B + kW2B + k * kW3Blk, 16 * 16, 128);
-      }
-      constexpr uint64_t kHalf = 2 * kGroupB / 16;  // second K half of 16 channels, in 16-byte units
-      uint32_t done_phase = 0;
+      const uint64_t ax = smem_desc(su32(buf0), 32, 128);  // pair-packed x: K group 1 two positions on
+      const uint64_t a1d = smem_desc(su32(buf1), kGroupB, 128);
+      const uint64_t a2d = smem_desc(su32(buf0), kGroupB, 128);
+      const uint64_t b1d = smem_desc(sw, 32 * 16, 128);
+      const uint64_t b2d = smem_desc(sw + kW1B, 32 * 16, 128);
+      const uint64_t b3d = smem_desc(sw + kW1B + kW2B, 16 * 16, 128);
+      constexpr uint64_t kHalf = 2 * kGroupB / 16;  // second half of 16 channels, in 16-byte units
+      constexpr uint32_t kId32 = instr_desc(128, 32), kId16 = instr_desc(128, 16);
+      uint32_t tile_phase = 0;  // parity of this tile's phase of x_ready and the ready barriers
       int c = 0;
       bool ok = true;
-      auto wait_layer = [&]() {
+      auto wait_ready = [&](uint64_t* bar) {  // a barrier completed once per tile
         if (ok) {
-          const int w = wait_phase_status(layer_done, done_phase, &s_abort, A.wait_ns);
+          const int w = wait_phase_status(bar, tile_phase, &s_abort, A.wait_ns);
           if (w == 2) atomicOr(A.error, kErrIssuerLayer);
           ok = w == 0;
         }
-        done_phase ^= 1u;
-        tc_after_sync();
       };
-      // M-tile c: wait for its slot to be released, return the slot's first column.
+      // M-tile c: wait until M-tile c - kSlots has released the slot, return the slot's first column.
       auto slot_col = [&]() -> uint32_t {
-        const int slot = c % kSlots;
-        if (ok) {
-          const int w = wait_phase_status(empty + slot, ((uint32_t)(c / kSlots) & 1u) ^ 1u, &s_abort, A.wait_ns);
+        if (ok && c >= kSlots) {
+          const int p = c - kSlots;
+          const int w = wait_phase_status(empty + p % kRing, (uint32_t)(p / kRing) & 1u, &s_abort, A.wait_ns);
           if (w == 2) atomicOr(A.error, kErrIssuerSlot);
           ok = w == 0;
         }
         tc_after_sync();
-        return tmem + (uint32_t)(slot * kSlotCols);
+        return tmem + (uint32_t)((c % kSlots) * kSlotCols);
       };
       for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
-        wait_layer();  // x of this tile is in buf0
-        for (int m = 0; m < kTiles1; ++m, ++c) {
-          if ((c & 1) != parity || !ok) continue;
-          const uint32_t d = slot_col();
+        wait_ready(x_ready);
+        const int c0 = c;
+        for (int i = (me - c0 % kIssuers + kIssuers) % kIssuers; i < kMTiles; i += kIssuers) {
+          c = c0 + i;
           if (!ok) continue;
-          const uint64_t a = a0 + (uint64_t)(kStart1 - 32 + m * 128);
-          mma(d, a, b1d[0], instr_desc(128, 96), 0);
-          mma(d, a + 32, b1d[1], instr_desc(128, 96), 1);
-          mma(d, a + 64, b1d[2], instr_desc(128, 96), 1);
-          commit(full + c % kSlots);
-        }
-        wait_layer();  // every a1 row is written
-        for (int m = 0; m < kTiles2; ++m, ++c) {
-          if ((c & 1) != parity || !ok) continue;
-          const uint32_t d = slot_col();
-          if (!ok) continue;
-          const uint64_t a = a1 + (uint64_t)(kStart2 - 32 + m * 128);
-#pragma unroll
-          for (int dy = 0; dy < 3; ++dy) {
-            mma(d, a + 32 * dy, b2d[2 * dy], instr_desc(128, 96), dy > 0);
-            mma(d, a + 32 * dy + kHalf, b2d[2 * dy + 1], instr_desc(128, 96), 1);
+          const int layer = kSchedule[i] >> 4, m = kSchedule[i] & 15;
+          if (layer == 2) {  // a1 rows it reads are written; x rows it overwrites are read
+            if (m > 0) wait_ready(ready1 + m - 1);
+            wait_ready(ready1 + m);
+            wait_ready(ready1 + m + 1);
+          } else if (layer == 3) {  // a2 rows it reads are written
+            wait_ready(ready2 + m);
+            if (m + 1 < kTiles2) wait_ready(ready2 + m + 1);
           }
-          mma(d, a_ones, b2bias, instr_desc(128, 96), 1);
-          commit(full + c % kSlots);
-        }
-        wait_layer();  // every a2 row is written
-        for (int m = 0; m < kTiles3; ++m, ++c) {
-          if ((c & 1) != parity || !ok) continue;
+          if (!ok) continue;
           const uint32_t d = slot_col();
           if (!ok) continue;
-          const uint64_t a = a0 + (uint64_t)(kStart3 - 32 + m * 128);
+          if (layer == 1) {
+            // output position p = kStart1 + 128 m + r; kernel row ky starts at p + 32 (ky - 1) - 1
+            const uint64_t a = ax + (uint64_t)(int64_t)(kStart1 - 33 + 128 * m);
 #pragma unroll
-          for (int dy = 0; dy < 3; ++dy) {
-            mma(d, a + 32 * dy, b3d[2 * dy], instr_desc(128, 16), dy > 0);
-            mma(d, a + 32 * dy + kHalf, b3d[2 * dy + 1], instr_desc(128, 16), 1);
+            for (int ky = 0; ky < 3; ++ky) mma(d, a + 32 * ky, b1d + (uint64_t)(ky * (kW1Blk / 16)), kId32, ky > 0);
+          } else if (layer == 2) {
+            const uint64_t a = a1d + (uint64_t)(kStart2 - 33 + 128 * m);
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {  // tap t = 3 ky + kx reads p + 32 (ky - 1) + kx - 1
+#pragma unroll
+              for (int h = 0; h < 2; ++h)
+                mma(d, a + 32 * (t / 3) + (t % 3) + h * kHalf, b2d + (uint64_t)((2 * t + h) * (kW2Blk / 16)), kId32,
+                    t > 0 || h > 0);
+            }
+          } else {
+            const uint64_t a = a2d + (uint64_t)(kStart3 - 32 + 128 * m);
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+#pragma unroll
+              for (int h = 0; h < 2; ++h)
+                mma(d, a + 32 * ky + h * kHalf, b3d + (uint64_t)((2 * ky + h) * (kW3Blk / 16)), kId16, ky > 0 || h > 0);
+            }
           }
-          mma(d, a_ones, b3bias, instr_desc(128, 16), 1);
-          commit(full + c % kSlots);
+          commit(full + c % kRing);
         }
+        c = c0 + kMTiles;
+        tile_phase ^= 1u;
       }
       if (!ok) s_abort = 1;
       // Drain: the commit arrives once every MMA this thread issued has completed.
       // Waited for even after an abort (the abort flag does not cut it short), so
       // the tensor memory is never deallocated under a running MMA.
-      commit(drain + parity);
-      if (wait_phase_status(drain + parity, 0u, nullptr, A.wait_ns > kDrainNs ? A.wait_ns : kDrainNs) == 2)
+      commit(drain + me);
+      if (wait_phase_status(drain + me, 0u, nullptr, A.wait_ns > kDrainNs ? A.wait_ns : kDrainNs) == 2)
         atomicOr(A.error, kErrDrain);
     }
   } else {
     // ---------------------------------------------------------------- epilogue warps
     const int quarter = warp & 3, group = warp >> 2;  // group g takes the M-tiles with c % kEpiGroups == g
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-    int c = 0;          // the same running M-tile counter as the MMA warp
+    int c = 0;  // the same running M-tile counter as the MMA warps
     bool ok = true;
     auto acquire = [&]() -> uint32_t {  // wait for M-tile c's accumulators (lane 0 polls)
-      const int slot = c % kSlots;
       int got = 1;
       if (lane == 0) {
-        const int w = wait_phase_status(full + slot, (uint32_t)(c / kSlots) & 1u, &s_abort, A.wait_ns);
+        const int w = wait_phase_status(full + c % kRing, (uint32_t)(c / kRing) & 1u, &s_abort, A.wait_ns);
         if (w == 2) atomicOr(A.error, kErrEpilogueFull);
         got = w == 0;
       }
       ok = __shfl_sync(0xffffffffu, got, 0) != 0;
       if (!ok) s_abort = 1;
       tc_after_sync();
-      return tmem + lane_base + (uint32_t)(slot * kSlotCols);
+      return tmem + lane_base + (uint32_t)((c % kSlots) * kSlotCols);
     };
     auto release = [&]() {  // the slot's accumulators are in registers
       tmem_wait_ld();
       tc_before_sync();
       __syncwarp();
-      if (lane == 0) arrive(empty + c % kSlots);
+      if (lane == 0) arrive(empty + c % kRing);
     };
-    auto layer_finished = [&]() {  // this warp's shared-memory rows are visible to the MMAs
+    auto published = [&](uint64_t* bar) {  // this warp's shared-memory rows are visible to the MMAs
       fence_async_smem();
       __syncwarp();
-      if (lane == 0) arrive(layer_done);
+      if (lane == 0) arrive(bar);
     };
-    // A hidden layer: M-tiles of rows start + 128 m into dst (BF16, 4 groups).
-    auto hidden = [&](int start, int n_mtiles, unsigned char* dst, int x0, int y0) {
-      for (int m = 0; m < n_mtiles; ++m, ++c) {
-        if (c % kEpiGroups != group || __any_sync(0xffffffffu, s_abort != 0)) continue;
-        const uint32_t t = acquire();
-        if (!ok) continue;
-        const int q = start + m * 128 + quarter * 32 + lane;  // halo row q / 32, column lane
-        const int gy = y0 - 3 + (q >> 5), gx = x0 - 3 + lane;
-        const bool inside = (q >> 5) < kHH && gy >= 0 && gy < H && gx >= 0 && gx < W;
+    // Hidden-layer M-tile m: ReLU(D + b) as BF16 into rows start + 128 m of dst
+    // (4 groups of 8 channels), zero outside the image; false after an abort.
+    auto hidden = [&](int start, int m, unsigned char* dst, int x0, int y0, bool add_bias) -> bool {
+      const uint32_t t = acquire();
+      if (!ok) return false;
+      const int q = start + m * 128 + quarter * 32 + lane;  // halo row q / 32, column lane
+      const int gy = y0 - 3 + (q >> 5), gx = x0 - 3 + lane;
+      const bool inside = (q >> 5) < kHH && gy >= 0 && gy < H && gx >= 0 && gx < W;
+      float v[32];
+      tmem_ld32(t, v);
+      release();  // waits for the load, then frees the slot for the MMA warps
+      if (add_bias) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {  // output channels 16h .. 16h + 15
-          float d0[16], d1[16], d2[16];
-          tmem_ld16(t + 0 * 32 + 16 * h, d0);
-          tmem_ld16(t + 1 * 32 + 16 * h, d1);
-          tmem_ld16(t + 2 * 32 + 16 * h, d2);
-          if (h == 1) release();  // waits for the loads, then frees the slot for the MMA warps
-          else tmem_wait_ld();
-          uint32_t w[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float v[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const int k = 2 * j + e;
-              const float left = __shfl_up_sync(0xffffffffu, d0[k], 1);     // kernel column 0 reads q - 1
-              const float right = __shfl_down_sync(0xffffffffu, d2[k], 1);  // kernel column 2 reads q + 1
-              v[e] = fmaxf(left + d1[k] + right, 0.f);  // the bias came with the MMAs
-            }
-            w[j] = inside ? pack2(v[0], v[1]) : 0u;
-          }
-          if (q < kRows) {
-            *reinterpret_cast<uint4*>(dst + (2 * h) * kGroupB + q * 16) = make_uint4(w[0], w[1], w[2], w[3]);
-            *reinterpret_cast<uint4*>(dst + (2 * h + 1) * kGroupB + q * 16) = make_uint4(w[4], w[5], w[6], w[7]);
-          }
+        for (int k = 0; k < 32; k += 4) {
+          const float4 b = *reinterpret_cast<const float4*>(bias + k);
+          v[k] += b.x;
+          v[k + 1] += b.y;
+          v[k + 2] += b.z;
+          v[k + 3] += b.w;
         }
       }
+      uint32_t w[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) w[j] = inside ? relu_pack2(v[2 * j], v[2 * j + 1]) : 0u;
+      if (q < kRows) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+          *reinterpret_cast<uint4*>(dst + g * kGroupB + q * 16) = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2],
+                                                                            w[4 * g + 3]);
+      }
+      return true;
     };
 
     for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
       int img, x0, y0;
       tile_origin(A, tile, img, x0, y0);
       const float4* in = reinterpret_cast<const float4*>(A.in) + (size_t)img * H * W;
-      // ---- x: FP32 halo (prefetched) -> BF16 group 0 of buf0, then the next halo starts
+      float4* out = reinterpret_cast<float4*>(A.out) + (size_t)img * H * W;
+      // ---- x: FP32 halo (prefetched) -> pair-packed BF16 in group 0 of buffer 0
       cp_async_wait_all();
-      epi_sync();  // every halo row landed; the previous tile's layer-3 MMAs are complete
-      for (int q = tid; q < kHH * kHW; q += kEpiThreads) {
-        const float4 v = reinterpret_cast<const float4*>(xs)[q];
-        *reinterpret_cast<uint4*>(buf0 + q * 16) = make_uint4(pack2(v.x, v.y), pack2(v.z, 1.f), 0u, 0u);
+      epi_sync();  // every halo row landed; every MMA of the previous tile is complete
+      for (int s = tid; s < kHH * kHW; s += kEpiThreads) {
+        const float4 v0 = reinterpret_cast<const float4*>(xs)[s];
+        const float4 v1 = s + 1 < kHH * kHW ? reinterpret_cast<const float4*>(xs)[s + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<uint4*>(buf0 + s * 16) =
+            make_uint4(pack2(v0.x, v0.y), pack2(v0.z, 1.f), pack2(v1.x, v1.y), pack2(v1.z, 1.f));
       }
-      layer_finished();  // layer 1 may start
-      epi_sync();        // xs is free
+      published(x_ready);  // layer 1 may start
+      epi_sync();          // xs is free
       if (tile + (int)gridDim.x < A.n_tiles) prefetch_halo(su32(xs), A, tile + gridDim.x);
 
-      hidden(kStart1, kTiles1, buf1, x0, y0);
-      layer_finished();
-      hidden(kStart2, kTiles2, buf0, x0, y0);
-      layer_finished();
-
-      // ---- layer 3 and the residual; the FP32 inputs of this warp's outputs load meanwhile.
-      // Layer-3 M-tile m has counter c + m; this group owns m = first + kEpiGroups * j.
-      const int first = (group - c % kEpiGroups + kEpiGroups) % kEpiGroups;
-      constexpr int kOwn = kTiles3 / kEpiGroups;
-      float4 xr[kOwn];
-      int oidx[kOwn];
-#pragma unroll
-      for (int j = 0; j < kOwn; ++j) {
-        const int m = first + kEpiGroups * j;
+      // ---- the tile's M-tiles in the issuers' order; group g takes those with c % 4 == g
+      const int c0 = c;
+      for (int i = (group - c0 % kEpiGroups + kEpiGroups) % kEpiGroups; i < kMTiles; i += kEpiGroups) {
+        c = c0 + i;
+        if (__any_sync(0xffffffffu, s_abort != 0)) continue;
+        const int layer = kSchedule[i] >> 4, m = kSchedule[i] & 15;
+        if (layer == 1) {
+          if (hidden(kStart1, m, buf1, x0, y0, false)) published(ready1 + m);
+          continue;
+        }
+        if (layer == 2) {
+          if (hidden(kStart2, m, buf0, x0, y0, true)) published(ready2 + m);
+          continue;
+        }
+        // layer 3 and the residual: this warp's row of the M-tile; its FP32 input loads first
         const int hy = (kStart3 >> 5) + 4 * m + quarter;
         const int gy = y0 - 3 + hy, gx = x0 - 3 + lane;
         const bool out_ok = hy < 3 + kTH && lane >= 3 && lane < 3 + kTW && gy < H && gx < W;
-        oidx[j] = out_ok ? gy * W + gx : -1;
-        xr[j] = out_ok ? in[(size_t)gy * W + gx] : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      float4* out = reinterpret_cast<float4*>(A.out) + (size_t)img * H * W;
-      const int c3 = c;  // counter of layer 3's first M-tile
-#pragma unroll
-      for (int j = 0; j < kOwn; ++j) {
-        c = c3 + first + kEpiGroups * j;
-        if (__any_sync(0xffffffffu, s_abort != 0)) continue;
+        const float4 x = out_ok ? in[(size_t)gy * W + gx] : make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t t = acquire();
         if (!ok) continue;
         float d[16];
@@ -459,12 +510,11 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
         float r[3];
 #pragma unroll
         for (int o = 0; o < 3; ++o) {
-          const float left = __shfl_up_sync(0xffffffffu, d[o], 1);
-          const float right = __shfl_down_sync(0xffffffffu, d[8 + o], 1);
-          r[o] = left + d[4 + o] + right;
+          const float left = __shfl_up_sync(0xffffffffu, d[o], 1);       // kernel column 0 reads q - 1
+          const float right = __shfl_down_sync(0xffffffffu, d[8 + o], 1);  // kernel column 2 reads q + 1
+          r[o] = left + d[4 + o] + right + bias[32 + o];
         }
-        if (oidx[j] >= 0) {
-          const float4 x = xr[j];
+        if (out_ok) {
           float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
           if (x.w > 0.f) {
             y.x = x.x + r[0];
@@ -472,10 +522,10 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
             y.z = x.z + r[2];
             y.w = 1.f;
           }
-          out[oidx[j]] = y;
+          out[(size_t)gy * W + gx] = y;
         }
       }
-      c = c3 + kTiles3;
+      c = c0 + kMTiles;
     }
     cp_async_wait_all();
   }
@@ -492,7 +542,6 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
 cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, const float* params,
                                 const __nv_bfloat16* packed, int sm_count, int32_t* error, uint64_t wait_ns,
                                 cudaStream_t s) {
-  (void)params;  // the biases are packed with the weights
   cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(refine_fused_kernel), kSmemBytes);
   if (e != cudaSuccess) return e;
   FusedArgs a;
@@ -505,6 +554,7 @@ cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in
   a.in = in;
   a.out = out;
   a.wtc = packed + kPackTc;
+  a.prm = params;
   a.error = error;
   a.wait_ns = wait_ns;
   if (a.n_tiles == 0) return cudaSuccess;
