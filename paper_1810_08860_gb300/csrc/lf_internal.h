@@ -193,7 +193,7 @@ constexpr int kRefineOffW1 = 0, kRefineOffB1 = 864, kRefineOffW2 = 896, kRefineO
 constexpr int kRefineOffW3 = 10144, kRefineOffB3 = 11008;
 // packed BF16 operands: w1f [32][32], w2f [9][32][32], w3f [9][8][32], w3b [32][32], w2b [9][32][32]
 // (mma.sync layers), then the fused kernel's B operands: L1 [3 dy][2 g][32][8] (pair-packed
-// taps), L2 [3 dy][3 dx][2 kc][2 g][32][8], L3 [3 dy][2 kc][2 g][16][8] (kernel columns along N)
+// taps), L2 [3 dy][2 kc][2 g][96][8], L3 [3 dy][2 kc][2 g][16][8] (kernel columns along N)
 constexpr int kPackW1f = 0, kPackW2f = 1024, kPackW3f = 10240, kPackW3b = 12544, kPackW2b = 13568;
 constexpr int kPackTc = 22784;
 constexpr int kRefinePackedElems = 22784 + 1536 + 9216 + 1536;

@@ -421,9 +421,9 @@ __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float*
 //   then the fused kernel's B operands, K-major groups g of 8 channels:
 //   L1 [dy][g][o][8] over the pair-packed input (x[q-1], x[q]) | (x[q+1], x[q+2]),
 //   four channels R, G, B, 1 per position: kernel column kx = 2g + (e >= 4),
-//   b1 at the constant 1 of the centre tap; L2 [dy][dx][kc][g][o][8] with input
-//   channel c = kc*16 + g*8 + e; L3 [dy][kc][g][kx*4 + o][8] (kernel columns
-//   stacked along N).  b2 and b3 are read in FP32 by the fused kernel.
+//   b1 at the constant 1 of the centre tap; L2 [dy][kc][g][kx*32 + o][8] and
+//   L3 [dy][kc][g][kx*4 + o][8] (kernel columns stacked along N) with input
+//   channel c = kc*16 + g*8 + e.  b2 and b3 are read in FP32 by the fused kernel.
 __global__ void pack_weights_kernel(const float* __restrict__ prm, __nv_bfloat16* __restrict__ w) {
   constexpr int n1 = 32 * 32, n2 = 9 * 32 * 32, n3 = 9 * 8 * 32, n3b = 32 * 32, n2b = 9 * 32 * 32;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -448,9 +448,9 @@ __global__ void pack_weights_kernel(const float* __restrict__ prm, __nv_bfloat16
     const int kx = 2 * g + (e >> 2), c = e & 3;
     if (kx < 3 && c < 3) v = prm[kRefineOffW1 + o * 27 + c * 9 + dy * 3 + kx];
     else if (kx == 1 && c == 3 && dy == 1) v = prm[kRefineOffB1 + o];  // b1 meets the constant input channel
-  } else if (i < kPackTc + 1536 + 9216) {  // L2 [dy][dx][kc][g][o][e], c = kc*16 + g*8 + e
-    const int j = i - kPackTc - 1536, dy = j / 3072, kx = (j / 1024) % 3, kc = (j / 512) & 1, g = (j / 256) & 1;
-    const int o = (j >> 3) & 31, c = kc * 16 + g * 8 + (j & 7);
+  } else if (i < kPackTc + 1536 + 9216) {  // L2 [dy][kc][g][n = kx*32 + o][e], c = kc*16 + g*8 + e
+    const int j = i - kPackTc - 1536, dy = j / 3072, kc = (j / 1536) & 1, g = (j / 768) & 1, n = (j >> 3) % 96;
+    const int c = kc * 16 + g * 8 + (j & 7), kx = n >> 5, o = n & 31;
     v = prm[kRefineOffW2 + (o * 32 + c) * 9 + dy * 3 + kx];
   } else if (i < kRefinePackedElems) {  // L3 [dy][kc][g][n = kx*4 + o][e], o < 3
     const int j = i - kPackTc - 1536 - 9216, dy = j / 512, kc = (j / 256) & 1, g = (j / 128) & 1, n = (j >> 3) & 15;

@@ -72,44 +72,63 @@ namespace {
 
 constexpr int kHW = 32, kHH = 36;            // halo tile (positions)
 constexpr int kTW = kHW - 6, kTH = kHH - 6;  // 26 x 30 output pixels
-constexpr int kRows = 1280;                  // positions held per buffer (10 x 128)
-constexpr int kGroupB = kRows * 16;          // bytes per group of 8 channels
-constexpr int kBufB = 4 * kGroupB;           // 32 channels
+// Positions held per buffer (row r of a buffer holds position base + r):
+//   x   (pair-packed layer-1 input, two buffers) read [-1, 1217), base 0
+//   a1  (buffer 1) written [32, 1184), read [31, 1121), base 32
+//   a2  (buffer 2) written [64, 1088), read [64, 1152), base 64 (rows never written stay zero)
+// A read one row before a buffer (an output column that is never used) meets
+// finite data: the weights or the previous buffer.
+constexpr int kRowsX = 1220, kRows1 = 1152, kRows2 = 1088;
+constexpr int kBase1 = 32, kBase2 = 64;
+constexpr int kGroup1B = kRows1 * 16, kGroup2B = kRows2 * 16;  // bytes per group of 8 channels
+constexpr int kXB = kRowsX * 16, kBuf1B = 4 * kGroup1B, kBuf2B = 4 * kGroup2B;
 // B operands, K-major [2 K groups][N rows][16 B]:
 //   layer 1 per kernel row ky (pair-packed taps kx = -1..+2, N = 32),
-//   layer 2 per (ky, kx, half of the 32 input channels) (N = 32),
+//   layer 2 per (ky, half of the 32 input channels) (N = 96: kx*32 + o),
 //   layer 3 per (ky, half) (N = 16: kx*4 + o).
-constexpr int kW1Blk = 2 * 32 * 16, kW2Blk = 2 * 32 * 16, kW3Blk = 2 * 16 * 16;
-constexpr int kW1B = 3 * kW1Blk, kW2B = 18 * kW2Blk, kW3B = 6 * kW3Blk;
+constexpr int kW1Blk = 2 * 32 * 16, kW2Blk = 2 * 96 * 16, kW3Blk = 2 * 16 * 16;
+constexpr int kW1B = 3 * kW1Blk, kW2B = 6 * kW2Blk, kW3B = 6 * kW3Blk;
 constexpr int kWB = kW1B + kW2B + kW3B;  // 24,576 bytes
 static_assert(kWB == 2 * (kRefinePackedElems - kPackTc), "the packed operands are the shared-memory image");
 constexpr int kXsB = kHH * kHW * 16;         // FP32 RGBA halo of the next tile
 constexpr int kBiasB = 48 * 4;               // b2[32], b3[3]
-constexpr int kSlots = 16, kSlotCols = 32;   // TMEM ring
+constexpr int kSlots = 5, kSlotCols = 96;    // TMEM ring
 constexpr int kIssuers = 4;                  // MMA warps
-constexpr int kRing = 16;                    // ring mbarriers, indexed by c % kRing
+constexpr int kRing = 20;                    // ring mbarriers, indexed by c % kRing
 constexpr int kEpiWarps = 16;                // epilogue warps: 4 groups of 4 (one warp per TMEM lane quadrant)
 constexpr int kEpiGroups = kEpiWarps / 4;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kThreads = kEpiThreads + 32 * kIssuers;
+constexpr int kLoaderWarp = kEpiWarps + kIssuers;  // stages each tile's input
+constexpr int kThreads = kEpiThreads + 32 * kIssuers + 32;
 static_assert(kRing % kSlots == 0 && kRing % kEpiGroups == 0 && kRing % kIssuers == 0 && kEpiGroups == kIssuers,
               "each ring mbarrier belongs to one slot, one epilogue group and one issuer");
 constexpr int kStart1 = 32, kTiles1 = 9;     // layer 1 rows [32, 1184): halo rows 1..36
 constexpr int kStart2 = 64, kTiles2 = 8;     // layer 2 rows [64, 1088): halo rows 2..33
 constexpr int kStart3 = 96, kTiles3 = 8;     // layer 3 rows [96, 1120): halo rows 3..34
 constexpr int kMTiles = kTiles1 + kTiles2 + kTiles3;
-// full[16], empty[16], x_ready, drain[4], ready1[9], ready2[8]
-constexpr int kNumBars = 2 * kRing + 1 + kIssuers + kTiles1 + kTiles2;
-constexpr int kSmemBytes = kWB + 2 * kBufB + kXsB + kBiasB + kNumBars * 8 + 16;
+// full[20], empty[20], x_ready[2], drain[4], ready1[9], ready2[8], done3[8], l1done[2]
+constexpr int kNumBars = 2 * kRing + 2 + kIssuers + kTiles1 + kTiles2 + kTiles3 + 2;
+constexpr int kSmemBytes = kWB + 2 * kXB + kBuf1B + kBuf2B + kXsB + kBiasB + kNumBars * 8 + 16;
+static_assert(kSmemBytes <= 227 * 1024, "fits one CTA's shared memory");
 constexpr uint32_t kTmemCols = 512;
 static_assert(kSlots * kSlotCols <= (int)kTmemCols, "the ring fits the tensor memory");
-// The order of a tile's M-tiles (layer << 4 | m): all of layer 1, then layer 2
-// with layer 3 following two layer-2 M-tiles behind.
-__device__ __constant__ const uint8_t kSchedule[kMTiles] = {
-    0x10, 0x11, 0x12, 0x13, 0x14, 0x15, 0x16, 0x17, 0x18, 0x20, 0x21, 0x22, 0x23,
-    0x30, 0x24, 0x31, 0x25, 0x32, 0x26, 0x33, 0x27, 0x34, 0x35, 0x36, 0x37};
+// A CTA's tiles run as a pipeline: period k issues layers 2 and 3 of its tile
+// k-1 together with layer 1 of its tile k (entries layer << 4 | m), so the
+// tensor core does not wait at tile boundaries.  A period issues all of layer
+// 2 first, then alternates layer 3 with the next tile's layer 1, so every
+// consumer comes at least seven M-tiles after its producers (the epilogue of
+// one M-tile takes longer than several M-tiles of tensor work); the first
+// period has only layer 1, the last no layer 1.
+constexpr int kLenFirst = kTiles1, kLenMid = kMTiles, kLenLast = kTiles2 + kTiles3;
+constexpr int kOffMid = kLenFirst, kOffLast = kLenFirst + kLenMid;
+__device__ __constant__ const uint8_t kSchedule[kLenFirst + kLenMid + kLenLast] = {
+    0x10, 0x11, 0x12, 0x13, 0x14, 0x15, 0x16, 0x17, 0x18,  // first
+    0x20, 0x21, 0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x30, 0x10, 0x31, 0x11, 0x32,
+    0x12, 0x33, 0x13, 0x34, 0x14, 0x35, 0x15, 0x36, 0x16, 0x37, 0x17, 0x18,  // middle
+    0x20, 0x21, 0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x30, 0x31, 0x32, 0x33, 0x34,
+    0x35, 0x36, 0x37};  // last
 // which wait ran out of time (bit 0: the CTA aborted)
-constexpr int kErrIssuerLayer = 2, kErrIssuerSlot = 4, kErrEpilogueFull = 8, kErrDrain = 16;
+constexpr int kErrIssuerLayer = 2, kErrIssuerSlot = 4, kErrEpilogueFull = 8, kErrDrain = 16, kErrLoader = 32;
 // The drain wait is not cut short by a small configured limit: MMAs that are
 // still running when their issuer gives up finish in microseconds, and the
 // tensor memory must not be freed under them.
@@ -180,8 +199,6 @@ __device__ __forceinline__ int wait_phase_status(uint64_t* bar, uint32_t parity,
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// Barrier among the epilogue warps only (named barrier 1).
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
   uint32_t r[16];
@@ -244,12 +261,12 @@ __device__ __forceinline__ void tile_origin(const FusedArgs& A, int tile, int& i
   x0 = (rem % A.tiles_x) * kTW;
 }
 
-// Epilogue threads start copying a tile's FP32 RGBA halo into xs (zeros outside the image).
-__device__ __forceinline__ void prefetch_halo(uint32_t xs, const FusedArgs& A, int tile) {
+// The loader warp starts copying a tile's FP32 RGBA halo into xs (zeros outside the image).
+__device__ __forceinline__ void prefetch_halo(uint32_t xs, const FusedArgs& A, int tile, int lane) {
   int img, x0, y0;
   tile_origin(A, tile, img, x0, y0);
   const float4* in = reinterpret_cast<const float4*>(A.in) + (size_t)img * A.H * A.W;
-  for (int q = threadIdx.x; q < kHH * kHW; q += kEpiThreads) {
+  for (int q = lane; q < kHH * kHW; q += 32) {
     const int gy = y0 - 3 + (q >> 5), gx = x0 - 3 + (q & 31);
     const bool ok = gy >= 0 && gy < A.H && gx >= 0 && gx < A.W;
     cp_async16(xs + q * 16, ok ? static_cast<const void*>(in + (size_t)gy * A.W + gx) : static_cast<const void*>(in),
@@ -263,27 +280,31 @@ __device__ __forceinline__ void prefetch_halo(uint32_t xs, const FusedArgs& A, i
 __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) {
   extern __shared__ __align__(1024) unsigned char sm[];
   // The weights come first: layer 1's first window reaches one position before
-  // buffer 0 (an output column that is never used) and reads finite weights there.
+  // the x buffer (an output column that is never used) and reads finite weights there.
   unsigned char* wts = sm;
-  unsigned char* buf0 = wts + kWB;   // x (pair-packed, group 0), then a2
-  unsigned char* buf1 = buf0 + kBufB;  // a1
-  unsigned char* xs = buf1 + kBufB;
+  unsigned char* xb = wts + kWB;       // x, pair-packed: tile j of this CTA in xb + (j % 2) * kXB
+  unsigned char* buf1 = xb + 2 * kXB;  // a1
+  unsigned char* buf2 = buf1 + kBuf1B;  // a2
+  unsigned char* xs = buf2 + kBuf2B;
   float* bias = reinterpret_cast<float*>(xs + kXsB);  // b2[32], b3[3]
   uint64_t* full = reinterpret_cast<uint64_t*>(xs + kXsB + kBiasB);
   uint64_t* empty = full + kRing;
-  uint64_t* x_ready = empty + kRing;  // x of the tile is in buffer 0
-  uint64_t* drain = x_ready + 1;      // one per issuer
+  uint64_t* x_ready = empty + kRing;    // x of tile j is in xb + (j % 2) * kXB: x_ready[j % 2]
+  uint64_t* drain = x_ready + 2;        // one per issuer
   uint64_t* ready1 = drain + kIssuers;  // layer-1 M-tile m is in buffer 1 (four arrivals)
-  uint64_t* ready2 = ready1 + kTiles1;  // layer-2 M-tile m is in buffer 0
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ready2 + kTiles2);
+  uint64_t* ready2 = ready1 + kTiles1;  // layer-2 M-tile m is in buffer 2
+  uint64_t* done3 = ready2 + kTiles2;   // layer-3 M-tile m has read buffer 2
+  uint64_t* l1done = done3 + kTiles3;   // every layer-1 M-tile of tile j is complete: l1done[j % 2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(l1done + 2);
   __shared__ volatile int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool issuer = warp >= kEpiWarps;
+  const bool issuer = warp >= kEpiWarps && warp < kLoaderWarp;
 
-  // Both activation buffers start at zero (rows never written stay finite),
+  // The x and activation buffers start at zero (rows never written stay finite),
   // then the weights and biases; the first tile's halo is already on its way.
-  if (!issuer && blockIdx.x < A.n_tiles) prefetch_halo(su32(xs), A, blockIdx.x);
-  for (int i = tid; i < 2 * kBufB / 16; i += kThreads) reinterpret_cast<uint4*>(buf0)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == kLoaderWarp && blockIdx.x < A.n_tiles) prefetch_halo(su32(xs), A, blockIdx.x, lane);
+  for (int i = tid; i < (2 * kXB + kBuf1B + kBuf2B) / 16; i += kThreads)
+    reinterpret_cast<uint4*>(xb)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < kWB / 16; i += kThreads)
     reinterpret_cast<uint4*>(wts)[i] = reinterpret_cast<const uint4*>(A.wtc)[i];
   if (tid < 32) bias[tid] = A.prm[kRefineOffB2 + tid];
@@ -294,10 +315,13 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(full + b)), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(empty + b)), "r"(4));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(x_ready)), "r"(kEpiWarps));
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(x_ready + b)), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(l1done + b)), "r"(4 * kTiles1));
+    }
     for (int b = 0; b < kIssuers; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(drain + b)), "r"(1));
-    for (int b = 0; b < kTiles1 + kTiles2; ++b)
+    for (int b = 0; b < kTiles1 + kTiles2 + kTiles3; ++b)  // ready1, ready2, done3: one group's four warps
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(ready1 + b)), "r"(4));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -313,6 +337,13 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
   const uint32_t tmem = *tmem_slot;
   const int H = A.H, W = A.W;
 
+  // Tiles of this CTA: blockIdx.x + j * gridDim.x, j < n_own; periods k = 0 .. n_own.
+  const int n_own = blockIdx.x < A.n_tiles ? (A.n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  auto period = [&](int k, int& off, int& len) {
+    if (k == 0) off = 0, len = kLenFirst;
+    else if (k == n_own) off = kOffLast, len = kLenLast;
+    else off = kOffMid, len = kLenMid;
+  };
   if (issuer) {
     // ------------------------------------------------------------ MMA warps (lane 0 of each)
     // Descriptors are precomputed; only their start address (in 16-byte
@@ -320,20 +351,21 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
     if (lane == 0) {
       const int me = warp - kEpiWarps;
       const uint32_t sw = su32(wts);
-      const uint64_t ax = smem_desc(su32(buf0), 32, 128);  // pair-packed x: K group 1 two positions on
-      const uint64_t a1d = smem_desc(su32(buf1), kGroupB, 128);
-      const uint64_t a2d = smem_desc(su32(buf0), kGroupB, 128);
+      // pair-packed x: K group 1 two positions on; a1, a2 descriptors address position 0
+      const uint64_t ax0 = smem_desc(su32(xb), 32, 128), ax1 = smem_desc(su32(xb) + kXB, 32, 128);
+      const uint64_t a1d = smem_desc(su32(buf1) - kBase1 * 16, kGroup1B, 128);
+      const uint64_t a2d = smem_desc(su32(buf2) - kBase2 * 16, kGroup2B, 128);
       const uint64_t b1d = smem_desc(sw, 32 * 16, 128);
-      const uint64_t b2d = smem_desc(sw + kW1B, 32 * 16, 128);
+      const uint64_t b2d = smem_desc(sw + kW1B, 96 * 16, 128);
       const uint64_t b3d = smem_desc(sw + kW1B + kW2B, 16 * 16, 128);
-      constexpr uint64_t kHalf = 2 * kGroupB / 16;  // second half of 16 channels, in 16-byte units
-      constexpr uint32_t kId32 = instr_desc(128, 32), kId16 = instr_desc(128, 16);
-      uint32_t tile_phase = 0;  // parity of this tile's phase of x_ready and the ready barriers
+      constexpr uint64_t kHalf1 = 2 * kGroup1B / 16, kHalf2 = 2 * kGroup2B / 16;  // second 16 channels
+      constexpr uint32_t kId32 = instr_desc(128, 32), kId96 = instr_desc(128, 96), kId16 = instr_desc(128, 16);
       int c = 0;
       bool ok = true;
-      auto wait_ready = [&](uint64_t* bar) {  // a barrier completed once per tile
+      // A barrier completed once per tile; parity = the tile's index in this CTA, mod 2.
+      auto wait_tile = [&](uint64_t* bar, uint32_t parity) {
         if (ok) {
-          const int w = wait_phase_status(bar, tile_phase, &s_abort, A.wait_ns);
+          const int w = wait_phase_status(bar, parity, &s_abort, A.wait_ns);
           if (w == 2) atomicOr(A.error, kErrIssuerLayer);
           ok = w == 0;
         }
@@ -349,37 +381,52 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
         tc_after_sync();
         return tmem + (uint32_t)((c % kSlots) * kSlotCols);
       };
-      for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
-        wait_ready(x_ready);
+      for (int k = 0; k <= n_own; ++k) {
+        int off, len;
+        period(k, off, len);
+        // parities of the tiles k (layer 1), k - 1 (layers 2, 3) and k - 2
+        const uint32_t pu = (uint32_t)k & 1u, pt = pu ^ 1u, pp = pu;
+        bool x_seen = false;
         const int c0 = c;
-        for (int i = (me - c0 % kIssuers + kIssuers) % kIssuers; i < kMTiles; i += kIssuers) {
+        for (int i = (me - c0 % kIssuers + kIssuers) % kIssuers; i < len; i += kIssuers) {
           c = c0 + i;
-          if (!ok) continue;
-          const int layer = kSchedule[i] >> 4, m = kSchedule[i] & 15;
-          if (layer == 2) {  // a1 rows it reads are written; x rows it overwrites are read
-            if (m > 0) wait_ready(ready1 + m - 1);
-            wait_ready(ready1 + m);
-            wait_ready(ready1 + m + 1);
-          } else if (layer == 3) {  // a2 rows it reads are written
-            wait_ready(ready2 + m);
-            if (m + 1 < kTiles2) wait_ready(ready2 + m + 1);
+          if (!ok) break;
+          const int layer = kSchedule[off + i] >> 4, m = kSchedule[off + i] & 15;
+          if (layer == 1) {
+            if (!x_seen) wait_tile(x_ready + (k & 1), (uint32_t)(k >> 1) & 1u);  // x of tile k is in its xb
+            x_seen = true;
+            // a1 rows it overwrites: layer-2 M-tiles m-1 .. m+1 of tile k-1 have read them
+            if (k > 0)
+              for (int j = m - 1; j <= m + 1; ++j)
+                if (j >= 0 && j < kTiles2) wait_tile(ready2 + j, pt);
+          } else if (layer == 2) {
+            // a1 rows it reads (layer-1 M-tiles m-1 .. m+1 of tile k-1) are written
+            for (int j = m - 1; j <= m + 1; ++j)
+              if (j >= 0) wait_tile(ready1 + j, pt);
+            // a2 rows it overwrites: layer-3 M-tiles m-1, m of tile k-2 have read them
+            if (k > 1) {
+              if (m > 0) wait_tile(done3 + m - 1, pp);
+              wait_tile(done3 + m, pp);
+            }
+          } else {  // a2 rows it reads (layer-2 M-tiles m, m+1 of tile k-1) are written
+            wait_tile(ready2 + m, pt);
+            if (m + 1 < kTiles2) wait_tile(ready2 + m + 1, pt);
           }
-          if (!ok) continue;
+          if (!ok) break;
           const uint32_t d = slot_col();
-          if (!ok) continue;
+          if (!ok) break;
           if (layer == 1) {
             // output position p = kStart1 + 128 m + r; kernel row ky starts at p + 32 (ky - 1) - 1
-            const uint64_t a = ax + (uint64_t)(int64_t)(kStart1 - 33 + 128 * m);
+            const uint64_t a = ((k & 1) ? ax1 : ax0) + (uint64_t)(int64_t)(kStart1 - 33 + 128 * m);
 #pragma unroll
             for (int ky = 0; ky < 3; ++ky) mma(d, a + 32 * ky, b1d + (uint64_t)(ky * (kW1Blk / 16)), kId32, ky > 0);
           } else if (layer == 2) {
-            const uint64_t a = a1d + (uint64_t)(kStart2 - 33 + 128 * m);
+            const uint64_t a = a1d + (uint64_t)(kStart2 - 32 + 128 * m);
 #pragma unroll
-            for (int t = 0; t < 9; ++t) {  // tap t = 3 ky + kx reads p + 32 (ky - 1) + kx - 1
+            for (int ky = 0; ky < 3; ++ky) {  // kernel row ky reads p + 32 (ky - 1); columns along N
 #pragma unroll
               for (int h = 0; h < 2; ++h)
-                mma(d, a + 32 * (t / 3) + (t % 3) + h * kHalf, b2d + (uint64_t)((2 * t + h) * (kW2Blk / 16)), kId32,
-                    t > 0 || h > 0);
+                mma(d, a + 32 * ky + h * kHalf1, b2d + (uint64_t)((2 * ky + h) * (kW2Blk / 16)), kId96, ky > 0 || h > 0);
             }
           } else {
             const uint64_t a = a2d + (uint64_t)(kStart3 - 32 + 128 * m);
@@ -387,13 +434,13 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
             for (int ky = 0; ky < 3; ++ky) {
 #pragma unroll
               for (int h = 0; h < 2; ++h)
-                mma(d, a + 32 * ky + h * kHalf, b3d + (uint64_t)((2 * ky + h) * (kW3Blk / 16)), kId16, ky > 0 || h > 0);
+                mma(d, a + 32 * ky + h * kHalf2, b3d + (uint64_t)((2 * ky + h) * (kW3Blk / 16)), kId16, ky > 0 || h > 0);
             }
           }
           commit(full + c % kRing);
         }
-        c = c0 + kMTiles;
-        tile_phase ^= 1u;
+        c = c0 + len;
+        if (!ok) break;
       }
       if (!ok) s_abort = 1;
       // Drain: the commit arrives once every MMA this thread issued has completed.
@@ -403,6 +450,41 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       if (wait_phase_status(drain + me, 0u, nullptr, A.wait_ns > kDrainNs ? A.wait_ns : kDrainNs) == 2)
         atomicOr(A.error, kErrDrain);
     }
+  } else if (warp == kLoaderWarp) {
+    // ---------------------------------------------------------------- input loader
+    // Tile j's FP32 halo (already streaming into xs) -> pair-packed BF16 in
+    // xb + (j % 2) * kXB, once that buffer's last reader, layer 1 of tile
+    // j - 2, is complete; then tile j + 1's halo starts streaming into xs.
+    bool ok = true;
+    for (int j = 0; j < n_own && ok; ++j) {
+      if (j >= 2) {
+        int got = 1;
+        if (lane == 0) {
+          const int w = wait_phase_status(l1done + (j & 1), (uint32_t)((j - 2) >> 1) & 1u, &s_abort, A.wait_ns);
+          if (w == 2) atomicOr(A.error, kErrLoader);
+          got = w == 0;
+        }
+        ok = __shfl_sync(0xffffffffu, got, 0) != 0;
+        if (!ok) {
+          s_abort = 1;
+          break;
+        }
+      }
+      cp_async_wait_all();
+      __syncwarp();  // every lane's copies landed
+      unsigned char* dst = xb + (j & 1) * kXB;
+      for (int q = lane; q < kHH * kHW; q += 32) {
+        const float4 v0 = reinterpret_cast<const float4*>(xs)[q];
+        const float4 v1 = q + 1 < kHH * kHW ? reinterpret_cast<const float4*>(xs)[q + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<uint4*>(dst + q * 16) =
+            make_uint4(pack2(v0.x, v0.y), pack2(v0.z, 1.f), pack2(v1.x, v1.y), pack2(v1.z, 1.f));
+      }
+      fence_async_smem();  // the rows are visible to the MMAs
+      __syncwarp();        // and every lane has read xs
+      if (lane == 0) arrive(x_ready + (j & 1));  // layer 1 of tile j may start
+      if (j + 1 < n_own) prefetch_halo(su32(xs), A, blockIdx.x + (j + 1) * gridDim.x, lane);
+    }
+    cp_async_wait_all();
   } else {
     // ---------------------------------------------------------------- epilogue warps
     const int quarter = warp & 3, group = warp >> 2;  // group g takes the M-tiles with c % kEpiGroups == g
@@ -432,81 +514,105 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       __syncwarp();
       if (lane == 0) arrive(bar);
     };
-    // Hidden-layer M-tile m: ReLU(D + b) as BF16 into rows start + 128 m of dst
-    // (4 groups of 8 channels), zero outside the image; false after an abort.
-    auto hidden = [&](int start, int m, unsigned char* dst, int x0, int y0, bool add_bias) -> bool {
+    // Hidden-layer M-tile m as BF16 into rows start + 128 m of dst (4 groups of
+    // 8 channels, group_b bytes apart), zero outside the image; false after an
+    // abort.  Layer 1 (full windows): ReLU(D).  Layer 2 (kernel columns along
+    // N): ReLU(D[q-1][o] + D[q][32 + o] + D[q+1][64 + o] + b2[o]), the
+    // neighbouring positions taken from the neighbouring lanes (columns 0 and
+    // 31 of the halo get a wrong neighbour; they are never used).
+    auto hidden = [&](int start, int m, unsigned char* dst, int base, int group_b, int rows, int x0, int y0,
+                      bool stacked) -> bool {
       const uint32_t t = acquire();
       if (!ok) return false;
       const int q = start + m * 128 + quarter * 32 + lane;  // halo row q / 32, column lane
       const int gy = y0 - 3 + (q >> 5), gx = x0 - 3 + lane;
       const bool inside = (q >> 5) < kHH && gy >= 0 && gy < H && gx >= 0 && gx < W;
-      float v[32];
-      tmem_ld32(t, v);
-      release();  // waits for the load, then frees the slot for the MMA warps
-      if (add_bias) {
+      unsigned char* row = dst + (q - base) * 16;
+      const bool keep = q - base < rows;
+      if (!stacked) {
+        float v[32];
+        tmem_ld32(t, v);
+        release();  // waits for the load, then frees the slot for the MMA warps
+        uint32_t w[16];
 #pragma unroll
-        for (int k = 0; k < 32; k += 4) {
-          const float4 b = *reinterpret_cast<const float4*>(bias + k);
-          v[k] += b.x;
-          v[k + 1] += b.y;
-          v[k + 2] += b.z;
-          v[k + 3] += b.w;
+        for (int j = 0; j < 16; ++j) w[j] = inside ? relu_pack2(v[2 * j], v[2 * j + 1]) : 0u;
+        if (keep) {
+#pragma unroll
+          for (int g = 0; g < 4; ++g)
+            *reinterpret_cast<uint4*>(row + g * group_b) = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
         }
+        return true;
       }
-      uint32_t w[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) w[j] = inside ? relu_pack2(v[2 * j], v[2 * j + 1]) : 0u;
-      if (q < kRows) {
+      for (int h = 0; h < 2; ++h) {  // output channels 16h .. 16h + 15
+        float d0[16], d1[16], d2[16];
+        tmem_ld16(t + 0 * 32 + 16 * h, d0);
+        tmem_ld16(t + 1 * 32 + 16 * h, d1);
+        tmem_ld16(t + 2 * 32 + 16 * h, d2);
+        if (h == 1) release();  // waits for the loads, then frees the slot for the MMA warps
+        else tmem_wait_ld();
+        uint32_t w[8];
 #pragma unroll
-        for (int g = 0; g < 4; ++g)
-          *reinterpret_cast<uint4*>(dst + g * kGroupB + q * 16) = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2],
-                                                                            w[4 * g + 3]);
+        for (int j = 0; j < 8; ++j) {
+          float v[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int k = 2 * j + e;
+            const float left = __shfl_up_sync(0xffffffffu, d0[k], 1);     // kernel column 0 reads q - 1
+            const float right = __shfl_down_sync(0xffffffffu, d2[k], 1);  // kernel column 2 reads q + 1
+            v[e] = left + d1[k] + right + bias[16 * h + k];
+          }
+          w[j] = inside ? relu_pack2(v[0], v[1]) : 0u;
+        }
+        if (keep) {
+          *reinterpret_cast<uint4*>(row + (2 * h) * group_b) = make_uint4(w[0], w[1], w[2], w[3]);
+          *reinterpret_cast<uint4*>(row + (2 * h + 1) * group_b) = make_uint4(w[4], w[5], w[6], w[7]);
+        }
       }
       return true;
     };
 
-    for (int tile = blockIdx.x; tile < A.n_tiles; tile += gridDim.x) {
-      int img, x0, y0;
-      tile_origin(A, tile, img, x0, y0);
-      const float4* in = reinterpret_cast<const float4*>(A.in) + (size_t)img * H * W;
+    for (int k = 0; k <= n_own; ++k) {
+      int off, len;
+      period(k, off, len);
+      int ux0 = 0, uy0 = 0, tx0 = 0, ty0 = 0, img = 0;
+      if (k > 0) tile_origin(A, blockIdx.x + (k - 1) * gridDim.x, img, tx0, ty0);
+      const float4* in = reinterpret_cast<const float4*>(A.in) + (size_t)img * H * W;  // tile k - 1
       float4* out = reinterpret_cast<float4*>(A.out) + (size_t)img * H * W;
-      // ---- x: FP32 halo (prefetched) -> pair-packed BF16 in group 0 of buffer 0
-      cp_async_wait_all();
-      epi_sync();  // every halo row landed; every MMA of the previous tile is complete
-      for (int s = tid; s < kHH * kHW; s += kEpiThreads) {
-        const float4 v0 = reinterpret_cast<const float4*>(xs)[s];
-        const float4 v1 = s + 1 < kHH * kHW ? reinterpret_cast<const float4*>(xs)[s + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-        *reinterpret_cast<uint4*>(buf0 + s * 16) =
-            make_uint4(pack2(v0.x, v0.y), pack2(v0.z, 1.f), pack2(v1.x, v1.y), pack2(v1.z, 1.f));
+      if (k < n_own) {
+        int uimg;
+        tile_origin(A, blockIdx.x + k * gridDim.x, uimg, ux0, uy0);
       }
-      published(x_ready);  // layer 1 may start
-      epi_sync();          // xs is free
-      if (tile + (int)gridDim.x < A.n_tiles) prefetch_halo(su32(xs), A, tile + gridDim.x);
 
-      // ---- the tile's M-tiles in the issuers' order; group g takes those with c % 4 == g
+      // ---- the period's M-tiles in the issuers' order; group g takes those with c % 4 == g
       const int c0 = c;
-      for (int i = (group - c0 % kEpiGroups + kEpiGroups) % kEpiGroups; i < kMTiles; i += kEpiGroups) {
+      for (int i = (group - c0 % kEpiGroups + kEpiGroups) % kEpiGroups; i < len && ok; i += kEpiGroups) {
         c = c0 + i;
-        if (__any_sync(0xffffffffu, s_abort != 0)) continue;
-        const int layer = kSchedule[i] >> 4, m = kSchedule[i] & 15;
+        if (__any_sync(0xffffffffu, s_abort != 0)) break;
+        const int layer = kSchedule[off + i] >> 4, m = kSchedule[off + i] & 15;
         if (layer == 1) {
-          if (hidden(kStart1, m, buf1, x0, y0, false)) published(ready1 + m);
+          if (hidden(kStart1, m, buf1, kBase1, kGroup1B, kRows1, ux0, uy0, false)) {
+            published(ready1 + m);
+            if (lane == 0) arrive(l1done + (k & 1));  // its MMAs (readers of x) are complete
+          }
           continue;
         }
         if (layer == 2) {
-          if (hidden(kStart2, m, buf0, x0, y0, true)) published(ready2 + m);
+          if (hidden(kStart2, m, buf2, kBase2, kGroup2B, kRows2, tx0, ty0, true)) published(ready2 + m);
           continue;
         }
-        // layer 3 and the residual: this warp's row of the M-tile; its FP32 input loads first
+        // layer 3 of tile k-1 and the residual: this warp's row of the M-tile; its FP32 input loads first
         const int hy = (kStart3 >> 5) + 4 * m + quarter;
-        const int gy = y0 - 3 + hy, gx = x0 - 3 + lane;
+        const int gy = ty0 - 3 + hy, gx = tx0 - 3 + lane;
         const bool out_ok = hy < 3 + kTH && lane >= 3 && lane < 3 + kTW && gy < H && gx < W;
         const float4 x = out_ok ? in[(size_t)gy * W + gx] : make_float4(0.f, 0.f, 0.f, 0.f);
         const uint32_t t = acquire();
-        if (!ok) continue;
+        if (!ok) break;
         float d[16];
         tmem_ld16(t, d);
         release();
+        __syncwarp();
+        if (lane == 0) arrive(done3 + m);  // its MMAs (the readers of buffer 2) are complete
         float r[3];
 #pragma unroll
         for (int o = 0; o < 3; ++o) {
@@ -525,9 +631,8 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
           out[(size_t)gy * W + gx] = y;
         }
       }
-      c = c0 + kMTiles;
+      c = c0 + len;
     }
-    cp_async_wait_all();
   }
 
   tc_before_sync();
