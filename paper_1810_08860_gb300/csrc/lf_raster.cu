@@ -288,24 +288,26 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
         S.cc[lane] = *reinterpret_cast<const float4*>(VR.cc);
         S.inv_r[lane] = VR.inv_r;
       }
-      S.tex[lane] = VR.tex;
-      int b0 = 0, bn = 0, g0 = 0, gn = 0;
-      if (VR.bin_off >= 0) {
-        const int lx = tx - VR.btx0, ly = ty - VR.bty0;
-        if (lx >= 0 && lx < VR.bntx && ly >= 0 && ly < VR.bnty) {
-          const int* offs = A.bin_offsets + VR.bin_off + ly * VR.bntx + lx;
-          b0 = offs[0];
-          bn = offs[1] - b0;
+      if constexpr (!SELECT) {  // the disk tests alone need only the disk
+        S.tex[lane] = VR.tex;
+        int b0 = 0, bn = 0, g0 = 0, gn = 0;
+        if (VR.bin_off >= 0) {
+          const int lx = tx - VR.btx0, ly = ty - VR.bty0;
+          if (lx >= 0 && lx < VR.bntx && ly >= 0 && ly < VR.bnty) {
+            const int* offs = A.bin_offsets + VR.bin_off + ly * VR.bntx + lx;
+            b0 = offs[0];
+            bn = offs[1] - b0;
+          }
+          g0 = VR.big_base;
+          gn = VR.big_count;
         }
-        g0 = VR.big_base;
-        gn = VR.big_count;
-      }
-      S.bstart[lane] = b0;
-      S.bcount[lane] = bn;
-      S.gbase[lane] = g0;
-      S.gcount[lane] = gn;
+        S.bstart[lane] = b0;
+        S.bcount[lane] = bn;
+        S.gbase[lane] = g0;
+        S.gcount[lane] = gn;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) S.Hm[lane][k] = VR.Hm[k];
+        for (int k = 0; k < 12; ++k) S.Hm[lane][k] = VR.Hm[k];
+      }
     }
     __syncwarp();
     // ---- disk membership of each pixel's sphere crossing, one bit per view
