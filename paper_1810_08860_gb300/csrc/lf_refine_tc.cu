@@ -105,7 +105,6 @@ static_assert(kRing % kSlots == 0 && kRing % kEpiGroups == 0 && kRing % kIssuers
 constexpr int kStart1 = 32, kTiles1 = 9;     // layer 1 rows [32, 1184): halo rows 1..36
 constexpr int kStart2 = 64, kTiles2 = 8;     // layer 2 rows [64, 1088): halo rows 2..33
 constexpr int kStart3 = 96, kTiles3 = 8;     // layer 3 rows [96, 1120): halo rows 3..34
-constexpr int kMTiles = kTiles1 + kTiles2 + kTiles3;
 // full[20], empty[20], x_ready[2], drain[4], ready1[9], ready2[8], done3[8], l1done[2]
 constexpr int kNumBars = 2 * kRing + 2 + kIssuers + kTiles1 + kTiles2 + kTiles3 + 2;
 constexpr int kSmemBytes = kWB + 2 * kXB + kBuf1B + kBuf2B + kXsB + kBiasB + kNumBars * 8 + 16;
@@ -114,19 +113,20 @@ constexpr uint32_t kTmemCols = 512;
 static_assert(kSlots * kSlotCols <= (int)kTmemCols, "the ring fits the tensor memory");
 // A CTA's tiles run as a pipeline: period k issues layers 2 and 3 of its tile
 // k-1 together with layer 1 of its tile k (entries layer << 4 | m), so the
-// tensor core does not wait at tile boundaries.  A period issues all of layer
-// 2 first, then alternates layer 3 with the next tile's layer 1, so every
+// tensor core does not wait at tile boundaries.  An entry (code << 4 | m)
+// holds the layer in the code's low two bits and the count of M-tiles less one
+// above them: layer 1 runs in triples (three 32-column accumulators fill a
+// slot) and layer 3 in pairs, so the ring's per-entry handshakes are shared.  A period issues all of layer 2 first, then alternates layer 3
+// with the next tile's layer 1, so every
 // consumer comes at least seven M-tiles after its producers (the epilogue of
 // one M-tile takes longer than several M-tiles of tensor work); the first
 // period has only layer 1, the last no layer 1.
-constexpr int kLenFirst = kTiles1, kLenMid = kMTiles, kLenLast = kTiles2 + kTiles3;
+constexpr int kLenFirst = 3, kLenMid = 15, kLenLast = 12;
 constexpr int kOffMid = kLenFirst, kOffLast = kLenFirst + kLenMid;
 __device__ __constant__ const uint8_t kSchedule[kLenFirst + kLenMid + kLenLast] = {
-    0x10, 0x11, 0x12, 0x13, 0x14, 0x15, 0x16, 0x17, 0x18,  // first
-    0x20, 0x21, 0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x30, 0x10, 0x31, 0x11, 0x32,
-    0x12, 0x33, 0x13, 0x34, 0x14, 0x35, 0x15, 0x36, 0x16, 0x37, 0x17, 0x18,  // middle
-    0x20, 0x21, 0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x30, 0x31, 0x32, 0x33, 0x34,
-    0x35, 0x36, 0x37};  // last
+    0x90, 0x93, 0x96,  // first
+    0x20, 0x21, 0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x70, 0x90, 0x72, 0x93, 0x74, 0x96, 0x76,  // middle
+    0x20, 0x21, 0x22, 0x23, 0x24, 0x25, 0x26, 0x27, 0x70, 0x72, 0x74, 0x76};  // last
 // which wait ran out of time (bit 0: the CTA aborted)
 constexpr int kErrIssuerLayer = 2, kErrIssuerSlot = 4, kErrEpilogueFull = 8, kErrDrain = 16, kErrLoader = 32;
 // The drain wait is not cut short by a small configured limit: MMAs that are
@@ -391,13 +391,14 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
         for (int i = (me - c0 % kIssuers + kIssuers) % kIssuers; i < len; i += kIssuers) {
           c = c0 + i;
           if (!ok) break;
-          const int layer = kSchedule[off + i] >> 4, m = kSchedule[off + i] & 15;
+          const int code = kSchedule[off + i] >> 4, m = kSchedule[off + i] & 15;
+          const int layer = code & 3, cnt = 1 + (code >> 2);  // M-tiles m .. m + cnt - 1
           if (layer == 1) {
             if (!x_seen) wait_tile(x_ready + (k & 1), (uint32_t)(k >> 1) & 1u);  // x of tile k is in its xb
             x_seen = true;
-            // a1 rows it overwrites: layer-2 M-tiles m-1 .. m+1 of tile k-1 have read them
+            // a1 rows it overwrites: layer-2 M-tiles m-1 .. m+cnt of tile k-1 have read them
             if (k > 0)
-              for (int j = m - 1; j <= m + 1; ++j)
+              for (int j = m - 1; j <= m + cnt; ++j)
                 if (j >= 0 && j < kTiles2) wait_tile(ready2 + j, pt);
           } else if (layer == 2) {
             // a1 rows it reads (layer-1 M-tiles m-1 .. m+1 of tile k-1) are written
@@ -408,9 +409,9 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
               if (m > 0) wait_tile(done3 + m - 1, pp);
               wait_tile(done3 + m, pp);
             }
-          } else {  // a2 rows it reads (layer-2 M-tiles m, m+1 of tile k-1) are written
-            wait_tile(ready2 + m, pt);
-            if (m + 1 < kTiles2) wait_tile(ready2 + m + 1, pt);
+          } else {  // a2 rows it reads (layer-2 M-tiles m .. m+cnt of tile k-1) are written
+            for (int j = m; j <= m + cnt; ++j)
+              if (j < kTiles2) wait_tile(ready2 + j, pt);
           }
           if (!ok) break;
           const uint32_t d = slot_col();
@@ -418,8 +419,11 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
           if (layer == 1) {
             // output position p = kStart1 + 128 m + r; kernel row ky starts at p + 32 (ky - 1) - 1
             const uint64_t a = ((k & 1) ? ax1 : ax0) + (uint64_t)(int64_t)(kStart1 - 33 + 128 * m);
+            for (int s = 0; s < cnt; ++s) {  // M-tile m + s into columns 32 s ..
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) mma(d, a + 32 * ky, b1d + (uint64_t)(ky * (kW1Blk / 16)), kId32, ky > 0);
+              for (int ky = 0; ky < 3; ++ky)
+                mma(d + 32 * s, a + 128 * s + 32 * ky, b1d + (uint64_t)(ky * (kW1Blk / 16)), kId32, ky > 0);
+            }
           } else if (layer == 2) {
             const uint64_t a = a1d + (uint64_t)(kStart2 - 32 + 128 * m);
 #pragma unroll
@@ -430,11 +434,14 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
             }
           } else {
             const uint64_t a = a2d + (uint64_t)(kStart3 - 32 + 128 * m);
+            for (int s = 0; s < cnt; ++s) {  // M-tile m + s into columns 16 s ..
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
+              for (int ky = 0; ky < 3; ++ky) {
 #pragma unroll
-              for (int h = 0; h < 2; ++h)
-                mma(d, a + 32 * ky + h * kHalf2, b3d + (uint64_t)((2 * ky + h) * (kW3Blk / 16)), kId16, ky > 0 || h > 0);
+                for (int h = 0; h < 2; ++h)
+                  mma(d + 16 * s, a + 128 * s + 32 * ky + h * kHalf2, b3d + (uint64_t)((2 * ky + h) * (kW3Blk / 16)),
+                      kId16, ky > 0 || h > 0);
+              }
             }
           }
           commit(full + c % kRing);
@@ -514,16 +521,15 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       __syncwarp();
       if (lane == 0) arrive(bar);
     };
-    // Hidden-layer M-tile m as BF16 into rows start + 128 m of dst (4 groups of
-    // 8 channels, group_b bytes apart), zero outside the image; false after an
-    // abort.  Layer 1 (full windows): ReLU(D).  Layer 2 (kernel columns along
+    // Hidden-layer M-tile m, accumulators at TMEM address t, as BF16 into rows
+    // start + 128 m of dst (4 groups of 8 channels, group_b bytes apart), zero
+    // outside the image; the slot is released after the loads when `last`.
+    // Layer 1 (full windows): ReLU(D).  Layer 2 (kernel columns along
     // N): ReLU(D[q-1][o] + D[q][32 + o] + D[q+1][64 + o] + b2[o]), the
     // neighbouring positions taken from the neighbouring lanes (columns 0 and
     // 31 of the halo get a wrong neighbour; they are never used).
-    auto hidden = [&](int start, int m, unsigned char* dst, int base, int group_b, int rows, int x0, int y0,
-                      bool stacked) -> bool {
-      const uint32_t t = acquire();
-      if (!ok) return false;
+    auto hidden = [&](uint32_t t, int start, int m, unsigned char* dst, int base, int group_b, int rows, int x0,
+                      int y0, bool stacked, bool last) {
       const int q = start + m * 128 + quarter * 32 + lane;  // halo row q / 32, column lane
       const int gy = y0 - 3 + (q >> 5), gx = x0 - 3 + lane;
       const bool inside = (q >> 5) < kHH && gy >= 0 && gy < H && gx >= 0 && gx < W;
@@ -532,7 +538,8 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       if (!stacked) {
         float v[32];
         tmem_ld32(t, v);
-        release();  // waits for the load, then frees the slot for the MMA warps
+        if (last) release();  // waits for the load, then frees the slot for the MMA warps
+        else tmem_wait_ld();
         uint32_t w[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) w[j] = inside ? relu_pack2(v[2 * j], v[2 * j + 1]) : 0u;
@@ -541,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
           for (int g = 0; g < 4; ++g)
             *reinterpret_cast<uint4*>(row + g * group_b) = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
         }
-        return true;
+        return;
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {  // output channels 16h .. 16h + 15
@@ -569,7 +576,6 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
           *reinterpret_cast<uint4*>(row + (2 * h + 1) * group_b) = make_uint4(w[4], w[5], w[6], w[7]);
         }
       }
-      return true;
     };
 
     for (int k = 0; k <= n_own; ++k) {
@@ -589,46 +595,66 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       for (int i = (group - c0 % kEpiGroups + kEpiGroups) % kEpiGroups; i < len && ok; i += kEpiGroups) {
         c = c0 + i;
         if (__any_sync(0xffffffffu, s_abort != 0)) break;
-        const int layer = kSchedule[off + i] >> 4, m = kSchedule[off + i] & 15;
+        const int code = kSchedule[off + i] >> 4, m = kSchedule[off + i] & 15;
+        const int layer = code & 3, cnt = 1 + (code >> 2);  // M-tiles m .. m + cnt - 1, one slot
         if (layer == 1) {
-          if (hidden(kStart1, m, buf1, kBase1, kGroup1B, kRows1, ux0, uy0, false)) {
-            published(ready1 + m);
+          const uint32_t t = acquire();
+          if (!ok) break;
+          for (int s = 0; s < cnt; ++s) {
+            hidden(t + 32 * s, kStart1, m + s, buf1, kBase1, kGroup1B, kRows1, ux0, uy0, false, s + 1 == cnt);
+            published(ready1 + m + s);
             if (lane == 0) arrive(l1done + (k & 1));  // its MMAs (readers of x) are complete
           }
           continue;
         }
         if (layer == 2) {
-          if (hidden(kStart2, m, buf2, kBase2, kGroup2B, kRows2, tx0, ty0, true)) published(ready2 + m);
+          const uint32_t t = acquire();
+          if (!ok) break;
+          hidden(t, kStart2, m, buf2, kBase2, kGroup2B, kRows2, tx0, ty0, true, true);
+          published(ready2 + m);
           continue;
         }
-        // layer 3 of tile k-1 and the residual: this warp's row of the M-tile; its FP32 input loads first
-        const int hy = (kStart3 >> 5) + 4 * m + quarter;
-        const int gy = ty0 - 3 + hy, gx = tx0 - 3 + lane;
-        const bool out_ok = hy < 3 + kTH && lane >= 3 && lane < 3 + kTW && gy < H && gx < W;
-        const float4 x = out_ok ? in[(size_t)gy * W + gx] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // layer 3 of tile k-1 and the residual: this warp's rows of the entry's
+        // M-tiles; their FP32 inputs load first
+        float4 x[2];
+        int pix[2];
+        for (int s = 0; s < 2; ++s) {
+          const int hy = (kStart3 >> 5) + 4 * (m + s) + quarter;
+          const int gy = ty0 - 3 + hy, gx = tx0 - 3 + lane;
+          const bool out_ok = s < cnt && hy < 3 + kTH && lane >= 3 && lane < 3 + kTW && gy < H && gx < W;
+          pix[s] = out_ok ? gy * W + gx : -1;
+          x[s] = out_ok ? in[(size_t)gy * W + gx] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         const uint32_t t = acquire();
         if (!ok) break;
-        float d[16];
-        tmem_ld16(t, d);
-        release();
-        __syncwarp();
-        if (lane == 0) arrive(done3 + m);  // its MMAs (the readers of buffer 2) are complete
-        float r[3];
-#pragma unroll
-        for (int o = 0; o < 3; ++o) {
-          const float left = __shfl_up_sync(0xffffffffu, d[o], 1);       // kernel column 0 reads q - 1
-          const float right = __shfl_down_sync(0xffffffffu, d[8 + o], 1);  // kernel column 2 reads q + 1
-          r[o] = left + d[4 + o] + right + bias[32 + o];
-        }
-        if (out_ok) {
-          float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (x.w > 0.f) {
-            y.x = x.x + r[0];
-            y.y = x.y + r[1];
-            y.z = x.z + r[2];
-            y.w = 1.f;
+        for (int s = 0; s < cnt; ++s) {
+          float d[16];
+          tmem_ld16(t + 16 * s, d);
+          if (s + 1 == cnt) {
+            release();
+            __syncwarp();
+            if (lane == 0)
+              for (int j = 0; j < cnt; ++j) arrive(done3 + m + j);  // their MMAs (the readers of buffer 2) are complete
+          } else {
+            tmem_wait_ld();
           }
-          out[(size_t)gy * W + gx] = y;
+          float r[3];
+#pragma unroll
+          for (int o = 0; o < 3; ++o) {
+            const float left = __shfl_up_sync(0xffffffffu, d[o], 1);       // kernel column 0 reads q - 1
+            const float right = __shfl_down_sync(0xffffffffu, d[8 + o], 1);  // kernel column 2 reads q + 1
+            r[o] = left + d[4 + o] + right + bias[32 + o];
+          }
+          if (pix[s] >= 0) {
+            float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (x[s].w > 0.f) {
+              y.x = x[s].x + r[0];
+              y.y = x[s].y + r[1];
+              y.z = x[s].z + r[2];
+              y.w = 1.f;
+            }
+            out[pix[s]] = y;
+          }
         }
       }
       c = c0 + len;
