@@ -359,7 +359,7 @@ LF_API lf_status lf_tune_batch(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes,
 
 typedef enum {
   LF_REFINE_FUSED_TC = 0,    /* one kernel, all three layers per tile, tcgen05 MMAs into TMEM */
-  LF_REFINE_MMA_LAYERS = 1   /* three launches (one per layer), mma.sync, hidden maps in HBM */
+  LF_REFINE_MMA_LAYERS = 1   /* three launches (one per layer), tcgen05, hidden maps in HBM */
 } lf_refine_kernel;
 
 /* Load refinement weights (copied; the caller keeps `params`).  Resets the

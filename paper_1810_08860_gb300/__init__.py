@@ -495,7 +495,7 @@ class Renderer:
         self._check(self.lib.lf_load_refiner(self.ctx, p.ctypes.data_as(ctypes.c_void_p)), "lf_load_refiner")
 
     def set_refine_kernel(self, kind: str):
-        """'fused' (one tcgen05 kernel per tile) or 'layers' (three mma.sync launches)."""
+        """'fused' (one tcgen05 kernel per tile) or 'layers' (three tcgen05 launches, one per layer)."""
         self._check(self.lib.lf_refine_set_kernel(self.ctx, REFINE_KERNELS[kind]), "lf_refine_set_kernel")
 
     def set_levels(self, n_fine: int, n_pages: int):

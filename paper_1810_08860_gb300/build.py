@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblf.so")
-SOURCES = ["lf_api.cu", "lf_setup.cu", "lf_raster.cu", "lf_refine.cu", "lf_refine_tc.cu", "lf_prefilter.cu", "lf_cache.cu"]
+SOURCES = ["lf_api.cu", "lf_setup.cu", "lf_raster.cu", "lf_refine.cu", "lf_refine_tc.cu", "lf_refine_conv_tc.cu", "lf_prefilter.cu", "lf_cache.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -1121,31 +1121,33 @@ lf_status refine_hidden(lf_ctx* c, int64_t n_pix, bool training) {
   return LF_OK;
 }
 
-RefineConvArgs conv_args(int32_t n, int32_t w, int32_t h) {
+RefineConvArgs conv_args(lf_ctx* c, int32_t n, int32_t w, int32_t h) {
   RefineConvArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = n;
   a.W = w;
   a.H = h;
+  a.error = reinterpret_cast<int32_t*>(static_cast<char*>(c->rf.scal.p) + 8);  // read by lf_get_refiner
+  a.wait_ns = (uint64_t)c->cfg.wait_limit;
   return a;
 }
 
-// The three layer launches of the mma.sync path (inference).
+// The three layer launches of the per-layer path (inference).
 lf_status refine_layers(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float* in, float* out, cudaStream_t s) {
   const float* prm = rf_params(c);
-  RefineConvArgs a = conv_args(n, w, h);
+  RefineConvArgs a = conv_args(c, n, w, h);
   a.src_f = in;
   a.wt = rf_w(c, kPackW1f);
   a.bias = prm + kRefineOffB1;
   a.out_h = static_cast<__nv_bfloat16*>(c->rf.a1.p);
   LF_CUDA(c, launch_refine_conv(kConvInRGBA, 32, kEpiRelu, a, s));
-  a = conv_args(n, w, h);
+  a = conv_args(c, n, w, h);
   a.src_h = static_cast<const __nv_bfloat16*>(c->rf.a1.p);
   a.wt = rf_w(c, kPackW2f);
   a.bias = prm + kRefineOffB2;
   a.out_h = static_cast<__nv_bfloat16*>(c->rf.a2.p);
   LF_CUDA(c, launch_refine_conv(kConvInBF16, 32, kEpiRelu, a, s));
-  a = conv_args(n, w, h);
+  a = conv_args(c, n, w, h);
   a.src_h = static_cast<const __nv_bfloat16*>(c->rf.a2.p);
   a.wt = rf_w(c, kPackW3f);
   a.bias = prm + kRefineOffB3;
@@ -1176,7 +1178,7 @@ lf_status refine_backward(lf_ctx* c, int32_t n, int32_t w, int32_t h, const floa
   if (st != LF_OK) return st;
   const int tiles_x = (w + 31) / 32, tiles_y = (h + 7) / 8;
   const int n_tiles = tiles_x * tiles_y * n;
-  const int n_ctas = std::max(1, std::min(n_tiles, 2 * c->sm_count));
+  const int n_ctas = std::max(1, std::min(n_tiles, 3 * c->sm_count));  // weight-gradient CTAs: three per SM
   LF_CUDA(c, ensure(c->rf.partial, sizeof(float) * (size_t)n_ctas * (896 + 9248 + 867)));
   float* loss = static_cast<float*>(c->rf.scal.p);
   int32_t* count = reinterpret_cast<int32_t*>(loss + 1);
@@ -1189,13 +1191,13 @@ lf_status refine_backward(lf_ctx* c, int32_t n, int32_t w, int32_t h, const floa
   auto* a2 = static_cast<__nv_bfloat16*>(c->rf.a2.p);  // later dL/dz1
   auto* gz2 = static_cast<__nv_bfloat16*>(c->rf.gz2.p);
   float* gr = static_cast<float*>(c->rf.gr.p);
-  RefineConvArgs a = conv_args(n, w, h);
+  RefineConvArgs a = conv_args(c, n, w, h);
   a.src_f = in; a.wt = rf_w(c, kPackW1f); a.bias = prm + kRefineOffB1; a.out_h = a1;
   LF_CUDA(c, launch_refine_conv(kConvInRGBA, 32, kEpiRelu, a, s));
-  a = conv_args(n, w, h);
+  a = conv_args(c, n, w, h);
   a.src_h = a1; a.wt = rf_w(c, kPackW2f); a.bias = prm + kRefineOffB2; a.out_h = a2;
   LF_CUDA(c, launch_refine_conv(kConvInBF16, 32, kEpiRelu, a, s));
-  a = conv_args(n, w, h);
+  a = conv_args(c, n, w, h);
   a.src_h = a2; a.wt = rf_w(c, kPackW3f); a.bias = prm + kRefineOffB3; a.x = in; a.target = tgt; a.out_f = gr;
   a.loss = loss; a.count = count;
   LF_CUDA(c, launch_refine_conv(kConvInBF16, 8, kEpiLoss, a, s));
@@ -1203,6 +1205,8 @@ lf_status refine_backward(lf_ctx* c, int32_t n, int32_t w, int32_t h, const floa
   RefineWgradArgs g;
   std::memset(&g, 0, sizeof(g));
   g.n = n; g.W = w; g.H = h; g.tiles_x = tiles_x; g.tiles_y = tiles_y; g.n_tiles = n_tiles; g.n_ctas = n_ctas;
+  g.error = reinterpret_cast<int32_t*>(static_cast<char*>(c->rf.scal.p) + 8);
+  g.wait_ns = (uint64_t)c->cfg.wait_limit;
   float* part = static_cast<float*>(c->rf.partial.p);
   float* part1 = part;
   float* part2 = part1 + (size_t)n_ctas * kRefineSegs[0];
@@ -1210,11 +1214,11 @@ lf_status refine_backward(lf_ctx* c, int32_t n, int32_t w, int32_t h, const floa
   // layer 3 weights (dL/dr with a2), then dL/dz2 through layer 3's input
   g.g_f = gr; g.a_h = a2; g.partial = part3;
   LF_CUDA(c, launch_refine_wgrad(3, g, s));
-  a = conv_args(n, w, h);
+  a = conv_args(c, n, w, h);
   a.src_f = gr; a.wt = rf_w(c, kPackW3b); a.mask = a2; a.out_h = gz2;
   LF_CUDA(c, launch_refine_conv(kConvInRGBA, 32, kEpiMask, a, s));
   // dL/dz1 through layer 2's input (into a2's buffer, no longer needed)
-  a = conv_args(n, w, h);
+  a = conv_args(c, n, w, h);
   a.src_h = gz2; a.wt = rf_w(c, kPackW2b); a.mask = a1; a.out_h = a2;
   LF_CUDA(c, launch_refine_conv(kConvInBF16, 32, kEpiMask, a, s));
   g.g_f = nullptr; g.g_h = gz2; g.a_h = a1; g.partial = part2;
@@ -1276,7 +1280,7 @@ lf_status lf_get_refiner(lf_ctx* c, float* params, float* grad, float* adam_m, f
   LF_CUDA(c, cudaMemcpy(&err, static_cast<char*>(c->rf.scal.p) + 8, sizeof(err), cudaMemcpyDeviceToHost));
   if (err) {
     char msg[96];
-    std::snprintf(msg, sizeof(msg), "a wait of the fused refinement kernel gave up (error word 0x%x)", (unsigned)err);
+    std::snprintf(msg, sizeof(msg), "a wait of a refinement kernel gave up (error word 0x%x)", (unsigned)err);
     return fail(c, LF_ERR_TIMEOUT, msg);
   }
   return LF_OK;

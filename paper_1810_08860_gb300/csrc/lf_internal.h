@@ -192,7 +192,7 @@ constexpr int kRefineParams = 11011;  // W1 864, b1 32, W2 9216, b2 32, W3 864, 
 constexpr int kRefineOffW1 = 0, kRefineOffB1 = 864, kRefineOffW2 = 896, kRefineOffB2 = 10112;
 constexpr int kRefineOffW3 = 10144, kRefineOffB3 = 11008;
 // packed BF16 operands: w1f [32][32], w2f [9][32][32], w3f [9][8][32], w3b [32][32], w2b [9][32][32]
-// (mma.sync layers), then the fused kernel's B operands: L1 [3 dy][2 g][32][8] (pair-packed
+// (the per-layer convolutions, rearranged by them into core-matrix blocks), then the fused kernel's B operands: L1 [3 dy][2 g][32][8] (pair-packed
 // taps), L2 [3 dy][2 kc][2 g][96][8], L3 [3 dy][2 kc][2 g][16][8] (kernel columns along N)
 constexpr int kPackW1f = 0, kPackW2f = 1024, kPackW3f = 10240, kPackW3b = 12544, kPackW2b = 13568;
 constexpr int kPackTc = 22784;
@@ -214,6 +214,8 @@ struct RefineConvArgs {
   float* out_f;                // kEpiResid: refined RGBA; kEpiLoss: dL/dr (RGB, a = 0)
   float* loss;                 // kEpiLoss: += sum of squared errors / (3 N)
   const int32_t* count;        // kEpiLoss: N, pixels valid in input and target
+  int32_t* error;              // set (bit 6) if the wait for a tile's MMAs gave up
+  uint64_t wait_ns;            // bound on that wait
 };
 
 struct RefineWgradArgs {
@@ -224,6 +226,8 @@ struct RefineWgradArgs {
   const __nv_bfloat16* a_h;    // modes 2, 3: the layer input (32 channels)
   const float* x;              // mode 1: the network input RGBA
   float* partial;              // [n_ctas][segment]
+  int32_t* error;              // set (bit 8) if a wait for a chunk's MMAs gave up
+  uint64_t wait_ns;            // bound on that wait
 };
 
 cudaError_t launch_refine_conv(int in_mode, int cout, int epi, const RefineConvArgs& a, cudaStream_t s);
