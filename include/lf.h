@@ -369,15 +369,17 @@ typedef enum {
 LF_API lf_status lf_load_refiner(lf_ctx* ctx, const float* params);
 
 /* Choose the inference kernel of lf_refine and lf_render_refined (default
- * LF_REFINE_MMA_LAYERS).  Training always uses the per-layer kernels. */
+ * LF_REFINE_MMA_LAYERS).  Training always uses the per-layer kernels.  The
+ * fused kernel reads its input through a TMA tensor map: with it, `in_rgba`
+ * must be 16-byte aligned (LF_ERR_INVALID_ARG otherwise). */
 LF_API lf_status lf_refine_set_kernel(lf_ctx* ctx, lf_refine_kernel kernel);
 
 /* Copy the refiner state to host arrays of LF_REFINE_N_PARAMS floats (any may
  * be NULL): FP32 master weights, the gradient of the last lf_refine_gradients
  * or lf_refine_train_step call, the Adam moments; the Adam step count and the
  * last loss.  Synchronises the device.  LF_ERR_STATE if no refiner is loaded;
- * LF_ERR_TIMEOUT if a wait inside the fused kernel gave up since the refiner
- * was loaded (its outputs are then incomplete). */
+ * LF_ERR_TIMEOUT if a wait inside a refinement kernel gave up since the
+ * refiner was loaded (its outputs are then incomplete). */
 LF_API lf_status lf_get_refiner(lf_ctx* ctx, float* params, float* grad, float* adam_m, float* adam_v,
                                 int32_t* step, float* last_loss);
 

@@ -166,6 +166,9 @@ struct Layout {
   std::vector<EyeParams> eyes;
 };
 
+// RGBA images are read and written as 16-byte texels.
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 lf_status make_layout(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
                       float* const* out, Layout& L) {
   if (n_eyes < 1 || n_eyes > c->cfg.max_eyes) return fail(c, LF_ERR_INVALID_ARG, "n_eyes out of range");
@@ -178,6 +181,7 @@ lf_status make_layout(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, const lf_i
       return fail(c, LF_ERR_INVALID_ARG, "eye size out of range");
     if (!(K.fx > 0) || !(K.fy > 0)) return fail(c, LF_ERR_INVALID_ARG, "focal length must be positive");
     if (!out[e]) return fail(c, LF_ERR_INVALID_ARG, "null output pointer");
+    if (!aligned16(out[e])) return fail(c, LF_ERR_INVALID_ARG, "output images must be 16-byte aligned (RGBA texels)");
     EyeParams& P = L.eyes[e];
     std::memset(&P, 0, sizeof(P));
     std::memcpy(P.R, eyes[e].R, sizeof(P.R));
@@ -1034,6 +1038,7 @@ extern "C" lf_status lf_render_static(lf_ctx* c, const lf_pose* eye, const lf_in
   if (c->G > kStaticMaxGrid) return fail(c, LF_ERR_CAPACITY, "lf_render_static: mesh grid larger than 33 x 33");
   // the one eye, checked as lf_render checks it, built without any allocation
   if (!eye || !intr || !out_rgba) return fail(c, LF_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(out_rgba)) return fail(c, LF_ERR_INVALID_ARG, "the output image must be 16-byte aligned (RGBA texels)");
   const lf_intrinsics& K = *intr;
   if (K.width < 1 || K.height < 1 || K.width > 32767 || K.height > 32767)
     return fail(c, LF_ERR_INVALID_ARG, "eye size out of range");
@@ -1105,6 +1110,7 @@ lf_status refine_check(lf_ctx* c, int32_t n, int32_t w, int32_t h, const void* a
   if (n < 0 || w < 0 || h < 0 || (int64_t)w * h > ((int64_t)1 << 28) || (int64_t)n * w * h > ((int64_t)1 << 30))
     return fail(c, LF_ERR_INVALID_ARG, "bad image sizes");
   if ((int64_t)n * w * h > 0 && (!a || !b)) return fail(c, LF_ERR_INVALID_ARG, "null image pointer");
+  if (!aligned16(a) || !aligned16(b)) return fail(c, LF_ERR_INVALID_ARG, "images must be 16-byte aligned (RGBA texels)");
   cudaError_t e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
   return LF_OK;
@@ -1160,6 +1166,8 @@ lf_status refine_layers(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float*
 lf_status refine_apply(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float* in, float* out, cudaStream_t s) {
   if ((int64_t)n * w * h == 0) return LF_OK;
   if (c->rf.kernel == LF_REFINE_FUSED_TC) {
+    if (reinterpret_cast<uintptr_t>(in) & 15u)  // the fused kernel reads the input through a TMA tensor map
+      return fail(c, LF_ERR_INVALID_ARG, "the fused refinement needs a 16-byte aligned input");
     int32_t* err = reinterpret_cast<int32_t*>(static_cast<char*>(c->rf.scal.p) + 8);
     LF_CUDA(c, launch_refine_fused(n, w, h, in, out, rf_params(c), static_cast<const __nv_bfloat16*>(c->rf.packed.p),
                                    c->sm_count, err, (uint64_t)c->cfg.wait_limit, s));
@@ -1325,6 +1333,9 @@ lf_status lf_render_refined(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, cons
   if (!c->rf.loaded) return lf_render(c, n_eyes, eyes, intr, out_rgba, stream);  // the plain method
   if (n_eyes < 1 || n_eyes > c->cfg.max_eyes || !eyes || !intr || !out_rgba)
     return fail(c, LF_ERR_INVALID_ARG, "bad eye arguments");
+  for (int e = 0; e < n_eyes; ++e)
+    if (!out_rgba[e] || !aligned16(out_rgba[e]))
+      return fail(c, LF_ERR_INVALID_ARG, "output images must be non-null and 16-byte aligned (RGBA texels)");
   size_t total = 0;
   std::vector<size_t> off(n_eyes);
   for (int e = 0; e < n_eyes; ++e) {
@@ -1586,6 +1597,7 @@ extern "C" lf_status lf_prefilter(lf_ctx* c, lf_ctx* dense, int32_t first_view, 
   if (first_view < 0 || n_views < 0 || (int64_t)first_view + n_views > c->n_views)
     return fail(c, LF_ERR_INVALID_ARG, "view range out of bounds");
   if (!samples || (n_views > 0 && !out_rgba)) return fail(c, LF_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(out_rgba)) return fail(c, LF_ERR_INVALID_ARG, "the output images must be 16-byte aligned (RGBA texels)");
   if (supersample < 1 || supersample > 4 || (int64_t)supersample * std::max(c->src_w, c->src_h) > 32767)
     return fail(c, LF_ERR_INVALID_ARG, "supersample must be 1 .. 4 with renders up to 32767 pixels");
   for (int j = 0; j < n_samples; ++j)

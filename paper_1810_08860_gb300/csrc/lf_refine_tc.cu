@@ -47,8 +47,9 @@
 // boundary every group has taken all 25 M-tiles (so every MMA of the tile is
 // complete) before the next tile's input overwrites buffer 0.
 //
-// The next tile's FP32 halo streams into a staging buffer with cp.async while
-// the current tile computes; the residual add uses FP32 inputs loaded into
+// The next tile's FP32 halo streams into a staging buffer with one tiled TMA
+// copy (cp.async.bulk.tensor over a tensor map of the input, zeros outside the
+// image) while the current tile computes; the residual add uses FP32 inputs loaded into
 // registers before layer 3's accumulators are read.  Every wait is bounded
 // (%globaltimer) and reports through an error flag instead of hanging; at the
 // end each issuer commits to its own "drain" mbarrier and waits for it, so no
@@ -58,6 +59,7 @@
 // (row) holds 8 channels in 16 contiguous bytes, rows follow every 16 bytes
 // (8-row core matrices 128 bytes apart), and each further group of 8 channels
 // starts kGroupB bytes later (layer 1's input: 32 bytes later, see above).
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is reached through the runtime)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -105,8 +107,8 @@ static_assert(kRing % kSlots == 0 && kRing % kEpiGroups == 0 && kRing % kIssuers
 constexpr int kStart1 = 32, kTiles1 = 9;     // layer 1 rows [32, 1184): halo rows 1..36
 constexpr int kStart2 = 64, kTiles2 = 8;     // layer 2 rows [64, 1088): halo rows 2..33
 constexpr int kStart3 = 96, kTiles3 = 8;     // layer 3 rows [96, 1120): halo rows 3..34
-// full[20], empty[20], x_ready[2], drain[4], ready1[9], ready2[8], done3[8], l1done[2]
-constexpr int kNumBars = 2 * kRing + 2 + kIssuers + kTiles1 + kTiles2 + kTiles3 + 2;
+// full[20], empty[20], x_ready[2], drain[4], ready1[9], ready2[8], done3[8], l1done[2], xs_full
+constexpr int kNumBars = 2 * kRing + 2 + kIssuers + kTiles1 + kTiles2 + kTiles3 + 2 + 1;
 constexpr int kSmemBytes = kWB + 2 * kXB + kBuf1B + kBuf2B + kXsB + kBiasB + kNumBars * 8 + 16;
 static_assert(kSmemBytes <= 227 * 1024, "fits one CTA's shared memory");
 constexpr uint32_t kTmemCols = 512;
@@ -237,11 +239,6 @@ __device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
   return r;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 struct FusedArgs {
   int32_t n, H, W, tiles_x, tiles_y, n_tiles;
@@ -261,23 +258,25 @@ __device__ __forceinline__ void tile_origin(const FusedArgs& A, int tile, int& i
   x0 = (rem % A.tiles_x) * kTW;
 }
 
-// The loader warp starts copying a tile's FP32 RGBA halo into xs (zeros outside the image).
-__device__ __forceinline__ void prefetch_halo(uint32_t xs, const FusedArgs& A, int tile, int lane) {
+// The loader's lane 0 starts the tiled TMA copy of a tile's FP32 RGBA halo
+// (4 channels x 32 positions x 36 rows of the tensor map over the input; zeros
+// where the box leaves the image) into xs; it completes on xs_full with its
+// byte count.  The loader's earlier reads of xs are ordered before the copy.
+__device__ __forceinline__ void load_halo(const CUtensorMap* tmap, uint32_t xs, uint64_t* xs_full, const FusedArgs& A,
+                                          int tile) {
   int img, x0, y0;
   tile_origin(A, tile, img, x0, y0);
-  const float4* in = reinterpret_cast<const float4*>(A.in) + (size_t)img * A.H * A.W;
-  for (int q = lane; q < kHH * kHW; q += 32) {
-    const int gy = y0 - 3 + (q >> 5), gx = x0 - 3 + (q & 31);
-    const bool ok = gy >= 0 && gy < A.H && gx >= 0 && gx < A.W;
-    cp_async16(xs + q * 16, ok ? static_cast<const void*>(in + (size_t)gy * A.W + gx) : static_cast<const void*>(in),
-               ok ? 16u : 0u);
-  }
-  cp_async_commit();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(xs_full)), "r"(kXsB) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
+          "r"(xs), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(x0 - 3), "r"(y0 - 3), "r"(img), "r"(su32(xs_full))
+      : "memory");
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) {
+__global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) unsigned char sm[];
   // The weights come first: layer 1's first window reaches one position before
   // the x buffer (an output column that is never used) and reads finite weights there.
@@ -295,14 +294,14 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
   uint64_t* ready2 = ready1 + kTiles1;  // layer-2 M-tile m is in buffer 2
   uint64_t* done3 = ready2 + kTiles2;   // layer-3 M-tile m has read buffer 2
   uint64_t* l1done = done3 + kTiles3;   // every layer-1 M-tile of tile j is complete: l1done[j % 2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(l1done + 2);
+  uint64_t* xs_full = l1done + 2;       // the TMA copy of a tile's halo landed in xs
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xs_full + 1);
   __shared__ volatile int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool issuer = warp >= kEpiWarps && warp < kLoaderWarp;
 
   // The x and activation buffers start at zero (rows never written stay finite),
   // then the weights and biases; the first tile's halo is already on its way.
-  if (warp == kLoaderWarp && blockIdx.x < A.n_tiles) prefetch_halo(su32(xs), A, blockIdx.x, lane);
   for (int i = tid; i < (2 * kXB + kBuf1B + kBuf2B) / 16; i += kThreads)
     reinterpret_cast<uint4*>(xb)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < kWB / 16; i += kThreads)
@@ -319,6 +318,7 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(x_ready + b)), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(l1done + b)), "r"(4 * kTiles1));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(xs_full)), "r"(1));
     for (int b = 0; b < kIssuers; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(drain + b)), "r"(1));
     for (int b = 0; b < kTiles1 + kTiles2 + kTiles3; ++b)  // ready1, ready2, done3: one group's four warps
@@ -459,10 +459,15 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
     }
   } else if (warp == kLoaderWarp) {
     // ---------------------------------------------------------------- input loader
-    // Tile j's FP32 halo (already streaming into xs) -> pair-packed BF16 in
+    // Tile j's FP32 halo (a TMA copy into xs) -> pair-packed BF16 in
     // xb + (j % 2) * kXB, once that buffer's last reader, layer 1 of tile
     // j - 2, is complete; then tile j + 1's halo starts streaming into xs.
     bool ok = true;
+    int pending = -1;  // the tile whose copy into xs was issued and not yet waited for
+    if (n_own > 0) {
+      if (lane == 0) load_halo(&tmap, su32(xs), xs_full, A, blockIdx.x);
+      pending = 0;
+    }
     for (int j = 0; j < n_own && ok; ++j) {
       if (j >= 2) {
         int got = 1;
@@ -477,8 +482,18 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
           break;
         }
       }
-      cp_async_wait_all();
-      __syncwarp();  // every lane's copies landed
+      int landed = 1;
+      if (lane == 0) {
+        const int w = wait_phase_status(xs_full, (uint32_t)j & 1u, &s_abort, A.wait_ns);
+        if (w == 2) atomicOr(A.error, kErrLoader);
+        landed = w == 0;
+      }
+      ok = __shfl_sync(0xffffffffu, landed, 0) != 0;
+      if (!ok) {
+        s_abort = 1;
+        break;
+      }
+      pending = -1;
       unsigned char* dst = xb + (j & 1) * kXB;
       for (int q = lane; q < kHH * kHW; q += 32) {
         const float4 v0 = reinterpret_cast<const float4*>(xs)[q];
@@ -489,9 +504,15 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
       fence_async_smem();  // the rows are visible to the MMAs
       __syncwarp();        // and every lane has read xs
       if (lane == 0) arrive(x_ready + (j & 1));  // layer 1 of tile j may start
-      if (j + 1 < n_own) prefetch_halo(su32(xs), A, blockIdx.x + (j + 1) * gridDim.x, lane);
+      if (j + 1 < n_own) {
+        if (lane == 0) load_halo(&tmap, su32(xs), xs_full, A, blockIdx.x + (j + 1) * gridDim.x);
+        pending = j + 1;
+      }
     }
-    cp_async_wait_all();
+    // after an abort, a copy still in flight lands before the CTA can leave
+    if (lane == 0 && pending >= 0 &&
+        wait_phase_status(xs_full, (uint32_t)pending & 1u, nullptr, A.wait_ns > kDrainNs ? A.wait_ns : kDrainNs) == 2)
+      atomicOr(A.error, kErrDrain);
   } else {
     // ---------------------------------------------------------------- epilogue warps
     const int quarter = warp & 3, group = warp >> 2;  // group g takes the M-tiles with c % kEpiGroups == g
@@ -670,6 +691,27 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A) 
   }
 }
 
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, reached through the runtime (no link against libcuda).
+EncodeTiled encode_tiled() {
+  static const EncodeTiled fn = []() -> EncodeTiled {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+}  // namespace
+
 cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, const float* params,
                                 const __nv_bfloat16* packed, int sm_count, int32_t* error, uint64_t wait_ns,
                                 cudaStream_t s) {
@@ -689,8 +731,22 @@ cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in
   a.error = error;
   a.wait_ns = wait_ns;
   if (a.n_tiles == 0) return cudaSuccess;
+  // The input as a 4-D tensor (4 channels, W, H, n) for the halo copies: a 16-byte aligned base,
+  // row and image strides of W * 16 and W * H * 16 bytes.
+  if ((reinterpret_cast<uintptr_t>(in) & 15u) != 0) return cudaErrorInvalidValue;
+  const EncodeTiled enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tmap;
+  const cuuint64_t dims[4] = {4, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+  const cuuint64_t strides[3] = {16, (cuuint64_t)w * 16, (cuuint64_t)w * h * 16};
+  const cuuint32_t box[4] = {4, (cuuint32_t)kHW, (cuuint32_t)kHH, 1};
+  const cuuint32_t step[4] = {1, 1, 1, 1};
+  if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(in), dims, strides, box, step,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   const int grid = a.n_tiles < sm_count ? a.n_tiles : sm_count;
-  refine_fused_kernel<<<grid, kThreads, kSmemBytes, s>>>(a);
+  refine_fused_kernel<<<grid, kThreads, kSmemBytes, s>>>(a, tmap);
   return cudaGetLastError();
 }
 

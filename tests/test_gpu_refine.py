@@ -360,3 +360,60 @@ def test_training_on_method_generated_pairs_gains_over_the_plain_render(lfmod):
         assert gain > 0.4, (kernel, base, gain)
     rf.get_refiner()
     rf.close()
+
+
+def test_refinement_rejects_misaligned_images(lfmod):
+    """The kernels read and write RGBA as 16-byte texels (the fused kernel's
+    input through a TMA tensor map): an image 4 bytes off a 16-byte boundary is
+    refused before any launch (LF_ERR_INVALID_ARG), for both kernels and for
+    training, and the context keeps working."""
+    import torch
+
+    rng = np.random.default_rng(12)
+    params = _params(lfmod, 6)
+    img = _smooth_image(rng, 40, 52)
+    flat = torch.zeros(img.size + 1, dtype=torch.float32, device="cuda")
+    flat[1:] = torch.from_numpy(img.reshape(-1)).cuda()
+    x = flat[1:].view(1, 40, 52, 4)  # 4 bytes past an aligned base
+    assert x.data_ptr() % 16 == 4
+    r = lfmod.Renderer(0)
+    r.load_refiner(params)
+    for kernel in ("fused", "layers"):
+        r.set_refine_kernel(kernel)
+        with pytest.raises(lfmod.LFError) as info:
+            r.refine(x)
+        assert info.value.status == 1  # LF_ERR_INVALID_ARG
+        y = r.refine(x.clone()).cpu().numpy()
+        _check_forward(list(y), [img], params)
+    with pytest.raises(lfmod.LFError) as info:
+        r.refine_train_step(x, x.clone(), 1e-3)
+    assert info.value.status == 1
+    assert r.get_refiner()["step"] == 0
+
+
+def test_training_wait_that_runs_out_reports_timeout_and_leaves_the_context_usable(lfmod):
+    """The tcgen05 training kernels bound their waits by the same limit: with
+    1 ns a training step's first wait for a tile's MMAs gives up, the kernels
+    return (the CTA drains its MMAs before freeing tensor memory), and
+    lf_get_refiner reports LF_ERR_TIMEOUT; with the default limit restored
+    the same context trains again."""
+    import torch
+
+    rng = np.random.default_rng(13)
+    params = _params(lfmod, 7)
+    x = torch.from_numpy(np.stack([_smooth_image(rng, 64, 80) for _ in range(2)])).cuda()
+    t = x.clone()
+    t[..., :3] = (t[..., :3] * 0.9 + 0.05).clamp(0, 1)
+    r = lfmod.Renderer(0)
+    r.load_refiner(params)
+    r.set_wait_limit(1)
+    r.refine_train_step(x, t, 1e-3)
+    torch.cuda.synchronize()
+    with pytest.raises(lfmod.LFError) as info:
+        r.get_refiner()
+    assert info.value.status == 5  # LF_ERR_TIMEOUT
+    r.set_wait_limit(0)
+    r.load_refiner(params)
+    r.refine_train_step(x, t, 1e-3)
+    st = r.get_refiner()
+    assert st["step"] == 1 and np.isfinite(st["loss"]) and st["loss"] > 0
