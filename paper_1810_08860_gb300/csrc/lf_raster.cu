@@ -353,13 +353,16 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
     const int T = S.off[32];
 
     int cur = -1;
-    int best_id[kPx], wcount[kPx], next_emit[kPx];
-    float best_iz[kPx];
+    // Depth winner per pixel as one key: the bits of 1/z (> 0, so they order as
+    // unsigned integers) above 0x7fffffff - id, so the largest key is the
+    // nearest fragment and equal depths go to the lower id.  0: none yet.
+    uint64_t best_key[kPx];
+    int wcount[kPx], next_emit[kPx];
     int n_cover[kPx], min_id[kPx], max_id[kPx];
     uint32_t hash[kPx];
 #pragma unroll
     for (int q = 0; q < kPx; ++q) {
-      best_id[q] = -1; best_iz[q] = 0.0f; wcount[q] = 0; next_emit[q] = 0;
+      best_key[q] = 0; wcount[q] = 0; next_emit[q] = 0;
       n_cover[q] = 0; min_id[q] = 0x7fffffff; max_id[q] = -1; hash[q] = 0u;
     }
     auto shade_flush = [&]() {
@@ -427,12 +430,13 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
           if constexpr (INSPECT) {
             for (int sl = next_emit[q]; sl < cur; ++sl)
               if ((inmask[q] >> sl) & 1u) emit(q, sl, 0, -1, 0, 0, 0u);
-            emit(q, cur, n_cover[q], best_id[q], min_id[q], max_id[q], hash[q]);
+            emit(q, cur, n_cover[q], best_key[q] ? 0x7fffffff - (int)(uint32_t)best_key[q] : -1, min_id[q], max_id[q],
+                 hash[q]);
             next_emit[q] = cur + 1;
           }
-          if (best_id[q] >= 0) {
+          if (best_key[q]) {
             S.wslot[wcount[q]][q][lane] = (uint8_t)cur;
-            S.wiz[wcount[q]][q][lane] = best_iz[q];
+            S.wiz[wcount[q]][q][lane] = __uint_as_float((uint32_t)(best_key[q] >> 32));
             full |= (++wcount[q] == kWinnerBuf);
           }
         }
@@ -521,8 +525,7 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
           cur = tsl;
 #pragma unroll
           for (int q = 0; q < kPx; ++q) {
-            best_id[q] = -1;
-            best_iz[q] = 0.0f;
+            best_key[q] = 0;
             if constexpr (INSPECT) {
               n_cover[q] = 0; min_id[q] = 0x7fffffff; max_id[q] = -1; hash[q] = 0u;
             }
@@ -563,9 +566,9 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
           }
           const float iz = __fmaf_rn(ia, ex, __fmaf_rn(ib, ey[q], ic));
           // nearest wins; equal depths go to the lower id, whatever the visiting order
-          if (iz > 0.0f && (best_id[q] < 0 || iz > best_iz[q] || (iz == best_iz[q] && id < best_id[q]))) {
-            best_iz[q] = iz;
-            best_id[q] = id;
+          if (iz > 0.0f) {
+            const uint64_t key = ((uint64_t)__float_as_uint(iz) << 32) | (uint32_t)(0x7fffffff - id);
+            if (key > best_key[q]) best_key[q] = key;
           }
         }
       }
