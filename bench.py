@@ -45,8 +45,8 @@ def parse_args():
                         "work so the clock sampler sees the load")
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["rig", "rig256", "tiny", "batch", "learned", "refine", "prefilter",
-                                          "twolevel"],
+    p.add_argument("--workload", choices=["rig", "rig256", "tiny", "batch", "learned", "refine", "train",
+                                          "prefilter", "twolevel"],
                    default="rig")
     p.add_argument("--samples", type=int, default=32, help="prefilter: Monte Carlo samples per pixel (Eq. 5)")
     p.add_argument("--supersample", type=int, default=1, help="prefilter: scale of the Lbar renders")
@@ -591,6 +591,10 @@ def run_batch(args):
 
 
 REFINE_FLOP_PER_PX = 2 * (27 * 32 + 288 * 32 + 288 * 3)  # 21,888: the three convolutions' multiply-adds x 2
+# A training step per pixel: the forward pass, dL/d(input) of layers 3 and 2 (layer 1's is not needed),
+# and the three layers' weight gradients, as multiply-adds x 2 (63,936).
+TRAIN_FLOP_PER_PX = 2 * ((27 * 32 + 288 * 32 + 288 * 3) + (27 * 32 + 288 * 32) + (27 * 32 + 288 * 32 + 288 * 3))
+TRAIN_LAUNCHES_PER_STEP = 13  # count, 3 convolutions, 3 weight gradients, 2 backward convolutions, 3 reductions, Adam, pack
 
 
 def measured_tensor_peak():
@@ -699,7 +703,7 @@ def run_refine(args):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": ncu_traffic(REFINE_PROFILE, REFINE_SOURCES) if args.refine_kernel == "fused" else None,
-                     "kernel": "refine_fused_kernel" if args.refine_kernel == "fused" else "conv_mma_kernel x3",
+                     "kernel": "refine_fused_kernel" if args.refine_kernel == "fused" else "conv_tc_kernel x3",
                      "peak_source": peak_kind + " bf16 (burst)", "flop_per_pixel": REFINE_FLOP_PER_PX},
         "e2e": {"value": whole_job_rate(px, e2e_ms, world), "unit": UNIT, "h2d_bytes_per_step": px * 16,
                 "d2h_bytes_per_step": px * 16,
@@ -707,6 +711,100 @@ def run_refine(args):
                         "host memory; events around all three, one step at a time"},
         "gpu_launches": (1 if args.refine_kernel == "fused" else 3) * args.steps,
         "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    r.close()
+    finish_dist(world)
+    return 0
+
+
+def run_train(args):
+    """One training step of the refinement (lf_refine_train_step: forward, loss,
+    backward, weight gradients, Adam) on a batch of 16 synthetic 256^2 crops and
+    targets (smooth colour fields, 2 % holes; the target a perturbed copy), the
+    batch shape of the learned workload's training."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    init_dist(world)
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_08860_gb300 as lfm
+
+    n, h, w = 16, 256, 256
+    rng = np.random.default_rng(7 + rank)
+    yy, xx = np.mgrid[0:h, 0:w].astype(np.float32)
+    imgs = np.zeros((n, h, w, 4), np.float32)
+    for k in range(n):
+        for c in range(3):
+            imgs[k, ..., c] = 0.5 + 0.3 * np.sin(rng.uniform(0.02, 0.3) * xx + rng.uniform(0.02, 0.3) * yy)
+        imgs[k, ..., 3] = (rng.uniform(size=(h, w)) > 0.02).astype(np.float32)
+    imgs[..., :3] *= imgs[..., 3:4]
+    tgt = imgs.copy()
+    tgt[..., :3] = np.clip(tgt[..., :3] * 0.9 + 0.05 * np.sin(0.05 * xx)[None, ..., None], 0, 1) * tgt[..., 3:4]
+    x = torch.from_numpy(imgs).cuda()
+    t = torch.from_numpy(tgt).cuda()
+    r = lfm.Renderer(local)
+    r.load_refiner(lfm.init_refiner_params(3, out_scale=0.1))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        r.refine_train_step(x, t, 1e-3)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        r.refine_train_step(x, t, 1e-3)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    # end to end: the batch from pinned host memory, the step, the refiner state
+    # (weights, gradient, moments, step, loss) read back by lf_get_refiner
+    hx, ht = x.cpu().pin_memory(), t.cpu().pin_memory()
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(max(3, args.steps // 4))]
+    for a, b in e2e_ev:
+        flush.zero_()
+        a.record(stream)
+        x.copy_(hx, non_blocking=True)
+        t.copy_(ht, non_blocking=True)
+        r.refine_train_step(x, t, 1e-3)
+        st = r.get_refiner()
+        b.record(stream)
+    torch.cuda.synchronize()
+    assert np.isfinite(st["loss"])
+    ms = [a.elapsed_time(b) for a, b in ev]
+    px = n * h * w
+    mean = max_over_ranks(sum(ms)) / len(ms)
+    e2e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in e2e_ev)) / len(e2e_ev)
+    peak, peak_kind = measured_tensor_peak()
+    achieved = TRAIN_FLOP_PER_PX * px / (mean / 1000.0) / 1e12
+    result = {
+        "metric": "training pixels/s of the learned refinement (Mpix/s), % of the BF16 tensor roofline",
+        "value": whole_job_rate(px, mean, world), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "refinement training step: batch of 16 RGBA crops 256x256 with targets, "
+                               "forward, loss, backward, weight gradients, Adam",
+                   "l2": "flushed (256 MiB write) between steps, outside the timed events"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "conv_tc_kernel x5 + wgrad_tc_kernel x3 (one step)",
+                     "peak_source": peak_kind + " bf16 (burst)", "flop_per_pixel": TRAIN_FLOP_PER_PX},
+        "e2e": {"value": whole_job_rate(px, e2e_ms, world), "unit": UNIT, "h2d_bytes_per_step": 2 * px * 16,
+                "d2h_bytes_per_step": 4 * 4 * 11011 + 8,
+                "what": "the batch and targets copied from pinned host memory, one training step, the refiner "
+                        "state read back (lf_get_refiner); events around all of it, one step at a time"},
+        "gpu_launches": TRAIN_LAUNCHES_PER_STEP * args.steps,
+        "clocks": clk,
+        "loss": float(st["loss"]),
     }
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -1561,6 +1659,8 @@ def main():
         return run_prefilter(args)
     if args.workload == "refine":
         return run_refine(args)
+    if args.workload == "train":
+        return run_train(args)
     if args.workload == "twolevel":
         return run_twolevel(args)
     return run_ours(args)

@@ -121,12 +121,6 @@ __global__ void pack_weights_kernel(const float* __restrict__ prm, __nv_bfloat16
 
 // ------------------------------------------------------------------ launchers
 
-namespace {
-
-}  // namespace
-
-
-
 cudaError_t launch_refine_reduce(const float* partial, int n_rows, int seg, float* grad, cudaStream_t s) {
   reduce_partials_kernel<<<(seg + 31) / 32, 256, 0, s>>>(partial, n_rows, seg, grad);
   return cudaGetLastError();
