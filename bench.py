@@ -580,7 +580,7 @@ def run_batch(args):
                      "peak_source": peak_kind + " (HBM copy)", "algorithmic_bytes_per_launch": raster_bytes,
                      "unique_texels_per_step": uniq, "ms_per_launch": mean_raster},
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
     if rank == 0:
@@ -926,7 +926,7 @@ def run_prefilter(args):
         "e2e": {"value": whole_job_rate(texels, e2e_ms, world), "unit": "Mtexel/s", "h2d_bytes_per_step": 16 * J,
                 "d2h_bytes_per_step": texels * 16,
                 "what": "lf_prefilter from host samples plus the prefiltered block copied to pinned host memory"},
-        "gpu_launches": 5 * V * args.steps,
+        "gpu_launches": 4 * V * args.steps,
         "clocks": clk,
         "scene_generation_s": gen_s,
     }
@@ -1183,7 +1183,7 @@ def run_learned(args):
                      "pairs_s": pairs_s, "scene_generation_s": gen_s, "adam_step": st["step"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 320, "d2h_bytes_per_step": px * 16,
                 "frame_latency_ms": e2e_latency, "what": E2E_WHAT % ("lf_render_host (refined)", "both refined eye images")},
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 5 * args.steps,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1268,7 +1268,7 @@ def forms_block(args, lfm, r, lf, heads, plain, flush, stream, local, peak, mean
     # ---- precision (pattern 1): the same 8 stereo poses with u8 / BF16 / FP8 textures and FP16 meshes
     outs = [torch.empty((e.height, e.width, 4), dtype=torch.float32, device="cuda") for e in heads[0]]
     for fmt, tb in (("u8", 4), ("bf16", 8), ("fp8", 4)):
-        rq = lfm.Renderer(local, timing=True)
+        rq = lfm.Renderer(local)
         rq.load_views(lf, tex_format=fmt)
         rq.build_meshes(lf, mesh_format="f16")
         for k in range(3):
@@ -1281,6 +1281,10 @@ def forms_block(args, lfm, r, lf, heads, plain, flush, stream, local, peak, mean
         ms = []
         for k in range(steps):
             ms += time_steps(lambda _: step(k), 1, flush, stream)
+        # the raster kernel's own duration: the same steps with per-kernel events
+        rq.set_timing(True)
+        for k in range(steps):
+            time_steps(lambda _: step(k), 1, flush, stream)
             raster.append(rq.stats()["ms_raster"])
         mean_ms, mean_raster = statistics.mean(ms), statistics.mean(raster)
         rbytes = mean_u * tb + out_bytes
@@ -1486,7 +1490,7 @@ def run_twolevel(args):
                     "valid_fraction": valid},
         "e2e": {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                 "note": "see loop (the streamed images are this workload's host traffic)"},
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": 6 * args.steps,
         "clocks": clk,
     }
     if rank == 0:
@@ -1539,7 +1543,7 @@ def run_ours(args):
         from paper_1810_08860_gb300 import disks
 
         lf = dataclasses.replace(lf, disk_ext=disks.oval_extents(lf))
-    r = lfm.Renderer(local, tile=(tw, th), timing=True)
+    r = lfm.Renderer(local, tile=(tw, th))
     r.load_views(lf, tex_format=args.tex)
     r.build_meshes(lf, mesh_format=args.mesh)
     stream = torch.cuda.current_stream()
@@ -1578,20 +1582,29 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     torch.cuda.synchronize()
-    raster_ms, setup_v_ms, setup_t_ms = [], [], []
     for k in range(args.steps):
         step(args.warmup + k, ev[k])
-        st = r.stats()  # waits for the step; the kernel times come from events on the launch stream
-        raster_ms.append(st["ms_raster"])
-        setup_v_ms.append(st["ms_view_setup"])
-        setup_t_ms.append(st["ms_tri_setup"])
-        assert st["error_word"] == 0
+        assert r.stats()["error_word"] == 0  # waits for the step
     torch.cuda.synchronize()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms))
     barrier_all()
     value = whole_job_rate(px_per_step * args.steps, total_ms, world)
+
+    # Each kernel's own duration: the same steps again with the library's
+    # per-kernel events on the launch stream (which rule out the programmatic
+    # launches of the timed steps above, so they are kept out of those).
+    r.set_timing(True)
+    raster_ms, setup_v_ms, setup_t_ms = [], [], []
+    for k in range(min(args.steps, 500)):
+        step(args.warmup + k)
+        st = r.stats()
+        raster_ms.append(st["ms_raster"])
+        setup_v_ms.append(st["ms_view_setup"])
+        setup_t_ms.append(st["ms_tri_setup"])
+        assert st["error_word"] == 0
+    r.set_timing(False)
 
     # End to end through lf_render_host: host poses in, both images delivered to
     # pinned host memory (the copy of one frame overlaps the render of the next).
@@ -1624,7 +1637,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 160 * len(heads[0]),
                 "d2h_bytes_per_step": out_bytes, "frame_latency_ms": e2e_latency,
                 "what": E2E_WHAT % ("lf_render_host", "both eye images")},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "clocks": clk,
     }
     # the CPU-baseline leg (the only part of this arm that runs the oracle) also compares

@@ -540,6 +540,14 @@ LF_API lf_status lf_levels_wanted(lf_ctx* ctx, int32_t cap, int32_t* views, int3
  * Errors: LF_ERR_INVALID_ARG for a negative value. */
 LF_API lf_status lf_set_wait_limit(lf_ctx* ctx, int64_t wait_ns);
 
+/* Set lf_config.timing of a live context (0 or 1) for the calls that follow.
+ * With timing off, lf_render launches the triangle set-up and the raster as
+ * programmatic dependents of the kernel before each (a grid's launch overlaps
+ * the end of the previous one), which the timing events between the kernels
+ * rule out.  No counterpart in the paper.  Errors: LF_ERR_INVALID_ARG for a
+ * null context or another value. */
+LF_API lf_status lf_set_timing(lf_ctx* ctx, int32_t on);
+
 /* Counters of the last render call; synchronises with its stream. */
 LF_API lf_status lf_get_stats(lf_ctx* ctx, lf_stats* out);
 

@@ -71,6 +71,7 @@ EXPORTS = ["lf_config_default", "lf_create", "lf_destroy", "lf_load_views", "lf_
            "lf_refine", "lf_refine_gradients", "lf_refine_train_step", "lf_render_refined", "lf_render_host",
            "lf_host_wait", "lf_prefilter", "lf_prefilter_cameras", "lf_set_disk_ovals",
            "lf_cache_create", "lf_cache_destroy", "lf_cache_frame", "lf_cache_pages", "lf_set_wait_limit",
+           "lf_set_timing",
            "lf_set_levels", "lf_upload_pages", "lf_levels_wanted"]
 HOST_FRAMES_IN_FLIGHT = 3
 HOST_FORMS = {"plain": 0, "refined": 1, "batch": 2}
@@ -186,6 +187,8 @@ def load_library(path: str = LIB_PATH):
     lib.lf_levels_wanted.restype = ctypes.c_int
     lib.lf_set_wait_limit.argtypes = [vp, i64]
     lib.lf_set_wait_limit.restype = ctypes.c_int
+    lib.lf_set_timing.argtypes = [vp, i32]
+    lib.lf_set_timing.restype = ctypes.c_int
     lib.lf_status_string.argtypes = [ctypes.c_int]
     lib.lf_status_string.restype = ctypes.c_char_p
     lib.lf_last_error.argtypes = [vp]
@@ -523,6 +526,10 @@ class Renderer:
         self._check(self.lib.lf_levels_wanted(self.ctx, int(cap), out.ctypes.data_as(ctypes.c_void_p),
                                               ctypes.byref(n)), "lf_levels_wanted")
         return out[:n.value].copy()
+
+    def set_timing(self, on: bool):
+        """Per-kernel timing events (lf_get_stats' kernel times) on or off for later calls."""
+        self._check(self.lib.lf_set_timing(self.ctx, 1 if on else 0), "lf_set_timing")
 
     def set_wait_limit(self, wait_ns: int):
         """Bound each later device wait to wait_ns nanoseconds (0: the default, 2 s)."""

@@ -302,16 +302,20 @@ FrameArgs frame_args(lf_ctx* c, const Layout& L) {
   return a;
 }
 
-// The per-call device work: clear, set up views, set up triangles, raster.
-// `timed` = false records no timing events and leaves what lf_get_stats
-// reports (the last lf_render-style call) untouched.
+// The per-call device work: clear the tile masks, set up views, set up and bin
+// triangles, raster.  The view set-up zeroes the counter block and the active
+// flags.  Without timing events between them (and outside graph capture: the
+// persistent raster), the triangle set-up and the raster are launched as
+// programmatic dependents of the kernel before them, so each grid's launch
+// overlaps the end of the previous one; each waits for its predecessor's
+// completion before it reads anything.  `timed` = false records no timing
+// events and leaves what lf_get_stats reports (the last lf_render-style call)
+// untouched.
 lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persistent, cudaStream_t s,
                         bool timed = true) {
   const bool t = timed && c->cfg.timing != 0;
+  const bool pdl = !t && !persistent;
   LF_CUDA(c, cudaMemsetAsync(a.tile_masks, 0, sizeof(uint32_t) * (size_t)a.total_tiles * a.mask_words, s));
-  // the counter block starts at zero each call
-  LF_CUDA(c, cudaMemsetAsync(a.pool_counter, 0, kCounterBlock, s));
-  LF_CUDA(c, cudaMemsetAsync(a.active, 0, (size_t)a.n_eyes * a.n_views, s));
   if (a.n_fine > 0) {
     LF_CUDA(c, cudaMemsetAsync(a.visible, 0, (size_t)a.n_eyes * a.n_views, s));
     LF_CUDA(c, cudaMemsetAsync(a.enable_bits, 0, sizeof(uint32_t) * (size_t)a.n_eyes * a.mask_words, s));
@@ -324,12 +328,11 @@ lf_status enqueue_frame(lf_ctx* c, const FrameArgs& a, bool inspect, bool persis
     LF_CUDA(c, launch_drawn(a, s));
   }
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[1], s));
-  LF_CUDA(c, launch_tri_setup(a, s));
-  LF_CUDA(c, launch_bin(a, s));
+  LF_CUDA(c, launch_tri_setup(a, s, pdl));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[2], s));
   // the persistent grid never exceeds the call's work items (tiles x strips >= tiles)
   const int blocks = std::min(c->persistent_blocks, std::max(1, a.total_tiles));
-  LF_CUDA(c, launch_raster(a, inspect, persistent, blocks, s));
+  LF_CUDA(c, launch_raster(a, inspect, persistent, blocks, s, pdl));
   if (t) LF_CUDA(c, cudaEventRecord(c->tev[3], s));
   if (timed) c->timed_call = t;
   return LF_OK;
@@ -471,6 +474,12 @@ lf_status lf_set_wait_limit(lf_ctx* c, int64_t wait_ns) {
   if (!c) return LF_ERR_INVALID_ARG;
   if (wait_ns < 0) return fail(c, LF_ERR_INVALID_ARG, "wait limit must be >= 0");
   c->cfg.wait_limit = wait_ns ? wait_ns : kDefaultWaitNs;
+  return LF_OK;
+}
+
+lf_status lf_set_timing(lf_ctx* c, int32_t on) {
+  if (!c || (on != 0 && on != 1)) return LF_ERR_INVALID_ARG;
+  c->cfg.timing = on;
   return LF_OK;
 }
 

@@ -34,7 +34,18 @@ constexpr int kMaxTileThreads = 256;
 constexpr int kSnapLimit = 1 << 29;     // |snapped| must stay below 2^29 subpixels
 constexpr int kBigEdge = 1 << 22;       // edge deltas from 2^22 subpixels use the int64 path
 constexpr int kQClamp = 1 << 28;        // clamp of the per-tile edge offset in the int32 path
-constexpr int kBinSmemTiles = 8192;     // footprint tiles a binning CTA counts in shared memory
+constexpr int kBinSmemTiles = 8192;     // footprint tiles a binning CTA counts in shared memory (at least)
+
+#ifdef __CUDACC__
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with the
+// programmatic stream serialization attribute may start before the previous
+// kernel of its stream has completed; griddep_wait() returns once that kernel
+// has completed and its memory is visible (at once when the launch had no such
+// attribute).  griddep_release() lets the next kernel of the stream launch as
+// soon as every block of this one has executed it (or exited).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
 
 // device error bits
 constexpr uint32_t kErrPoolOverflow = 1u << 0;
@@ -168,10 +179,9 @@ cudaError_t launch_convert_textures(const uint8_t* src, void* dst, int64_t n_tex
                                     const float* scale_per_texel_view, int64_t texels_per_view,
                                     cudaStream_t s);
 cudaError_t launch_view_setup(const FrameArgs& a, cudaStream_t s);
-cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s);
-cudaError_t launch_bin(const FrameArgs& a, cudaStream_t s);
+cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_raster(const FrameArgs& a, bool inspect, bool persistent, int persistent_blocks,
-                          cudaStream_t s);
+                          cudaStream_t s, bool pdl = false);
 cudaError_t raster_occupancy(int tile_w, int tile_h, int tex_format, int disk_mode, int* blocks_per_sm);
 // Two-level frames: the exact view selection of every view into a.visible (the
 // raster's disk tests alone), then the drawn views into a.enable_bits, which

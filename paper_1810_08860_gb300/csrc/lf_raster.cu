@@ -25,6 +25,7 @@
 #include <type_traits>
 
 #include "lf_internal.h"
+#include "lf_launch.h"
 
 namespace lfk {
 
@@ -606,6 +607,11 @@ __global__ void __launch_bounds__(TW * TH / kPx, 6) raster_kernel(FrameArgs A) {
   using Smem = typename std::conditional<OVAL, WarpSmemOval, WarpSmem>::type;
   __shared__ Smem S[WARPS];
   const int warp = threadIdx.x >> 5;
+  // Launched early (programmatic dependent launch), the blocks wait here until
+  // the set-up grid before this one has completed: everything read below (eye
+  // constants, tile masks, view records, bins, the work counter) is written by
+  // the kernels of the frame before this one.
+  griddep_wait();
   if constexpr (!PERSISTENT) {
     raster_strip<TW, TH, FMT, INSPECT, false, OVAL, SELECT>(A, blockIdx.x, warp, S[warp]);
   } else {
@@ -621,39 +627,38 @@ __global__ void __launch_bounds__(TW * TH / kPx, 6) raster_kernel(FrameArgs A) {
 }
 
 template <int TW, int TH, int FMT, bool OVAL>
-static cudaError_t launch_disk(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s) {
-  if (inspect) {
-    raster_kernel<TW, TH, FMT, true, false, OVAL><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
-  } else if (persistent) {
-    raster_kernel<TW, TH, FMT, false, true, OVAL><<<pblocks, TW * TH / kPx, 0, s>>>(a);
-  } else {
-    raster_kernel<TW, TH, FMT, false, false, OVAL><<<a.total_tiles, TW * TH / kPx, 0, s>>>(a);
-  }
-  return cudaGetLastError();
+static cudaError_t launch_disk(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s,
+                               bool pdl) {
+  const dim3 block(TW * TH / kPx);
+  if (inspect) return launch_kernel(raster_kernel<TW, TH, FMT, true, false, OVAL>, dim3(a.total_tiles), block, 0, s, pdl, a);
+  if (persistent) return launch_kernel(raster_kernel<TW, TH, FMT, false, true, OVAL>, dim3(pblocks), block, 0, s, pdl, a);
+  return launch_kernel(raster_kernel<TW, TH, FMT, false, false, OVAL>, dim3(a.total_tiles), block, 0, s, pdl, a);
 }
 
 template <int TW, int TH, int FMT>
-static cudaError_t launch_fmt(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s) {
-  if (a.disk_mode == 1) return launch_disk<TW, TH, FMT, true>(a, inspect, persistent, pblocks, s);
-  return launch_disk<TW, TH, FMT, false>(a, inspect, persistent, pblocks, s);
+static cudaError_t launch_fmt(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s,
+                              bool pdl) {
+  if (a.disk_mode == 1) return launch_disk<TW, TH, FMT, true>(a, inspect, persistent, pblocks, s, pdl);
+  return launch_disk<TW, TH, FMT, false>(a, inspect, persistent, pblocks, s, pdl);
 }
 
 template <int TW, int TH>
-static cudaError_t launch_tile(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s) {
+static cudaError_t launch_tile(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s,
+                               bool pdl) {
   switch (a.tex_format) {
-    case LF_TEX_F32: return launch_fmt<TW, TH, LF_TEX_F32>(a, inspect, persistent, pblocks, s);
-    case LF_TEX_U8: return launch_fmt<TW, TH, LF_TEX_U8>(a, inspect, persistent, pblocks, s);
-    case LF_TEX_BF16: return launch_fmt<TW, TH, LF_TEX_BF16>(a, inspect, persistent, pblocks, s);
-    case LF_TEX_FP8E4M3: return launch_fmt<TW, TH, LF_TEX_FP8E4M3>(a, inspect, persistent, pblocks, s);
+    case LF_TEX_F32: return launch_fmt<TW, TH, LF_TEX_F32>(a, inspect, persistent, pblocks, s, pdl);
+    case LF_TEX_U8: return launch_fmt<TW, TH, LF_TEX_U8>(a, inspect, persistent, pblocks, s, pdl);
+    case LF_TEX_BF16: return launch_fmt<TW, TH, LF_TEX_BF16>(a, inspect, persistent, pblocks, s, pdl);
+    case LF_TEX_FP8E4M3: return launch_fmt<TW, TH, LF_TEX_FP8E4M3>(a, inspect, persistent, pblocks, s, pdl);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_raster(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s) {
+cudaError_t launch_raster(const FrameArgs& a, bool inspect, bool persistent, int pblocks, cudaStream_t s, bool pdl) {
   if (a.total_tiles <= 0) return cudaSuccess;
-  if (a.tile_w == 16 && a.tile_h == 16) return launch_tile<16, 16>(a, inspect, persistent, pblocks, s);
-  if (a.tile_w == 32 && a.tile_h == 8) return launch_tile<32, 8>(a, inspect, persistent, pblocks, s);
-  if (a.tile_w == 8 && a.tile_h == 8) return launch_tile<8, 8>(a, inspect, persistent, pblocks, s);
+  if (a.tile_w == 16 && a.tile_h == 16) return launch_tile<16, 16>(a, inspect, persistent, pblocks, s, pdl);
+  if (a.tile_w == 32 && a.tile_h == 8) return launch_tile<32, 8>(a, inspect, persistent, pblocks, s, pdl);
+  if (a.tile_w == 8 && a.tile_h == 8) return launch_tile<8, 8>(a, inspect, persistent, pblocks, s, pdl);
   return cudaErrorInvalidValue;
 }
 

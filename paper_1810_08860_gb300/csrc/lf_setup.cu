@@ -19,6 +19,8 @@
 #include <cuda_fp8.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "lf_internal.h"
 #include "lf_launch.h"
 
@@ -209,6 +211,18 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
   const float tile_half_diag = 0.5f * sqrtf((float)(A.tile_w * A.tile_w + A.tile_h * A.tile_h));
   const float alpha_tile = tile_half_diag / fminf((float)E.fx, (float)E.fy);
   const bool writer = blockIdx.z == 0;  // the other slices only share the cone tests
+  // Triangle set-up may launch now: it waits for this grid to complete before
+  // it reads anything the grid writes.
+  griddep_wait();
+  griddep_release();
+  if (writer && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    // the frame's counters start at zero (no kernel before this one uses them)
+    *A.pool_counter = 0ull;
+    *A.error_word = 0u;
+    *A.work_counter = 0;
+    *A.bin_offsets_counter = 0ull;
+    *A.bin_entries_counter = 0ull;
+  }
   if (writer && blockIdx.x == 0 && threadIdx.x == 0) {
     // the eye's FP32 decision constants, each rounded once from FP64
     EyeFloat& F = A.eyes_f[e];
@@ -226,6 +240,7 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
     if (v < A.n_views) {
       const ViewStatic& V = A.views[v];
       if (writer) {
+      A.active[(int64_t)e * A.n_views + v] = 0;  // set by the raster when a pixel sees the view
       ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
       // A1: M = R_eye^T R_i, m = R_eye^T (t_i - t_eye) in FP64, fixed order, no fusion.
       double M[9], m[3];
@@ -531,6 +546,110 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int& tot
   return base + x - v;
 }
 
+// ------------------------------------------------------------------ binning
+
+// Bins one (eye, view)'s n set-up triangles (pool records tri_base ..
+// tri_base + n - 1, written by this block) into the screen tiles of its
+// footprint box; the triangle set-up block calls it once its records are
+// written.  Per tile the bin holds pool indices of the triangles whose pixel
+// box overlaps it, in no particular order (the per-view depth decision does
+// not depend on order); triangles whose box spans more than A.bin_max_tiles
+// tiles go to the view's list of big ones, which every tile of the view scans
+// (only the static-scratch render caps it).  Offsets and cursors live in the
+// offset pool: [ntiles + 1 absolute entry offsets][ntiles cursors]; the
+// per-tile counts and cursors use `cnt` (cnt_cap ints of shared memory) when
+// the footprint fits, else the pool's cursor half.
+template <int BLOCK>
+__device__ void bin_view(const FrameArgs& A, ViewRec& R, int n, int tri_base, int* cnt_smem, int cnt_cap,
+                         int* s_warp) {
+  __shared__ long long s_off, s_ent;
+  __shared__ int s_big;
+  const int tw = A.tile_w, th = A.tile_h;
+  const int tx0 = R.bb[0] / tw, ty0 = R.bb[1] / th;
+  const int ntx = R.bb[2] / tw - tx0 + 1, nty = R.bb[3] / th - ty0 + 1;
+  const int nt = ntx * nty;
+  if (threadIdx.x == 0) {
+    const unsigned long long o = atomicAdd(A.bin_offsets_counter, (unsigned long long)(2 * nt + 1));
+    s_off = ((long long)o + 2 * nt + 1 <= A.bin_offsets_capacity) ? (long long)o : -1;
+    if (s_off < 0) atomicOr(A.error_word, kErrPoolOverflow);
+    s_big = 0;
+  }
+  __syncthreads();
+  if (s_off < 0) return;
+  int* offs = A.bin_offsets + s_off;
+  int* curs = offs + nt + 1;
+  int* cnt = nt <= cnt_cap ? cnt_smem : curs;  // counts, then cursors
+  for (int k = threadIdx.x; k < nt; k += BLOCK) cnt[k] = 0;
+  __syncthreads();
+  const TriRec* tris = A.pool + tri_base;
+  auto span = [&](int t, int& x0, int& y0, int& x1, int& y1) {
+    const int2 bb = *reinterpret_cast<const int2*>(tris + t);
+    x0 = max((int)(int16_t)(bb.x & 0xffff) / tw - tx0, 0);
+    y0 = max((bb.x >> 16) / th - ty0, 0);
+    x1 = min((int)(int16_t)(bb.y & 0xffff) / tw - tx0, ntx - 1);
+    y1 = min((bb.y >> 16) / th - ty0, nty - 1);
+  };
+  int my_big = 0;
+  for (int t = threadIdx.x; t < n; t += BLOCK) {
+    int x0, y0, x1, y1;
+    span(t, x0, y0, x1, y1);
+    if (x0 > x1 || y0 > y1) continue;
+    if ((x1 - x0 + 1) * (y1 - y0 + 1) > A.bin_max_tiles) { ++my_big; continue; }
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) atomicAdd(&cnt[y * ntx + x], 1);
+  }
+  if (my_big) atomicAdd(&s_big, my_big);
+  __syncthreads();
+  // exclusive scan of the counts in place; each thread owns a contiguous run
+  const int per = (nt + BLOCK - 1) / BLOCK;
+  const int r0 = threadIdx.x * per, r1 = min(r0 + per, nt);
+  int run = 0;
+  for (int k = r0; k < r1; ++k) run += cnt[k];
+  int total;
+  int o = block_exclusive_scan(run, s_warp, total);
+  if (threadIdx.x == 0) {
+    const int need = total + s_big;
+    const unsigned long long b = atomicAdd(A.bin_entries_counter, (unsigned long long)need);
+    s_ent = ((long long)b + need <= A.bin_entries_capacity) ? (long long)b : -1;
+    if (s_ent < 0) atomicOr(A.error_word, kErrPoolOverflow);
+  }
+  __syncthreads();
+  const long long ent = s_ent;
+  if (ent < 0) return;
+  for (int k = r0; k < r1; ++k) {
+    const int c = cnt[k];
+    offs[k] = (int)(ent + o);
+    cnt[k] = (int)(ent + o);  // cursor
+    o += c;
+  }
+  if (threadIdx.x == 0) {
+    offs[nt] = (int)(ent + total);
+    s_big = 0;
+  }
+  __syncthreads();
+  const int big_base = (int)(ent + total);
+  for (int t = threadIdx.x; t < n; t += BLOCK) {
+    int x0, y0, x1, y1;
+    span(t, x0, y0, x1, y1);
+    if (x0 > x1 || y0 > y1) continue;
+    const int idx = tri_base + t;
+    if ((x1 - x0 + 1) * (y1 - y0 + 1) > A.bin_max_tiles) {
+      A.bin_entries[big_base + atomicAdd(&s_big, 1)] = idx;
+      continue;
+    }
+    for (int y = y0; y <= y1; ++y)
+      for (int x = x0; x <= x1; ++x) A.bin_entries[atomicAdd(&cnt[y * ntx + x], 1)] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    R.bin_off = (int32_t)s_off;
+    R.btx0 = (int16_t)tx0; R.bty0 = (int16_t)ty0;
+    R.bntx = (int16_t)ntx; R.bnty = (int16_t)nty;
+    R.big_base = big_base;
+    R.big_count = s_big;
+  }
+}
+
 // Shared-memory row stride of the vertex arrays: >= G and = 4 (mod 32), so
 // the 4x4 cells of a cluster read 16 different banks.
 __host__ __device__ inline int vertex_row_stride(int G) { return G + ((36 - G % 32) % 32); }
@@ -543,12 +662,18 @@ __host__ __device__ inline int vertex_row_stride(int G) { return G + ((36 - G % 
 // threads share the candidates for the full set-up (snap, clip, orientation,
 // fill rule).  Pass 1 counts the records, one atomic reserves the view's
 // segment, pass 2 writes them.  The order inside a segment does not matter:
-// the raster's depth decision within a view is order-independent.
+// the raster's depth decision within a view is order-independent.  Then the
+// block bins its records into the screen tiles (bin_view), the shared memory
+// of the vertex arrays holding the per-tile counts.
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_rows) {
+__global__ void __launch_bounds__(BLOCK, 3) tri_setup_kernel(FrameArgs A, int band_rows, int cnt_cap) {
   constexpr int NW = BLOCK / 32;
   const int v = blockIdx.x, e = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // the view set-up has completed (it wrote the view records read below); the
+  // raster may then launch, and waits for this grid before it reads the bins
+  griddep_wait();
+  griddep_release();
   ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
   const int bb0 = R.bb[0], bb1 = R.bb[1], bb2 = R.bb[2], bb3 = R.bb[3];
   if (bb0 > bb2 || bb1 > bb3) return;  // disk footprint misses the eye
@@ -716,6 +841,8 @@ __global__ void __launch_bounds__(BLOCK) tri_setup_kernel(FrameArgs A, int band_
       }
     }
   }
+  __syncthreads();  // the block's records are written and visible to all its threads
+  bin_view<BLOCK>(A, R, total, (int)tri_base, reinterpret_cast<int*>(smem), cnt_cap, s_warp);
 }
 
 constexpr int kSetupBlock = 256;
@@ -732,129 +859,17 @@ static int setup_band_rows(int G, size_t smem_limit) {
   return rows < kClusterCells ? kClusterCells : rows;
 }
 
-// ------------------------------------------------------------------ binning
-
-// One CTA per (eye, view) with triangles: bins the view's triangles into the
-// screen tiles of its footprint box.  Per tile the bin holds pool indices of
-// the triangles whose pixel box overlaps it, in no particular order (the
-// per-view depth decision does not depend on order); triangles whose box
-// spans more than A.bin_max_tiles tiles go to the view's list of big ones,
-// which every tile of the view scans (only the static-scratch render caps it).  Counts, offsets and cursors live in the
-// offset pool: [ntiles + 1 absolute entry offsets][ntiles cursors].
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) bin_kernel(FrameArgs A) {
-  const int v = blockIdx.x, e = blockIdx.y;
-  ViewRec& R = A.vrecs[(int64_t)e * A.n_views + v];
-  const int n = R.tri_count;
-  if (n <= 0) return;
-  __shared__ int s_warp[BLOCK / 32];
-  __shared__ long long s_off, s_ent;
-  __shared__ int s_big;
-  // per-tile counts, then cursors: in shared memory when the footprint fits
-  // (nearly always), else in the offset pool's cursor half
-  __shared__ int s_cnt[kBinSmemTiles];
-  const int tw = A.tile_w, th = A.tile_h;
-  const int tx0 = R.bb[0] / tw, ty0 = R.bb[1] / th;
-  const int ntx = R.bb[2] / tw - tx0 + 1, nty = R.bb[3] / th - ty0 + 1;
-  const int nt = ntx * nty;
-  if (threadIdx.x == 0) {
-    const unsigned long long o = atomicAdd(A.bin_offsets_counter, (unsigned long long)(2 * nt + 1));
-    s_off = ((long long)o + 2 * nt + 1 <= A.bin_offsets_capacity) ? (long long)o : -1;
-    if (s_off < 0) atomicOr(A.error_word, kErrPoolOverflow);
-    s_big = 0;
-  }
-  __syncthreads();
-  if (s_off < 0) return;
-  int* offs = A.bin_offsets + s_off;
-  int* curs = offs + nt + 1;
-  const bool in_smem = nt <= kBinSmemTiles;
-  int* cnt = in_smem ? s_cnt : curs;  // counts, then cursors
-  for (int k = threadIdx.x; k < nt; k += BLOCK) cnt[k] = 0;
-  __syncthreads();
-  const TriRec* tris = A.pool + R.tri_base;
-  auto span = [&](int t, int& x0, int& y0, int& x1, int& y1) {
-    const int2 bb = *reinterpret_cast<const int2*>(tris + t);
-    x0 = max((int)(int16_t)(bb.x & 0xffff) / tw - tx0, 0);
-    y0 = max((bb.x >> 16) / th - ty0, 0);
-    x1 = min((int)(int16_t)(bb.y & 0xffff) / tw - tx0, ntx - 1);
-    y1 = min((bb.y >> 16) / th - ty0, nty - 1);
-  };
-  int my_big = 0;
-  for (int t = threadIdx.x; t < n; t += BLOCK) {
-    int x0, y0, x1, y1;
-    span(t, x0, y0, x1, y1);
-    if (x0 > x1 || y0 > y1) continue;
-    if ((x1 - x0 + 1) * (y1 - y0 + 1) > A.bin_max_tiles) { ++my_big; continue; }
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) atomicAdd(&cnt[y * ntx + x], 1);
-  }
-  if (my_big) atomicAdd(&s_big, my_big);
-  __syncthreads();
-  // exclusive scan of the counts in place; each thread owns a contiguous run
-  const int per = (nt + BLOCK - 1) / BLOCK;
-  const int r0 = threadIdx.x * per, r1 = min(r0 + per, nt);
-  int run = 0;
-  for (int k = r0; k < r1; ++k) run += cnt[k];
-  int total;
-  int o = block_exclusive_scan(run, s_warp, total);
-  if (threadIdx.x == 0) {
-    const int need = total + s_big;
-    const unsigned long long b = atomicAdd(A.bin_entries_counter, (unsigned long long)need);
-    s_ent = ((long long)b + need <= A.bin_entries_capacity) ? (long long)b : -1;
-    if (s_ent < 0) atomicOr(A.error_word, kErrPoolOverflow);
-  }
-  __syncthreads();
-  const long long ent = s_ent;
-  if (ent < 0) return;
-  for (int k = r0; k < r1; ++k) {
-    const int c = cnt[k];
-    offs[k] = (int)(ent + o);
-    cnt[k] = (int)(ent + o);  // cursor
-    o += c;
-  }
-  if (threadIdx.x == 0) {
-    offs[nt] = (int)(ent + total);
-    s_big = 0;
-  }
-  __syncthreads();
-  const int big_base = (int)(ent + total);
-  for (int t = threadIdx.x; t < n; t += BLOCK) {
-    int x0, y0, x1, y1;
-    span(t, x0, y0, x1, y1);
-    if (x0 > x1 || y0 > y1) continue;
-    const int idx = R.tri_base + t;
-    if ((x1 - x0 + 1) * (y1 - y0 + 1) > A.bin_max_tiles) {
-      A.bin_entries[big_base + atomicAdd(&s_big, 1)] = idx;
-      continue;
-    }
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) A.bin_entries[atomicAdd(&cnt[y * ntx + x], 1)] = idx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    R.bin_off = (int32_t)s_off;
-    R.btx0 = (int16_t)tx0; R.bty0 = (int16_t)ty0;
-    R.bntx = (int16_t)ntx; R.bnty = (int16_t)nty;
-    R.big_base = big_base;
-    R.big_count = s_big;
-  }
-}
-
-cudaError_t launch_bin(const FrameArgs& a, cudaStream_t s) {
-  dim3 grid(a.n_views, a.n_eyes);
-  bin_kernel<256><<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s) {
+cudaError_t launch_tri_setup(const FrameArgs& a, cudaStream_t s, bool pdl) {
   const size_t limit = 96 * 1024;
   cudaError_t err = ensure_dynamic_smem(reinterpret_cast<const void*>(tri_setup_kernel<kSetupBlock>), (int)limit + 64);
   if (err != cudaSuccess) return err;
   const int rows = setup_band_rows(a.G, limit);
-  const size_t bytes = (size_t)(rows + 1) * vertex_row_stride(a.G) * kVtxBytes + 2 * 2 * (size_t)(a.G - 1) * rows + 64;
+  const size_t vtx = (size_t)(rows + 1) * vertex_row_stride(a.G) * kVtxBytes + 2 * 2 * (size_t)(a.G - 1) * rows + 64;
+  // the binning counts reuse the vertex arrays' shared memory: at least kBinSmemTiles ints
+  const size_t bytes = std::max(vtx, sizeof(int) * (size_t)kBinSmemTiles);
+  const int cnt_cap = (int)(bytes / sizeof(int));
   dim3 grid(a.n_views, a.n_eyes);
-  tri_setup_kernel<kSetupBlock><<<grid, kSetupBlock, bytes, s>>>(a, rows);
-  return cudaGetLastError();
+  return launch_kernel(tri_setup_kernel<kSetupBlock>, grid, dim3(kSetupBlock), bytes, s, pdl, a, rows, cnt_cap);
 }
 
 }  // namespace lfk

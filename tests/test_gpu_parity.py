@@ -220,6 +220,38 @@ def test_render_matches_inspect_and_batch(lfmod, tiny):
     r.close()
 
 
+def test_timed_and_programmatic_launches_agree(lfmod, tiny):
+    """Without timing events the triangle set-up and the raster are launched as
+    programmatic dependents of the kernel before each; the frames, counters and
+    flags must equal those of the timed (fully serialised) launches, also for
+    frames enqueued back to back without a synchronisation between them."""
+    eyes = [tiny.eyes[0], scene.Eye(tiny.eyes[0].pose, np.array([60.0, 60.0, 50.0, 40.0]), 100, 90)]
+    r = lfmod.Renderer(0, max_eyes=2, timing=True)
+    r.load_views(tiny)
+    r.build_meshes(tiny)
+    ref = [o.cpu() for o in r.render(eyes)]
+    st_ref = r.stats()
+    assert st_ref["ms_raster"] > 0 and st_ref["ms_tri_setup"] > 0
+    r.set_timing(False)
+    got = [o.cpu() for o in r.render(eyes)]
+    st = r.stats()
+    for x, y in zip(ref, got):
+        assert (x == y).all()
+    assert st["ms_raster"] == 0
+    for k in ("triangles", "tiles", "active_views", "error_word"):
+        assert st[k] == st_ref[k], k
+    torch = pytest.importorskip("torch")
+    outs = [[torch.empty((e.height, e.width, 4), dtype=torch.float32, device="cuda") for e in eyes] for _ in range(6)]
+    for o in outs:
+        r.render(eyes, out=o)
+    torch.cuda.synchronize()
+    for o in outs:
+        for x, y in zip(ref, o):
+            assert (x == y.cpu()).all()
+    assert r.stats()["error_word"] == 0
+    r.close()
+
+
 # ---------------------------------------------------------------- against the FP64 definition
 
 # The kernels take the integer decisions in FP32 (the oracle's "fp32" mode, matched
