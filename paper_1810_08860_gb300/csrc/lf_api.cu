@@ -1172,19 +1172,38 @@ lf_status refine_layers(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float*
   return LF_OK;
 }
 
-lf_status refine_apply(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float* in, float* out, cudaStream_t s) {
+lf_status refine_apply(lf_ctx* c, int32_t n, int32_t w, int32_t h, const float* in, float* out, cudaStream_t s,
+                       float* out1 = nullptr, bool pdl = false) {
   if ((int64_t)n * w * h == 0) return LF_OK;
   if (c->rf.kernel == LF_REFINE_FUSED_TC) {
     if (reinterpret_cast<uintptr_t>(in) & 15u)  // the fused kernel reads the input through a TMA tensor map
       return fail(c, LF_ERR_INVALID_ARG, "the fused refinement needs a 16-byte aligned input");
     int32_t* err = reinterpret_cast<int32_t*>(static_cast<char*>(c->rf.scal.p) + 8);
-    LF_CUDA(c, launch_refine_fused(n, w, h, in, out, rf_params(c), static_cast<const __nv_bfloat16*>(c->rf.packed.p),
-                                   c->sm_count, err, (uint64_t)c->cfg.wait_limit, s));
+    LF_CUDA(c, launch_refine_fused(n, w, h, in, out, out1, rf_params(c),
+                                   static_cast<const __nv_bfloat16*>(c->rf.packed.p), c->sm_count, err,
+                                   (uint64_t)c->cfg.wait_limit, s, pdl));
     return LF_OK;
   }
   lf_status st = refine_hidden(c, (int64_t)n * w * h, false);
   if (st != LF_OK) return st;
   return refine_layers(c, n, w, h, in, out, s);
+}
+
+// The refinement of a rendered frame: eye e's image in[e] (FP32 RGBA) into
+// out[e].  A pair of equal-sized eyes whose inputs lie back to back in one
+// buffer is refined by one fused launch (the two images' tiles share the
+// grid); `pdl` (no timing events after the raster) launches the first
+// refinement as a programmatic dependent of the raster.
+lf_status refine_eyes(lf_ctx* c, int32_t n_eyes, const lf_intrinsics* intr, float* const* in, float* const* out,
+                      cudaStream_t s, bool pdl) {
+  if (c->rf.kernel == LF_REFINE_FUSED_TC && n_eyes == 2 && intr[0].width == intr[1].width &&
+      intr[0].height == intr[1].height && in[1] == in[0] + (size_t)intr[0].width * intr[0].height * 4)
+    return refine_apply(c, 2, intr[0].width, intr[0].height, in[0], out[0], s, out[1], pdl);
+  for (int e = 0; e < n_eyes; ++e) {
+    lf_status st = refine_apply(c, 1, intr[e].width, intr[e].height, in[e], out[e], s, nullptr, pdl && e == 0);
+    if (st != LF_OK) return st;
+  }
+  return LF_OK;
 }
 
 // Forward with the loss epilogue, then the backward pass into rf_grad.
@@ -1358,11 +1377,7 @@ lf_status lf_render_refined(lf_ctx* c, int32_t n_eyes, const lf_pose* eyes, cons
   for (int e = 0; e < n_eyes; ++e) tmp[e] = static_cast<float*>(c->rf.frame.p) + off[e];
   lf_status st = lf_render(c, n_eyes, eyes, intr, tmp.data(), stream);
   if (st != LF_OK) return st;
-  for (int e = 0; e < n_eyes; ++e)
-    if ((st = refine_apply(c, 1, intr[e].width, intr[e].height, tmp[e], out_rgba[e],
-                           static_cast<cudaStream_t>(stream))) != LF_OK)
-      return st;
-  return LF_OK;
+  return refine_eyes(c, n_eyes, intr, tmp.data(), out_rgba, static_cast<cudaStream_t>(stream), !c->cfg.timing);
 }
 
 }  // extern "C"
@@ -1427,9 +1442,7 @@ lf_status host_enqueue(lf_ctx* c, int slot, int32_t n_eyes, const lf_pose* eyes,
   if (form == LF_HOST_BATCH && (st = ensure_persistent_blocks(c)) != LF_OK) return st;
   // lf_get_stats does not report host-delivered frames: no timing events
   if ((st = enqueue_frame(c, a, false, form == LF_HOST_BATCH, s, false)) != LF_OK) return st;
-  if (refined)
-    for (int e = 0; e < n_eyes; ++e)
-      if ((st = refine_apply(c, 1, intr[e].width, intr[e].height, target[e], dev[e], s)) != LF_OK) return st;
+  if (refined && (st = refine_eyes(c, n_eyes, intr, target.data(), dev.data(), s, true)) != LF_OK) return st;
   LF_CUDA(c, cudaEventRecord(H.rendered[slot], s));
   LF_CUDA(c, cudaStreamWaitEvent(H.copy, H.rendered[slot], 0));
   for (int e = 0; e < n_eyes; ++e)

@@ -248,8 +248,10 @@ cudaError_t launch_refine_adam(float* p, float* m, float* v, const float* g, int
                                double beta2, float eps, float c1, float c2, cudaStream_t s);
 cudaError_t launch_refine_pack(const float* params, __nv_bfloat16* w, cudaStream_t s);
 // Fused inference (lf_refine_tc.cu): all three layers per tile, tcgen05 MMAs.
-cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, const float* params,
-                                const __nv_bfloat16* packed, int sm_count, int32_t* error, uint64_t wait_ns,
-                                cudaStream_t s);
+// Image i goes to out + i*h*w*4, except image 1 to out1 when out1 is set; with
+// pdl the launch is a programmatic dependent of the kernel before it.
+cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, float* out1,
+                                const float* params, const __nv_bfloat16* packed, int sm_count, int32_t* error,
+                                uint64_t wait_ns, cudaStream_t s, bool pdl);
 
 }  // namespace lfk

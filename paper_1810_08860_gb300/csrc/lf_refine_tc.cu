@@ -243,7 +243,8 @@ __device__ __forceinline__ uint32_t relu_pack2(float lo, float hi) {
 struct FusedArgs {
   int32_t n, H, W, tiles_x, tiles_y, n_tiles;
   const float* in;
-  float* out;
+  float* out;                // image i at out + i * H * W * 4 ...
+  float* out1;               // ... except image 1 at out1 when set (a stereo pair's two buffers)
   const __nv_bfloat16* wtc;  // B operands: L1, L2, L3 blocks
   const float* prm;          // FP32 parameters (b2, b3 read from here)
   int32_t* error;            // set to 1 if a wait gave up
@@ -336,6 +337,10 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A, 
   tc_after_sync();
   const uint32_t tmem = *tmem_slot;
   const int H = A.H, W = A.W;
+  // Launched as a programmatic dependent of the render, the set-up above (weights
+  // and biases, written long before the render began) overlaps the end of the
+  // raster; its output, this kernel's input, is read only past this wait.
+  griddep_wait();
 
   // Tiles of this CTA: blockIdx.x + j * gridDim.x, j < n_own; periods k = 0 .. n_own.
   const int n_own = blockIdx.x < A.n_tiles ? (A.n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
@@ -605,7 +610,8 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A, 
       int ux0 = 0, uy0 = 0, tx0 = 0, ty0 = 0, img = 0;
       if (k > 0) tile_origin(A, blockIdx.x + (k - 1) * gridDim.x, img, tx0, ty0);
       const float4* in = reinterpret_cast<const float4*>(A.in) + (size_t)img * H * W;  // tile k - 1
-      float4* out = reinterpret_cast<float4*>(A.out) + (size_t)img * H * W;
+      float4* out = (img == 1 && A.out1) ? reinterpret_cast<float4*>(A.out1)
+                                         : reinterpret_cast<float4*>(A.out) + (size_t)img * H * W;
       if (k < n_own) {
         int uimg;
         tile_origin(A, blockIdx.x + k * gridDim.x, uimg, ux0, uy0);
@@ -712,9 +718,9 @@ EncodeTiled encode_tiled() {
 
 }  // namespace
 
-cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, const float* params,
-                                const __nv_bfloat16* packed, int sm_count, int32_t* error, uint64_t wait_ns,
-                                cudaStream_t s) {
+cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, float* out1,
+                                const float* params, const __nv_bfloat16* packed, int sm_count, int32_t* error,
+                                uint64_t wait_ns, cudaStream_t s, bool pdl) {
   cudaError_t e = ensure_dynamic_smem(reinterpret_cast<const void*>(refine_fused_kernel), kSmemBytes);
   if (e != cudaSuccess) return e;
   FusedArgs a;
@@ -726,6 +732,7 @@ cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in
   a.n_tiles = a.tiles_x * a.tiles_y * n;
   a.in = in;
   a.out = out;
+  a.out1 = n > 1 ? out1 : nullptr;
   a.wtc = packed + kPackTc;
   a.prm = params;
   a.error = error;
@@ -746,8 +753,7 @@ cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const int grid = a.n_tiles < sm_count ? a.n_tiles : sm_count;
-  refine_fused_kernel<<<grid, kThreads, kSmemBytes, s>>>(a, tmap);
-  return cudaGetLastError();
+  return launch_kernel(refine_fused_kernel, dim3(grid), dim3(kThreads), kSmemBytes, s, pdl, a, tmap);
 }
 
 }  // namespace lfk

@@ -155,6 +155,31 @@ def test_refine_of_an_actual_render(lfmod):
     r.close()
 
 
+def test_render_refined_pairs_equal_per_eye_refinement(lfmod):
+    # an equal-sized stereo pair is refined by one fused launch into the two
+    # caller buffers (launched as a programmatic dependent of the raster); a
+    # pair of different sizes by one launch per eye: both equal the refinement
+    # of each eye's render on its own
+    import torch
+
+    lf = scene.tiny_light_field(1)
+    base = lf.eyes[0]
+    r = lfmod.Renderer(0, max_eyes=2)
+    r.load_views(lf)
+    r.build_meshes(lf)
+    r.load_refiner(_params(lfmod, 11))
+    r.set_refine_kernel("fused")
+    other = scene.Eye(base.pose, np.array([70.0, 70.0, 41.0, 37.0]), base.width, base.height)
+    small = scene.Eye(base.pose, np.array([60.0, 60.0, 33.0, 30.0]), 70, 61)
+    for pair in ([base, other], [base, small]):
+        got = [o.cpu() for o in r.render_refined(pair)]
+        for eye, g in zip(pair, got):
+            want = r.refine(r.render([eye])[0]).cpu()
+            assert torch.equal(g, want), (eye.width, eye.height)
+    r.get_refiner()  # raises if a wait of the fused kernel gave up
+    r.close()
+
+
 def test_refine_full_size_sampled(lfmod):
     # the stereo eye size of the rig workload, in the fused launch the bench times;
     # each sampled output depends only on the 7x7 window around it
