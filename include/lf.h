@@ -403,7 +403,8 @@ LF_API lf_status lf_refine_train_step(lf_ctx* ctx, int32_t n_images, int32_t wid
                                       const float* in_rgba, const float* target_rgba, float lr, void* stream);
 
 /* lf_render followed by lf_refine of every eye (through a scratch image the
- * context owns).  With no refiner loaded it is lf_render, the plain method. */
+ * context owns; with the fused kernel, two eyes of equal size are refined by
+ * one launch).  With no refiner loaded it is lf_render, the plain method. */
 LF_API lf_status lf_render_refined(lf_ctx* ctx, int32_t n_eyes, const lf_pose* eyes, const lf_intrinsics* intr,
                                    float* const* out_rgba, void* stream);
 
