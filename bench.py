@@ -1404,7 +1404,7 @@ def run_twolevel(args):
         disk_c=np.concatenate([fine.disk_c, coarse.disk_c]), disk_r=np.concatenate([fine.disk_r, coarse.disk_r]),
         name="two-level")
     nf, pages = fine.n_views, args.pages
-    r = lfm.Renderer(local, timing=True)
+    r = lfm.Renderer(local)
     r.load_views(both)
     r.build_meshes(both)
     r.set_levels(nf, pages)
@@ -1445,9 +1445,16 @@ def run_twolevel(args):
         t1 = time.perf_counter()
         if f >= args.warmup:
             rec.append({"render_ms": e0.elapsed_time(e1), "frame_ms": 1000 * (t1 - t0), "wanted": int(len(wanted)),
-                        "missing": miss, "admitted": len(adm), "drawn": sum(st["active_views"]),
-                        "raster_ms": st["ms_raster"]})
+                        "missing": miss, "admitted": len(adm), "drawn": sum(st["active_views"])})
     clk = clocks.stop()
+    # the raster kernel's own duration: frames of the last head pose with per-kernel events
+    # (timed frames above run without them, as a user's calls do)
+    r.set_timing(True)
+    raster_ms = []
+    for _ in range(5):
+        r.render(head(args.warmup + args.steps - 1), out=outs, stream=stream)
+        raster_ms.append(r.stats()["ms_raster"])
+    r.set_timing(False)
     render_ms = max_over_ranks(sum(x["render_ms"] for x in rec)) / len(rec)
     frame_ms = max_over_ranks(sum(x["frame_ms"] for x in rec)) / len(rec)
     # quality of the last frame against the analytic truth, beside the fine level alone
@@ -1484,7 +1491,7 @@ def run_twolevel(args):
                    "mean_missing": statistics.mean(x["missing"] for x in rec),
                    "mean_admitted": statistics.mean(x["admitted"] for x in rec),
                    "mean_drawn_views": statistics.mean(x["drawn"] for x in rec),
-                   "raster_ms": statistics.mean(x["raster_ms"] for x in rec),
+                   "raster_ms": statistics.mean(raster_ms),
                    "upload_bytes_per_frame": 1024 * 1024 * 4 * statistics.mean(x["admitted"] for x in rec)},
         "quality": {"psnr_vs_analytic_truth_db": psnr(prog), "fine_level_alone_db": psnr(full),
                     "valid_fraction": valid},

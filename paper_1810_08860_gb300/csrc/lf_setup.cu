@@ -202,9 +202,9 @@ constexpr int kViewSetupSlices = 8;  // blocks sharing one group of views' (view
 // of the tile's centre ray (rays through image points s apart differ by at
 // most s/f in angle), so a tile is skipped only when the two cones are apart.
 __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs A) {
-  __shared__ int s_bb[kViewsPerSetupBlock][4];
   __shared__ float s_dir[kViewsPerSetupBlock][4];   // unit direction to the disk centre, cos of the cone limit
-  __shared__ int s_off[kViewsPerSetupBlock + 1];
+  __shared__ int s_off[kViewsPerSetupBlock + 1];   // exclusive prefix of the footprints' tile counts
+  __shared__ int s_tile[kViewsPerSetupBlock][3];    // footprint: first tile column and row, tile columns
   const int e = blockIdx.y;
   const int v0 = blockIdx.x * kViewsPerSetupBlock;
   const EyeParams& E = A.eyes[e];
@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
     F.R2 = __double2float_rn(__dmul_rn(A.sphere_r, A.sphere_r));
     F.pad[0] = F.pad[1] = F.pad[2] = 0.0f;
   }
+  int n_tiles = 0;  // tiles of this thread's view's footprint (threads 0-15)
   if (threadIdx.x < kViewsPerSetupBlock) {
     const int v = v0 + threadIdx.x;
     int bb[4] = {1, 1, 0, 0};
@@ -366,31 +367,40 @@ __global__ void __launch_bounds__(kViewSetupThreads) view_setup_kernel(FrameArgs
         dir[3] = -2.0f;  // the eye is inside the ball: every tile of the footprint
       }
     }
-    for (int k = 0; k < 4; ++k) { s_bb[threadIdx.x][k] = bb[k]; s_dir[threadIdx.x][k] = dir[k]; }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int k = 0; k < kViewsPerSetupBlock; ++k) {
-      s_off[k] = acc;
-      if (s_bb[k][0] <= s_bb[k][2] && s_bb[k][1] <= s_bb[k][3]) {
-        const int ntx = s_bb[k][2] / A.tile_w - s_bb[k][0] / A.tile_w + 1;
-        const int nty = s_bb[k][3] / A.tile_h - s_bb[k][1] / A.tile_h + 1;
-        acc += ntx * nty;
-      }
+    for (int k = 0; k < 4; ++k) s_dir[threadIdx.x][k] = dir[k];
+    int tx0 = 0, ty0 = 0, ntx = 1;
+    if (bb[0] <= bb[2] && bb[1] <= bb[3]) {
+      tx0 = bb[0] / A.tile_w;
+      ty0 = bb[1] / A.tile_h;
+      ntx = bb[2] / A.tile_w - tx0 + 1;
+      n_tiles = ntx * (bb[3] / A.tile_h - ty0 + 1);
     }
-    s_off[kViewsPerSetupBlock] = acc;
+    s_tile[threadIdx.x][0] = tx0;
+    s_tile[threadIdx.x][1] = ty0;
+    s_tile[threadIdx.x][2] = ntx;
+  }
+  // the footprints' tile counts, scanned by warp 0 (which holds threads 0-15)
+  if (threadIdx.x < 32) {
+    int incl = n_tiles;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)threadIdx.x >= o) incl += y;
+    }
+    if (threadIdx.x < kViewsPerSetupBlock) s_off[threadIdx.x] = incl - n_tiles;
+    if (threadIdx.x == kViewsPerSetupBlock - 1) s_off[kViewsPerSetupBlock] = incl;
   }
   __syncthreads();
   const int total = s_off[kViewsPerSetupBlock];
   const float fx = (float)E.fx, fy = (float)E.fy, cx = (float)E.cx, cy = (float)E.cy;
   for (int f = threadIdx.x + blockIdx.z * kViewSetupThreads; f < total; f += kViewSetupThreads * kViewSetupSlices) {
-    int k = 0;
-    while (k + 1 < kViewsPerSetupBlock && s_off[k + 1] <= f) ++k;
+    int k = 0;  // the view whose range [s_off[k], s_off[k + 1]) holds f
+#pragma unroll
+    for (int step = kViewsPerSetupBlock / 2; step > 0; step >>= 1)
+      if (s_off[k + step] <= f) k += step;
     const int q = f - s_off[k];
-    const int tx0 = s_bb[k][0] / A.tile_w, ty0 = s_bb[k][1] / A.tile_h;
-    const int ntx = s_bb[k][2] / A.tile_w - tx0 + 1;
-    const int tx = tx0 + q % ntx, ty = ty0 + q / ntx;
+    const int ntx = s_tile[k][2];
+    const int tx = s_tile[k][0] + q % ntx, ty = s_tile[k][1] + q / ntx;
     // centre ray of the tile's pixel-centre rectangle
     const float xc = (float)(tx * A.tile_w) + 0.5f * (float)(A.tile_w - 1) + 0.5f;
     const float yc = (float)(ty * A.tile_h) + 0.5f * (float)(A.tile_h - 1) + 0.5f;

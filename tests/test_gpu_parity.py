@@ -232,6 +232,7 @@ def test_timed_and_programmatic_launches_agree(lfmod, tiny):
     ref = [o.cpu() for o in r.render(eyes)]
     st_ref = r.stats()
     assert st_ref["ms_raster"] > 0 and st_ref["ms_tri_setup"] > 0
+    assert lfmod.STATUS[r.lib.lf_set_timing(r.ctx, 2)] == "LF_ERR_INVALID_ARG"  # 0 or 1 only
     r.set_timing(False)
     got = [o.cpu() for o in r.render(eyes)]
     st = r.stats()
