@@ -471,12 +471,12 @@ __device__ void raster_strip(const FrameArgs& A, const int item, const int strip
                                          : __ldg(A.bin_entries + S.gbase[sl] + (k - S.bcount[sl]));
         const TriRec* tr = A.pool + idx;
         ra = __ldg(reinterpret_cast<const int4*>(tr));       // bbox, x0, x1
+        rb = __ldg(reinterpret_cast<const int4*>(tr) + 1);   // x2, y0, y1, y2
+        rc = __ldg(reinterpret_cast<const int4*>(tr) + 2);   // ia, ib, ic, id_tl
         const int bx0 = (int16_t)(ra.x & 0xffff), by0 = ra.x >> 16;
         const int bx1 = (int16_t)(ra.y & 0xffff), by1 = ra.y >> 16;
         pred = bx0 <= i0 + TW - 1 && bx1 >= i0 && by0 <= wrow1 && by1 >= wrow0;
         if (pred) {
-          rb = __ldg(reinterpret_cast<const int4*>(tr) + 1);   // x2, y0, y1, y2
-          rc = __ldg(reinterpret_cast<const int4*>(tr) + 2);   // ia, ib, ic, id_tl
           const int32_t X[3] = {ra.z, ra.w, rb.x};
           const int32_t Y[3] = {rb.y, rb.z, rb.w};
 #pragma unroll
