@@ -62,7 +62,7 @@ typedef enum {
   LF_ERR_OOM = 3,          /* a device or pinned allocation failed */
   LF_ERR_STATE = 4,        /* views or meshes not loaded, or loaded with other sizes */
   LF_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
-  LF_ERR_UNSUPPORTED = 6,  /* a valid request this build does not implement */
+  LF_ERR_UNSUPPORTED = 6,  /* a valid request the library does not implement */
   LF_ERR_CAPACITY = 7      /* per-frame scratch too small; raise lf_config.tri_capacity */
 } lf_status;
 
