@@ -1,6 +1,7 @@
 // lf_launch.h - host-side launch helpers shared by the kernel files.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is reached through the runtime)
 #include <cuda_runtime.h>
 
 #include <utility>
@@ -33,5 +34,23 @@ cudaError_t launch_kernel(void (*kernel)(P...), dim3 grid, dim3 block, size_t sm
 // context, so a flag kept per process would leave a second device unset.
 // Thread safe.  Defined in lf_api.cu.
 cudaError_t ensure_dynamic_smem(const void* kernel, int bytes);
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, reached through the runtime (no link
+// against libcuda); null when the driver does not provide it.
+inline EncodeTiled encode_tiled() {
+  static const EncodeTiled fn = []() -> EncodeTiled {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
 
 }  // namespace lfk

@@ -22,10 +22,14 @@
 // a kernel row: 3 MMAs per M-tile.  Output columns 0 and 31 of the halo see a
 // wrapped neighbour and are never stored.
 //
-// Per tile: the four warps stage the halo (zeros outside the image), one
-// thread issues the tile's MMAs and commits to an mbarrier, every warp waits
-// (bounded by wait_ns, an error word on give-up), reads its lane quadrant of
-// each M-tile's accumulators with tcgen05.ld and runs the epilogue.  Four CTAs
+// Per tile: the halo is staged (zeros outside the image), one thread issues
+// the tile's MMAs and commits to an mbarrier, every warp waits (bounded by
+// wait_ns, an error word on give-up), reads its lane quadrant of each M-tile's
+// accumulators with tcgen05.ld and runs the epilogue.  A 32-channel BF16 halo
+// arrives by TMA (one tiled copy per group of 8 channels, straight into the
+// MMA operand layout), the next tile's copy issued as soon as the current
+// tile's MMAs have read the buffer, so it lands during the epilogue; the
+// 3-channel FP32 halo is converted to BF16 pairs by the four warps.  Four CTAs
 // share an SM, so one CTA's MMAs overlap another's staging and epilogue.
 //
 // Shared-memory operands use the K-major layout without swizzling: a position
@@ -38,6 +42,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "lf_internal.h"
 #include "lf_launch.h"
@@ -51,7 +56,9 @@ constexpr int kCHW = 32, kCHH = kCTH + 2;         // halo: 32 positions x 18 row
 constexpr int kCMT = kCTH / 4;                    // M-tiles of 128 positions per tile
 constexpr int kCPos = kCHH * kCHW;                // 576 positions
 constexpr int kCGuard = 2;                        // positions before and after (reads reach one beyond)
-constexpr int kCGroupB = (kCPos + 2 * kCGuard) * 16;  // bytes per group of 8 channels
+constexpr int kCGroupB = ((kCPos + 2 * kCGuard) * 16 + 127) / 128 * 128;  // bytes per group of 8 channels
+constexpr int kCXOff = 128 - kCGuard * 16;        // halo position 0 of each group starts 128-byte aligned
+constexpr int kCHaloTx = 4 * kCPos * 16;          // bytes of a tile's four TMA copies (32-channel halo)
 constexpr int kCThreads = 128;
 constexpr int kCPerSM = 4;                        // CTAs per SM: 4 x 128 TMEM columns
 constexpr uint32_t kCTmemCols = 128;
@@ -113,6 +120,22 @@ __device__ __forceinline__ void c_tmem_ld16(uint32_t addr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Tile `tile`'s 32-channel BF16 halo by TMA: one tiled copy per group g of 8
+// channels (a box of 8 channels x 32 positions x 18 rows of the 5-D tensor map
+// {8, 4, W, H, n} over the map; zeros where the box leaves the image) into the
+// group's operand rows, completing on `bar` with the copies' byte count.
+__device__ __forceinline__ void c_load_halo(const CUtensorMap* tmap, uint32_t sx0, uint64_t* bar, int img, int x0,
+                                            int y0) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(c_su32(bar)), "r"(kCHaloTx) : "memory");
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+        "[%7];" ::"r"(sx0 + g * kCGroupB),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(g), "r"(x0 - 1), "r"(y0 - 1), "r"(img), "r"(c_su32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ uint32_t c_pack(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
@@ -121,7 +144,8 @@ __device__ __forceinline__ uint32_t c_pack(float lo, float hi) {
 }  // namespace
 
 template <int IN, int COUT, int EPI>
-__global__ void __launch_bounds__(kCThreads, kCPerSM) conv_tc_kernel(RefineConvArgs A) {
+__global__ void __launch_bounds__(kCThreads, kCPerSM)
+    conv_tc_kernel(RefineConvArgs A, const __grid_constant__ CUtensorMap tmap) {
   constexpr int N = COUT < 16 ? 16 : COUT;                 // MMA N (the 3-output layer pads to 16)
   constexpr int NB = IN == kConvInBF16 ? 18 : 3;           // B blocks: (tap, half) or kernel row
   constexpr int kBlkB = 2 * N * 16;
@@ -129,9 +153,10 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM) conv_tc_kernel(RefineConvA
   constexpr int G = IN == kConvInBF16 ? 4 : 1;             // channel groups in the halo
   extern __shared__ __align__(128) unsigned char sm[];
   unsigned char* sw = sm;
-  unsigned char* sx = sm + kWBytes;  // group g, position p: sx + g * kCGroupB + (p + kCGuard) * 16
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sx + G * kCGroupB);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  unsigned char* sx = sm + kWBytes + kCXOff;  // group g, position p: sx + g * kCGroupB + (p + kCGuard) * 16
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sx + G * kCGroupB);  // the tile's MMAs completed
+  uint64_t* xbar = bar + 1;                                         // the tile's TMA halo landed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ float s_bias[32];
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -165,10 +190,12 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM) conv_tc_kernel(RefineConvA
   }
   for (int i = tid; i < G * kCGroupB / 16; i += kCThreads)  // the guard rows stay zero
     reinterpret_cast<uint4*>(sx)[i] = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the zeros, to the tensor core and TMA
   if (tid < 32) s_bias[tid] = (EPI == kEpiRelu || (EPI != kEpiMask && tid < 3)) ? A.bias[tid] : 0.f;
   if (tid == 0) {
     s_abort = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(c_su32(bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(c_su32(xbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -188,21 +215,37 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM) conv_tc_kernel(RefineConvA
   }
   const int tiles_x = (W + kCTW - 1) / kCTW, tiles_y = (H + kCTH - 1) / kCTH;
   const int n_tiles = tiles_x * tiles_y * A.n;
-  uint32_t phase = 0;
-  bool issued = false;  // an MMA commit of this CTA may still be outstanding
+  // tile -> image and output origin (the halo starts one row and one column before)
+  auto origin = [&](int tile, int& img, int& x0, int& y0) {
+    img = tile / (tiles_x * tiles_y);
+    const int rem = tile - img * tiles_x * tiles_y;
+    y0 = (rem / tiles_x) * kCTH;
+    x0 = (rem % tiles_x) * kCTW;
+  };
+  const uint32_t sx0 = c_su32(sx) + kCGuard * 16;  // halo position 0 of group 0 (128-byte aligned)
+  uint32_t phase = 0, xphase = 0;
+  bool issued = false;        // an MMA commit of this CTA may still be outstanding
+  bool halo_pending = false;  // thread 0: a TMA halo copy may still be landing
+  if (IN == kConvInBF16 && tid == 0 && (int)blockIdx.x < n_tiles) {
+    int img, x0, y0;
+    origin(blockIdx.x, img, x0, y0);
+    c_load_halo(&tmap, sx0, xbar, img, x0, y0);
+    halo_pending = true;
+  }
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int img = tile / (tiles_x * tiles_y), rem = tile - img * tiles_x * tiles_y;
-    const int y0 = (rem / tiles_x) * kCTH, x0 = (rem % tiles_x) * kCTW;  // output origin; halo at (y0-1, x0-1)
+    int img, x0, y0;
+    origin(tile, img, x0, y0);
 
     // ---- stage the halo
-    if (IN == kConvInBF16) {
-      for (int i = tid; i < kCPos * 4; i += kCThreads) {  // 16 bytes (8 channels) each
-        const int p = i >> 2, g = i & 3;
-        const int gy = y0 - 1 + (p >> 5), gx = x0 - 1 + (p & 31);
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-          v = reinterpret_cast<const uint4*>(A.src_h + (((size_t)img * H + gy) * W + gx) * 32)[g];
-        *reinterpret_cast<uint4*>(sx + g * kCGroupB + (p + kCGuard) * 16) = v;
+    if (IN == kConvInBF16) {  // issued before this tile (above, or during the previous epilogue)
+      if (tid == 0) {
+        if (c_wait(xbar, xphase, A.wait_ns) != 0) {
+          atomicOr(A.error, 1024);
+          s_abort = 1;
+        } else {
+          xphase ^= 1u;
+          halo_pending = false;
+        }
       }
     } else {
       for (int p = tid; p < kCPos; p += kCThreads) {
@@ -223,6 +266,7 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM) conv_tc_kernel(RefineConvA
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (s_abort) break;  // the halo copy's wait gave up
 
     // ---- the tile's MMAs: M-tile m holds output positions 32 (4m + 1) + r, r < 128
     if (tid == 0) {
@@ -258,6 +302,13 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM) conv_tc_kernel(RefineConvA
     if (s_abort) break;
     issued = false;
     phase ^= 1u;
+    // the MMAs have read the halo: the next tile's copy lands during this epilogue
+    if (IN == kConvInBF16 && tid == 0 && tile + (int)gridDim.x < n_tiles) {
+      int nimg, nx0, ny0;
+      origin(tile + gridDim.x, nimg, nx0, ny0);
+      c_load_halo(&tmap, sx0, xbar, nimg, nx0, ny0);
+      halo_pending = true;
+    }
 
     // ---- epilogue: warp w reads lanes 32w.. (halo row 4m + 1 + w, column lane) of each M-tile
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
@@ -340,6 +391,8 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM) conv_tc_kernel(RefineConvA
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (tid == 0 && issued && s_abort && c_wait(bar, phase, kCDrainNs) != 0) atomicOr(A.error, 128);
+  // and for a halo copy still landing (a wait that gave up) before the shared memory is released
+  if (tid == 0 && halo_pending && c_wait(xbar, xphase, kCDrainNs) != 0) atomicOr(A.error, 2048);
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -352,7 +405,7 @@ namespace {
 template <int IN, int COUT, int EPI>
 cudaError_t launch_conv_tc_t(const RefineConvArgs& a, cudaStream_t s) {
   constexpr int N = COUT < 16 ? 16 : COUT;
-  constexpr int used = (IN == kConvInBF16 ? 18 : 3) * 2 * N * 16 + (IN == kConvInBF16 ? 4 : 1) * kCGroupB + 16;
+  constexpr int used = (IN == kConvInBF16 ? 18 : 3) * 2 * N * 16 + kCXOff + (IN == kConvInBF16 ? 4 : 1) * kCGroupB + 24;
   // At least 54 KB: no more than kCPerSM CTAs share an SM, so their tensor memory (128 columns each)
   // always fits and no CTA waits in tcgen05.alloc for another persistent CTA to finish.
   constexpr int smem = used < 54 * 1024 ? 54 * 1024 : used;
@@ -363,8 +416,26 @@ cudaError_t launch_conv_tc_t(const RefineConvArgs& a, cudaStream_t s) {
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  // The 32-channel input as a 5-D tensor {8 channels, 4 groups, W, H, n} of BF16 for the halo
+  // copies: a 16-byte aligned base; group, position, row and image strides of 16, 64, W * 64 and
+  // W * H * 64 bytes.  (Unused by the 3-channel instantiations.)
+  CUtensorMap tmap;
+  std::memset(&tmap, 0, sizeof(tmap));
+  if (IN == kConvInBF16) {
+    if ((reinterpret_cast<uintptr_t>(a.src_h) & 15u) != 0) return cudaErrorInvalidValue;
+    const EncodeTiled enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[5] = {8, 4, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
+    const cuuint64_t strides[4] = {16, 64, (cuuint64_t)a.W * 64, (cuuint64_t)a.W * a.H * 64};
+    const cuuint32_t box[5] = {8, 1, (cuuint32_t)kCHW, (cuuint32_t)kCHH, 1};
+    const cuuint32_t step[5] = {1, 1, 1, 1, 1};
+    if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(a.src_h), dims, strides, box,
+            step, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
   const int grid = n_tiles < sms * kCPerSM ? n_tiles : sms * kCPerSM;
-  conv_tc_kernel<IN, COUT, EPI><<<grid, kCThreads, smem, s>>>(a);
+  conv_tc_kernel<IN, COUT, EPI><<<grid, kCThreads, smem, s>>>(a, tmap);
   return cudaGetLastError();
 }
 

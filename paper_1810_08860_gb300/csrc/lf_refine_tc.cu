@@ -697,27 +697,6 @@ __global__ void __launch_bounds__(kThreads, 1) refine_fused_kernel(FusedArgs A, 
   }
 }
 
-namespace {
-
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// cuTensorMapEncodeTiled from the driver, reached through the runtime (no link against libcuda).
-EncodeTiled encode_tiled() {
-  static const EncodeTiled fn = []() -> EncodeTiled {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return nullptr;
-    return reinterpret_cast<EncodeTiled>(p);
-  }();
-  return fn;
-}
-
-}  // namespace
-
 cudaError_t launch_refine_fused(int32_t n, int32_t w, int32_t h, const float* in, float* out, float* out1,
                                 const float* params, const __nv_bfloat16* packed, int sm_count, int32_t* error,
                                 uint64_t wait_ns, cudaStream_t s, bool pdl) {
