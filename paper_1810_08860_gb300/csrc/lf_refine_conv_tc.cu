@@ -25,12 +25,14 @@
 // Per tile: the halo is staged (zeros outside the image), one thread issues
 // the tile's MMAs and commits to an mbarrier, every warp waits (bounded by
 // wait_ns, an error word on give-up), reads its lane quadrant of each M-tile's
-// accumulators with tcgen05.ld and runs the epilogue.  A 32-channel BF16 halo
-// arrives by TMA (one tiled copy per group of 8 channels, straight into the
-// MMA operand layout), the next tile's copy issued as soon as the current
-// tile's MMAs have read the buffer, so it lands during the epilogue; the
-// 3-channel FP32 halo is converted to BF16 pairs by the four warps.  Four CTAs
-// share an SM, so one CTA's MMAs overlap another's staging and epilogue.
+// accumulators with tcgen05.ld and runs the epilogue.  Halos arrive by TMA: a
+// 32-channel BF16 halo by one tiled copy per group of 8 channels straight into
+// the MMA operand layout, the next tile's copy issued as soon as the current
+// tile's MMAs have read the buffer (it lands during the epilogue); a 3-channel
+// FP32 RGBA halo into a staging buffer that the four warps convert to BF16
+// pairs, the next tile's copy issued as soon as they have read it (it lands
+// during the MMAs and the epilogue).  Four CTAs share an SM, so one CTA's MMAs
+// overlap another's staging and epilogue.
 //
 // Shared-memory operands use the K-major layout without swizzling: a position
 // (row) holds 8 channels in 16 contiguous bytes, rows follow every 16 bytes
@@ -59,6 +61,7 @@ constexpr int kCGuard = 2;                        // positions before and after 
 constexpr int kCGroupB = ((kCPos + 2 * kCGuard) * 16 + 127) / 128 * 128;  // bytes per group of 8 channels
 constexpr int kCXOff = 128 - kCGuard * 16;        // halo position 0 of each group starts 128-byte aligned
 constexpr int kCHaloTx = 4 * kCPos * 16;          // bytes of a tile's four TMA copies (32-channel halo)
+constexpr int kCXsB = kCPos * 16;                 // a tile's FP32 RGBA halo (3-channel input), one TMA copy
 constexpr int kCThreads = 128;
 constexpr int kCPerSM = 4;                        // CTAs per SM: 4 x 128 TMEM columns
 constexpr uint32_t kCTmemCols = 128;
@@ -136,6 +139,22 @@ __device__ __forceinline__ void c_load_halo(const CUtensorMap* tmap, uint32_t sx
         : "memory");
 }
 
+// Tile `tile`'s FP32 RGBA halo by TMA: one tiled copy (4 channels x 32
+// positions x 18 rows of the 4-D tensor map {4, W, H, n}; zeros outside the
+// image) into the staging buffer xs, completing on `bar`.  Earlier reads of xs
+// by this CTA's threads are ordered before the copy by a barrier and the
+// proxy fence.
+__device__ __forceinline__ void c_load_rgba(const CUtensorMap* tmap, uint32_t xs, uint64_t* bar, int img, int x0,
+                                            int y0) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(c_su32(bar)), "r"(kCXsB) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::
+          "r"(xs), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(x0 - 1), "r"(y0 - 1), "r"(img),
+      "r"(c_su32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ uint32_t c_pack(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
@@ -154,7 +173,10 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM)
   extern __shared__ __align__(128) unsigned char sm[];
   unsigned char* sw = sm;
   unsigned char* sx = sm + kWBytes + kCXOff;  // group g, position p: sx + g * kCGroupB + (p + kCGuard) * 16
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sx + G * kCGroupB);  // the tile's MMAs completed
+  constexpr int kXsOff = (kWBytes + kCXOff + G * kCGroupB + 127) / 128 * 128;
+  unsigned char* xs = sm + kXsOff;             // 3-channel input: the FP32 RGBA halo as it landed
+  constexpr int kBarOff = IN == kConvInBF16 ? kWBytes + kCXOff + G * kCGroupB : kXsOff + kCXsB;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kBarOff);     // the tile's MMAs completed
   uint64_t* xbar = bar + 1;                                         // the tile's TMA halo landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ float s_bias[32];
@@ -226,10 +248,11 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM)
   uint32_t phase = 0, xphase = 0;
   bool issued = false;        // an MMA commit of this CTA may still be outstanding
   bool halo_pending = false;  // thread 0: a TMA halo copy may still be landing
-  if (IN == kConvInBF16 && tid == 0 && (int)blockIdx.x < n_tiles) {
+  if (tid == 0 && (int)blockIdx.x < n_tiles) {
     int img, x0, y0;
     origin(blockIdx.x, img, x0, y0);
-    c_load_halo(&tmap, sx0, xbar, img, x0, y0);
+    if (IN == kConvInBF16) c_load_halo(&tmap, sx0, xbar, img, x0, y0);
+    else c_load_rgba(&tmap, c_su32(xs), xbar, img, x0, y0);
     halo_pending = true;
   }
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -247,19 +270,22 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM)
           halo_pending = false;
         }
       }
-    } else {
-      for (int p = tid; p < kCPos; p += kCThreads) {
-        float4 v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int q = p + h;
-          const int gy = y0 - 1 + (q >> 5), gx = x0 - 1 + (q & 31);
-          v[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (q < kCPos && gy >= 0 && gy < H && gx >= 0 && gx < W)
-            v[h] = reinterpret_cast<const float4*>(A.src_f)[((size_t)img * H + gy) * W + gx];
+    } else {  // every thread waits for the staged FP32 halo, then converts its positions
+      if (c_wait(xbar, xphase, A.wait_ns) != 0) {
+        atomicOr(A.error, 1024);
+        s_abort = 1;
+      } else {
+        xphase ^= 1u;
+        if (tid == 0) halo_pending = false;
+      }
+      __syncthreads();
+      if (!s_abort) {
+        const float4* xf = reinterpret_cast<const float4*>(xs);
+        for (int p = tid; p < kCPos; p += kCThreads) {
+          const float4 v0 = xf[p], v1 = p + 1 < kCPos ? xf[p + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+          *reinterpret_cast<uint4*>(sx + (p + kCGuard) * 16) =
+              make_uint4(c_pack(v0.x, v0.y), c_pack(v0.z, 0.f), c_pack(v1.x, v1.y), c_pack(v1.z, 0.f));
         }
-        *reinterpret_cast<uint4*>(sx + (p + kCGuard) * 16) =
-            make_uint4(c_pack(v[0].x, v[0].y), c_pack(v[0].z, 0.f), c_pack(v[1].x, v[1].y), c_pack(v[1].z, 0.f));
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
@@ -267,6 +293,13 @@ __global__ void __launch_bounds__(kCThreads, kCPerSM)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (s_abort) break;  // the halo copy's wait gave up
+    // the warps have read the staged FP32 halo: the next tile's copy lands during the MMAs
+    if (IN == kConvInRGBA && tid == 0 && tile + (int)gridDim.x < n_tiles) {
+      int nimg, nx0, ny0;
+      origin(tile + gridDim.x, nimg, nx0, ny0);
+      c_load_rgba(&tmap, c_su32(xs), xbar, nimg, nx0, ny0);
+      halo_pending = true;
+    }
 
     // ---- the tile's MMAs: M-tile m holds output positions 32 (4m + 1) + r, r < 128
     if (tid == 0) {
@@ -405,7 +438,9 @@ namespace {
 template <int IN, int COUT, int EPI>
 cudaError_t launch_conv_tc_t(const RefineConvArgs& a, cudaStream_t s) {
   constexpr int N = COUT < 16 ? 16 : COUT;
-  constexpr int used = (IN == kConvInBF16 ? 18 : 3) * 2 * N * 16 + kCXOff + (IN == kConvInBF16 ? 4 : 1) * kCGroupB + 24;
+  constexpr int kW = (IN == kConvInBF16 ? 18 : 3) * 2 * N * 16;
+  constexpr int used = IN == kConvInBF16 ? kW + kCXOff + 4 * kCGroupB + 24
+                                         : (kW + kCXOff + kCGroupB + 127) / 128 * 128 + kCXsB + 24;
   // At least 54 KB: no more than kCPerSM CTAs share an SM, so their tensor memory (128 columns each)
   // always fits and no CTA waits in tcgen05.alloc for another persistent CTA to finish.
   constexpr int smem = used < 54 * 1024 ? 54 * 1024 : used;
@@ -416,21 +451,32 @@ cudaError_t launch_conv_tc_t(const RefineConvArgs& a, cudaStream_t s) {
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  // The 32-channel input as a 5-D tensor {8 channels, 4 groups, W, H, n} of BF16 for the halo
-  // copies: a 16-byte aligned base; group, position, row and image strides of 16, 64, W * 64 and
-  // W * H * 64 bytes.  (Unused by the 3-channel instantiations.)
+  // The halo copies' tensor map, over a 16-byte aligned base.  32-channel input: a 5-D tensor
+  // {8 channels, 4 groups, W, H, n} of BF16, with group, position, row and image strides of 16,
+  // 64, W * 64 and W * H * 64 bytes.  3-channel input: a 4-D tensor {4 channels, W, H, n} of FP32
+  // RGBA, strides 16, W * 16 and W * H * 16 bytes.
   CUtensorMap tmap;
   std::memset(&tmap, 0, sizeof(tmap));
+  const EncodeTiled enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
   if (IN == kConvInBF16) {
     if ((reinterpret_cast<uintptr_t>(a.src_h) & 15u) != 0) return cudaErrorInvalidValue;
-    const EncodeTiled enc = encode_tiled();
-    if (!enc) return cudaErrorNotSupported;
     const cuuint64_t dims[5] = {8, 4, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
     const cuuint64_t strides[4] = {16, 64, (cuuint64_t)a.W * 64, (cuuint64_t)a.W * a.H * 64};
     const cuuint32_t box[5] = {8, 1, (cuuint32_t)kCHW, (cuuint32_t)kCHH, 1};
     const cuuint32_t step[5] = {1, 1, 1, 1, 1};
     if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(a.src_h), dims, strides, box,
             step, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  } else {
+    if ((reinterpret_cast<uintptr_t>(a.src_f) & 15u) != 0) return cudaErrorInvalidValue;
+    const cuuint64_t dims[4] = {4, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.n};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)a.W * 16, (cuuint64_t)a.W * a.H * 16};
+    const cuuint32_t box[4] = {4, (cuuint32_t)kCHW, (cuuint32_t)kCHH, 1};
+    const cuuint32_t step[4] = {1, 1, 1, 1};
+    if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(a.src_f), dims, strides, box, step,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
