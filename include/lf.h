@@ -109,7 +109,9 @@ typedef struct {
   int32_t n_eyes;
   int32_t n_views;
   int32_t active_views[2];  /* views with a nonzero disk weight at some pixel, eyes 0 and 1 */
-  int64_t triangles;        /* set-up (sub-)triangle records written */
+  int64_t triangles;        /* triangle pool records the call took: per view its set-up
+                               (sub-)triangles, or an upper bound of them (one per candidate
+                               triangle, two where two vertices lie in front of z_near) */
   int64_t tiles;            /* screen tiles rasterised */
   uint32_t error_word;      /* device error bits, 0 when clean */
   float ms_view_setup;      /* kernel durations of the last call when lf_config.timing = 1, else 0 */

@@ -670,8 +670,10 @@ __host__ __device__ inline int vertex_row_stride(int G) { return G + ((36 - G % 
 // vertices all lie beyond one side (or behind the eye), and append the
 // triangles that pass their own outcode test to a candidate list; (3) all
 // threads share the candidates for the full set-up (snap, clip, orientation,
-// fill rule).  Pass 1 counts the records, one atomic reserves the view's
-// segment, pass 2 writes them.  The order inside a segment does not matter:
+// fill rule).  With the whole grid in one band (the usual case) one atomic
+// reserves an upper bound of the view's records and one pass writes them;
+// with several bands pass 1 counts the records, one atomic reserves the
+// view's segment and pass 2 writes them.  The order inside a segment does not matter:
 // the raster's depth decision within a view is order-independent.  Then the
 // block bins its records into the screen tiles (bin_view), the shared memory
 // of the vertex arrays holding the per-tile counts.
@@ -703,7 +705,7 @@ __global__ void __launch_bounds__(BLOCK, 3) tri_setup_kernel(FrameArgs A, int ba
   uint16_t* s_cand = reinterpret_cast<uint16_t*>(S.z + nv_band);  // candidate triangles of the band
   S.oc = reinterpret_cast<uint8_t*>(s_cand + 2 * n_cell * band_rows);
   __shared__ int s_warp[NW];
-  __shared__ int s_ncand, s_pos;
+  __shared__ int s_ncand, s_pos, s_ntwo;
   __shared__ long long s_tri_base;
 
   SetupCtx C;
@@ -761,7 +763,7 @@ __global__ void __launch_bounds__(BLOCK, 3) tri_setup_kernel(FrameArgs A, int ba
   };
   // Warps walk the band's clusters; surviving triangles join the candidate list.
   auto gather = [&](int k0, int k1) {
-    if (threadIdx.x == 0) s_ncand = 0;
+    if (threadIdx.x == 0) s_ncand = s_ntwo = 0;
     __syncthreads();
     const int cy0 = k0 / kClusterCells, cy1 = (k1 + kClusterCells - 1) / kClusterCells;
     const int c0 = cy0 * ncl, c1 = cy1 * ncl;
@@ -777,13 +779,18 @@ __global__ void __launch_bounds__(BLOCK, 3) tri_setup_kernel(FrameArgs A, int ba
       if (__reduce_and_sync(0xffffffffu, oca) != 0u) continue;
       const int cell = lane >> 1, half = lane & 1;
       const int j = cl_x * kClusterCells + (cell & 3), k = cl_y * kClusterCells + (cell >> 2);
-      bool keep = false;
+      bool keep = false, two = false;
       if (j < n_cell && k < k1) {
         int q0, q1, q2;
         tri_slots(k - k0, j, half, q0, q1, q2);
-        keep = (S.oc[q0] & S.oc[q1] & S.oc[q2]) == 0;
+        const uint8_t o0 = S.oc[q0], o1 = S.oc[q1], o2 = S.oc[q2];
+        keep = (o0 & o1 & o2) == 0;
+        // exactly two vertices in front of the near plane: clipping may give two sub-triangles
+        two = keep && ((o0 & kOcBehind) == 0) + ((o1 & kOcBehind) == 0) + ((o2 & kOcBehind) == 0) == 2;
       }
       const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+      const uint32_t bal2 = __ballot_sync(0xffffffffu, two);
+      if (lane == 0 && bal2) atomicAdd(&s_ntwo, __popc(bal2));
       int base = 0;
       if (lane == 0 && bal) base = atomicAdd(&s_ncand, __popc(bal));
       base = __shfl_sync(0xffffffffu, base, 0);
@@ -801,7 +808,49 @@ __global__ void __launch_bounds__(BLOCK, 3) tri_setup_kernel(FrameArgs A, int ba
     return setup_parent(id, q0, q1, q2, S, C, tmp);
   };
 
-  // Pass 1: count the kept records.
+  if (n_bands == 1) {
+    // The whole grid in one band: one pass.  The view reserves an upper bound of
+    // its records (one per candidate, two for a candidate with exactly two
+    // vertices in front of the near plane), then writes the records it keeps
+    // compactly from the start of the reservation.
+    __syncthreads();
+    load_band(0, n_cell);
+    __syncthreads();
+    gather(0, n_cell);
+    const int nc = s_ncand;
+    if (threadIdx.x == 0) {
+      const int bound = nc + s_ntwo;
+      long long tb_ = -1;
+      if (bound > 0) {
+        const unsigned long long b = atomicAdd(A.pool_counter, (unsigned long long)bound);
+        if ((long long)b + bound <= A.pool_capacity) tb_ = (long long)b;
+        else atomicOr(A.error_word, kErrPoolOverflow);
+      }
+      s_tri_base = tb_;
+      s_pos = 0;
+    }
+    __syncthreads();
+    const long long tri_base = s_tri_base;
+    if (tri_base < 0) return;
+    for (int i = threadIdx.x; i < nc; i += BLOCK) {
+      TriRec tmp[2];
+      const int n = setup_cand(0, s_cand[i], tmp);
+      if (n) {
+        const int pos = atomicAdd(&s_pos, n);
+        for (int k = 0; k < n; ++k) A.pool[tri_base + pos + k] = tmp[k];
+      }
+    }
+    __syncthreads();  // the block's records are written and visible to all its threads
+    const int total = s_pos;
+    if (threadIdx.x == 0) {
+      R.tri_base = (int32_t)tri_base;
+      R.tri_count = total;
+    }
+    if (total > 0) bin_view<BLOCK>(A, R, total, (int)tri_base, reinterpret_cast<int*>(smem), cnt_cap, s_warp);
+    return;
+  }
+
+  // Several bands: pass 1 counts the kept records, pass 2 writes them.
   int my_count = 0;
   for (int bnd = 0; bnd < n_bands; ++bnd) {
     const int k0 = bnd * band_rows, k1 = min(k0 + band_rows, n_cell);
@@ -832,15 +881,13 @@ __global__ void __launch_bounds__(BLOCK, 3) tri_setup_kernel(FrameArgs A, int ba
   __syncthreads();
   const long long tri_base = s_tri_base;
   if (tri_base < 0) return;
-  // Pass 2: write the records (candidates of a single band are reused).
+  // Pass 2: write the records.
   for (int bnd = 0; bnd < n_bands; ++bnd) {
     const int k0 = bnd * band_rows, k1 = min(k0 + band_rows, n_cell);
-    if (n_bands > 1) {
-      __syncthreads();
-      load_band(k0, k1);
-      __syncthreads();
-      gather(k0, k1);
-    }
+    __syncthreads();
+    load_band(k0, k1);
+    __syncthreads();
+    gather(k0, k1);
     const int nc = s_ncand;
     for (int i = threadIdx.x; i < nc; i += BLOCK) {
       TriRec tmp[2];
